@@ -1,0 +1,292 @@
+"""CPU oracle for the Gaussian-splatting hot path (test infrastructure only).
+
+Only the test suite, the package smoke check and the benchmark's CPU-baseline
+leg may import this package.  It never imports the CUDA package: it takes plain
+numpy arrays (or the seeded input generator's dataclasses, read by attribute)
+and computes, in FP64, what the method defines (Sec. 3.1 projection and
+blending of splats, Sec. 3.2 Eq. 1 depth).  The integer decisions (visibility,
+radius, tile rectangle, depth key) are taken in FP32, the kernel's precision,
+by a fixed sequence of rounded operations in ``vrs_oracle.c``.
+
+Record and tile numbering of a multi-view batch (shared convention with the
+library's C-ABI, restated here from its definition):
+  record index of (view v, Gaussian g) = sum_{v' < v} N[scene(v')] + g
+  global tile id of tile (tx, ty) of view v = sum_{v' < v} gw[v'] gh[v'] + ty gw[v] + tx
+  sort key = (global tile id << 32) | float32 bits of the depth key
+  sorted order = (key, record index) ascending.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vrs_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+ALPHA_WIN = 5e-5     # relative window around 1/255 that marks a knife-edge pixel
+T_WIN = 1e-4         # relative window around the 1e-4 transmittance stop
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP, no fused multiply-add contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+               "-fopenmp", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class OrcCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("znear", ctypes.c_float), ("tan_fovx", ctypes.c_float),
+                ("tan_fovy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class OrcFlagOpts(ctypes.Structure):
+    _fields_ = [("alpha_win", ctypes.c_double), ("t_win", ctypes.c_double)]
+
+
+PROJ_DTYPE = np.dtype([("ubar", "f8"), ("vbar", "f8"), ("depth", "f8"), ("conic", "f8", 3),
+                       ("opacity", "f8"), ("rgb", "f8", 3), ("clamp_rgb", "i4", 3),
+                       ("clamp_x", "i4"), ("clamp_y", "i4")], align=True)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            L.orc_exp32.restype = ctypes.c_float
+            L.orc_exp32.argtypes = [ctypes.c_float]
+            L.orc_sh_basis_xyz.restype = None
+            L.orc_sh_basis_xyz.argtypes = [ctypes.c_double] * 3 + [P]
+            L.orc_decide.restype = ctypes.c_int
+            L.orc_decide.argtypes = [ctypes.c_int, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
+                                     P, P, P, P, P, P]
+            L.orc_project.restype = None
+            L.orc_project.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                      ctypes.POINTER(OrcCamera), P]
+            L.orc_render_brute.restype = None
+            L.orc_render_brute.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
+                                           ctypes.c_int, ctypes.POINTER(OrcFlagOpts), P, P, P, P, P,
+                                           P]
+            L.orc_render_bucketed.restype = None
+            L.orc_render_bucketed.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
+                                              ctypes.c_int, ctypes.POINTER(OrcFlagOpts), P, P, P, P,
+                                              P, P, P]
+            L.orc_render_bwd.restype = None
+            L.orc_render_bwd.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
+                                         ctypes.c_int, P, P, P, P]
+            L.orc_param_grads.restype = None
+            L.orc_param_grads.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                          ctypes.POINTER(OrcCamera), P, P, P, P, P, P, P]
+            L.orc_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def camera(cam) -> OrcCamera:
+    c = OrcCamera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.znear = float(cam.znear)
+    c.tan_fovx = float(np.float32(cam.tan_fovx))
+    c.tan_fovy = float(np.float32(cam.tan_fovy))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def exp32(x: float) -> float:
+    return float(lib().orc_exp32(float(np.float32(x))))
+
+
+def sh_basis(x: float, y: float, z: float) -> np.ndarray:
+    out = np.zeros(16, np.float64)
+    lib().orc_sh_basis_xyz(float(x), float(y), float(z), _p(out))
+    return out
+
+
+def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
+    """FP32 integer decisions for every Gaussian of `scene` in view `cam`."""
+    n = scene.n
+    means, ls, q = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)
+    out = dict(visible=np.zeros(n, np.uint8), depth=np.zeros(n, np.float32),
+               ubar=np.zeros(n, np.float32), vbar=np.zeros(n, np.float32),
+               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32))
+    c = camera(cam)
+    st = lib().orc_decide(n, _p(means), _p(ls), _p(q), ctypes.byref(c), tile,
+                          _p(out["visible"]), _p(out["depth"]), _p(out["ubar"]), _p(out["vbar"]),
+                          _p(out["radius"]), _p(out["rect"]))
+    out["status"] = int(st)
+    return out
+
+
+def project(scene, cam) -> np.ndarray:
+    """FP64 projection record (PROJ_DTYPE) of every Gaussian in view `cam`."""
+    n = scene.n
+    out = np.zeros(n, PROJ_DTYPE)
+    sh = _f32(scene.sh)
+    K = sh.shape[1] if n else (scene.sh_degree + 1) ** 2
+    c = camera(cam)
+    lib().orc_project(n, _p(_f32(scene.means)), _p(_f32(scene.log_scales)), _p(_f32(scene.quats)),
+                      _p(_f32(scene.opacity_logits)), _p(sh), K, ctypes.byref(c), _p(out))
+    return out
+
+
+def render(scene, cam, tile: int = 16, mode: str = "bucketed", dec=None, proj=None,
+           tile_mask: Optional[np.ndarray] = None, alpha_win: float = ALPHA_WIN,
+           t_win: float = T_WIN) -> Dict[str, np.ndarray]:
+    """Composited RGB [3,H,W], Eq. 1 depth [H,W], final T [H,W], n_contrib, knife-edge flags."""
+    dec = decide(scene, cam, tile) if dec is None else dec
+    proj = project(scene, cam) if proj is None else proj
+    H, W = cam.height, cam.width
+    out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), T=np.ones((H, W)),
+               n_contrib=np.zeros((H, W), np.int32), flags=np.zeros((H, W), np.uint8),
+               sig=np.zeros((H, W), np.int32))
+    c = camera(cam)
+    fo = OrcFlagOpts(alpha_win, t_win)
+    args = (scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(proj),
+            ctypes.byref(c), tile, ctypes.byref(fo))
+    if mode == "brute":
+        lib().orc_render_brute(*args, _p(out["rgb"]), _p(out["depth"]), _p(out["T"]),
+                               _p(out["n_contrib"]), _p(out["flags"]), _p(out["sig"]))
+    else:
+        tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+        lib().orc_render_bucketed(*args, None if tm is None else _p(tm), _p(out["rgb"]),
+                                  _p(out["depth"]), _p(out["T"]), _p(out["n_contrib"]),
+                                  _p(out["flags"]), _p(out["sig"]))
+    return out
+
+
+def render_bwd(scene, cam, dL_drgb, dL_ddepth, dL_dT=None, tile: int = 16, dec=None, proj=None):
+    """Per-Gaussian 2D gradients [N, 10] (d ubar, d vbar, d conic a/b/c, d opacity, d rgb, d depth)."""
+    dec = decide(scene, cam, tile) if dec is None else dec
+    proj = project(scene, cam) if proj is None else proj
+    g2 = np.zeros((scene.n, 10), np.float64)
+    gr = np.ascontiguousarray(dL_drgb, np.float64)
+    gd = np.ascontiguousarray(dL_ddepth, np.float64)
+    gt = None if dL_dT is None else np.ascontiguousarray(dL_dT, np.float64)
+    c = camera(cam)
+    lib().orc_render_bwd(scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(proj),
+                         ctypes.byref(c), tile, _p(gr), _p(gd), None if gt is None else _p(gt),
+                         _p(g2))
+    return g2
+
+
+def param_grads(scene, cam, g2, dec=None, tile: int = 16, acc=None) -> Dict[str, np.ndarray]:
+    """Chain rule from [N,10] 2D gradients to parameter gradients (FP64, accumulated)."""
+    dec = decide(scene, cam, tile) if dec is None else dec
+    n = scene.n
+    K = scene.sh.shape[1]
+    if acc is None:
+        acc = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+                   opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
+    c = camera(cam)
+    g2 = np.ascontiguousarray(g2, np.float64)
+    lib().orc_param_grads(n, _p(_f32(scene.means)), _p(_f32(scene.log_scales)),
+                          _p(_f32(scene.quats)), _p(_f32(scene.opacity_logits)),
+                          _p(_f32(scene.sh)), K, ctypes.byref(c), _p(dec["visible"]), _p(g2),
+                          _p(acc["means"]), _p(acc["log_scales"]), _p(acc["quats"]),
+                          _p(acc["opacity_logits"]), _p(acc["sh"]))
+    return acc
+
+
+def grads(scene, cam, dL_drgb, dL_ddepth, dL_dT=None, tile: int = 16):
+    """Full reverse pass of one view: parameter gradients in FP64."""
+    dec = decide(scene, cam, tile)
+    proj = project(scene, cam)
+    g2 = render_bwd(scene, cam, dL_drgb, dL_ddepth, dL_dT, tile, dec, proj)
+    return param_grads(scene, cam, g2, dec, tile)
+
+
+# ---------------------------------------------------------------------------
+# Integer binning and sort of a multi-view batch (Sec. 1: tiling and sorting of
+# all primitives), written directly from the key definition.
+
+def grid(cam, tile: int):
+    return (cam.width + tile - 1) // tile, (cam.height + tile - 1) // tile
+
+
+def bin_sort(scenes: Sequence, views: Sequence, tile: int = 16, decs: Optional[List] = None):
+    """Sorted 64-bit keys, record indices, per-tile [start, end) ranges and per-record counts."""
+    rec_base, tile_base = [], []
+    r = t = 0
+    for v in views:
+        rec_base.append(r)
+        tile_base.append(t)
+        r += scenes[v.scene].n
+        gw, gh = grid(v, tile)
+        t += gw * gh
+    n_tiles = t
+    keys, vals = [], []
+    counts = np.zeros(r, np.int64)
+    if decs is None:
+        decs = [decide(scenes[v.scene], v, tile) for v in views]
+    for vi, (v, d) in enumerate(zip(views, decs)):
+        gw, _ = grid(v, tile)
+        vis = np.nonzero(d["visible"])[0]
+        rect = d["rect"][vis].astype(np.int64)
+        nx = rect[:, 1] - rect[:, 0]
+        ny = rect[:, 3] - rect[:, 2]
+        cnt = nx * ny
+        counts[rec_base[vi] + vis] = cnt
+        if cnt.sum() == 0:
+            continue
+        owner = np.repeat(np.arange(len(vis)), cnt)
+        start = np.cumsum(cnt) - cnt
+        k = np.arange(cnt.sum()) - np.repeat(start, cnt)
+        ox = k % np.repeat(nx, cnt)
+        oy = k // np.repeat(nx, cnt)
+        tx = rect[owner, 0] + ox
+        ty = rect[owner, 2] + oy
+        tid = tile_base[vi] + ty * gw + tx
+        dbits = d["depth"][vis].view(np.uint32).astype(np.uint64)[owner]
+        keys.append((tid.astype(np.uint64) << np.uint64(32)) | dbits)
+        vals.append((rec_base[vi] + vis[owner]).astype(np.uint32))
+    if keys:
+        keys = np.concatenate(keys)
+        vals = np.concatenate(vals)
+    else:
+        keys = np.zeros(0, np.uint64)
+        vals = np.zeros(0, np.uint32)
+    order = np.lexsort((vals, keys))
+    keys, vals = keys[order], vals[order]
+    tiles_of = (keys >> np.uint64(32)).astype(np.int64)
+    ranges = np.zeros((n_tiles, 2), np.int64)
+    if len(keys):
+        ids = np.arange(n_tiles)
+        ranges[:, 0] = np.searchsorted(tiles_of, ids, side="left")
+        ranges[:, 1] = np.searchsorted(tiles_of, ids, side="right")
+    return dict(keys=keys, vals=vals, ranges=ranges, counts=counts, rec_base=rec_base,
+                tile_base=tile_base)

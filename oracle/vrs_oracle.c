@@ -1,0 +1,851 @@
+/*
+ * CPU oracle for the tile-based 3D Gaussian Splatting rasterizer that draws
+ * VR-Splatting's peripheral image P and its approximate depth buffer
+ * (Sec. 3.2, Eq. 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header or constant table with the CUDA path; it is written from the method's
+ * definition, step by step, so that it can be checked by eye.
+ *
+ * Two precisions, on purpose:
+ *  - The integer decisions of the method (visibility, screen radius, tile
+ *    rectangle, depth sort key) are taken in FP32, the kernel's precision,
+ *    following a fixed sequence of individually rounded operations
+ *    (orc_decide).  Build with -ffp-contract=off so that no multiply-add is
+ *    fused behind our back.
+ *  - Every floating output (2D mean, conic, opacity, colour, the composited
+ *    image, depth and transmittance, and all gradients) is computed in FP64
+ *    from the same FP32 inputs (orc_project, orc_render, orc_render_bwd,
+ *    orc_param_grads).
+ *
+ * Projection follows the EWA splatting / 3DGS formulation that the paper's
+ * periphery renderer builds on (Sec. 3.1 "Naive Method": splats with opacity,
+ * colour and a covariance built from scale and rotation, projected and blended
+ * to screen).  Compositing is front-to-back alpha blending with the 1/255 skip,
+ * the 0.99 clamp and the T < 1e-4 stop; the depth channel is Eq. 1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    float R[9];          /* world -> camera rotation, row-major */
+    float t[3];          /* x_cam = R x_world + t */
+    float fx, fy, cx, cy;
+    float znear;
+    float tan_fovx, tan_fovy;   /* half-FOV tangents bounding the Jacobian clamp */
+    int32_t width, height;
+} orc_camera;
+
+/* Output record of the FP64 projection, one per Gaussian. */
+typedef struct {
+    double ubar, vbar;        /* fx*x/z, fy*y/z: pixel offset from the principal point */
+    double depth;             /* view-space z of the mean (d_i of Eq. 1) */
+    double conic[3];          /* inverse of the dilated 2D covariance: a, b, c */
+    double opacity;
+    double rgb[3];
+    int32_t clamp_rgb[3];     /* 1 where max(0, .) clamped the colour channel */
+    int32_t clamp_x, clamp_y; /* 1 where the Jacobian clamp was active */
+} orc_proj;
+
+/* ------------------------------------------------------------------------- */
+/* Real spherical harmonics up to degree 3, in the (l, m = -l..l) order used by
+ * 3DGS, with the orthonormalisation constants written from their closed form
+ * (sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the polynomial's own factor). */
+
+static double sh_c0(void) { return 0.5 / sqrt(M_PI); }              /* 1/(2 sqrt(pi)) */
+static double sh_c1(void) { return sqrt(3.0 / (4.0 * M_PI)); }
+static double sh_c2a(void) { return 0.5 * sqrt(15.0 / M_PI); }
+static double sh_c2b(void) { return 0.25 * sqrt(5.0 / M_PI); }
+static double sh_c2c(void) { return 0.25 * sqrt(15.0 / M_PI); }
+static double sh_c3a(void) { return 0.25 * sqrt(35.0 / (2.0 * M_PI)); }
+static double sh_c3b(void) { return 0.5 * sqrt(105.0 / M_PI); }
+static double sh_c3c(void) { return 0.25 * sqrt(21.0 / (2.0 * M_PI)); }
+static double sh_c3d(void) { return 0.25 * sqrt(7.0 / M_PI); }
+static double sh_c3e(void) { return 0.25 * sqrt(105.0 / M_PI); }
+
+/* Basis polynomials at (x, y, z); the renderer passes a unit direction. */
+void orc_sh_basis_xyz(double x, double y, double z, double *Y)
+{
+    double xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = sh_c0();
+    Y[1] = -sh_c1() * y;
+    Y[2] = sh_c1() * z;
+    Y[3] = -sh_c1() * x;
+    Y[4] = sh_c2a() * x * y;
+    Y[5] = -sh_c2a() * y * z;
+    Y[6] = sh_c2b() * (2.0 * zz - xx - yy);
+    Y[7] = -sh_c2a() * x * z;
+    Y[8] = sh_c2c() * (xx - yy);
+    Y[9] = -sh_c3a() * y * (3.0 * xx - yy);
+    Y[10] = sh_c3b() * x * y * z;
+    Y[11] = -sh_c3c() * y * (4.0 * zz - xx - yy);
+    Y[12] = sh_c3d() * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = -sh_c3c() * x * (4.0 * zz - xx - yy);
+    Y[14] = sh_c3e() * z * (xx - yy);
+    Y[15] = -sh_c3a() * x * (xx - 3.0 * yy);
+}
+
+/* Partial derivatives of the 16 basis polynomials w.r.t. x, y, z. */
+static void sh_basis_grad(double x, double y, double z, double *dx, double *dy, double *dz)
+{
+    double xx = x * x, yy = y * y, zz = z * z;
+    for (int k = 0; k < 16; ++k) dx[k] = dy[k] = dz[k] = 0.0;
+    dy[1] = -sh_c1();
+    dz[2] = sh_c1();
+    dx[3] = -sh_c1();
+    dx[4] = sh_c2a() * y;            dy[4] = sh_c2a() * x;
+    dy[5] = -sh_c2a() * z;           dz[5] = -sh_c2a() * y;
+    dx[6] = -2.0 * sh_c2b() * x;     dy[6] = -2.0 * sh_c2b() * y;   dz[6] = 4.0 * sh_c2b() * z;
+    dx[7] = -sh_c2a() * z;           dz[7] = -sh_c2a() * x;
+    dx[8] = 2.0 * sh_c2c() * x;      dy[8] = -2.0 * sh_c2c() * y;
+    dx[9] = -sh_c3a() * 6.0 * x * y;                 dy[9] = -sh_c3a() * (3.0 * xx - 3.0 * yy);
+    dx[10] = sh_c3b() * y * z;  dy[10] = sh_c3b() * x * z;  dz[10] = sh_c3b() * x * y;
+    dx[11] = sh_c3c() * 2.0 * x * y;
+    dy[11] = -sh_c3c() * (4.0 * zz - xx - 3.0 * yy);
+    dz[11] = -sh_c3c() * 8.0 * y * z;
+    dx[12] = -sh_c3d() * 6.0 * x * z;   dy[12] = -sh_c3d() * 6.0 * y * z;
+    dz[12] = sh_c3d() * (6.0 * zz - 3.0 * xx - 3.0 * yy);
+    dx[13] = -sh_c3c() * (4.0 * zz - 3.0 * xx - yy);
+    dy[13] = sh_c3c() * 2.0 * x * y;
+    dz[13] = -sh_c3c() * 8.0 * x * z;
+    dx[14] = sh_c3e() * 2.0 * x * z;  dy[14] = -sh_c3e() * 2.0 * y * z;  dz[14] = sh_c3e() * (xx - yy);
+    dx[15] = -sh_c3a() * (3.0 * xx - 3.0 * yy);     dy[15] = sh_c3a() * 6.0 * x * y;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 exponential used by the decision path: Cody & Waite's range reduction
+ * (x = k ln2 + r with ln2 split into a short high part and a low correction)
+ * followed by the degree-7 Taylor polynomial of e^r on |r| <= ln2/2, evaluated
+ * by Horner's rule with fused multiply-adds, and an exact scaling by 2^k. */
+float orc_exp32(float x)
+{
+    if (x > 80.0f) x = 80.0f;
+    if (x < -80.0f) x = -80.0f;
+    const float log2e = 1.44269502f;
+    const float ln2_hi = 0.693145751953125f;       /* 22713 / 32768 */
+    const float ln2_lo = 1.42860677e-06f;          /* ln 2 - ln2_hi */
+    float kf = rintf(x * log2e);
+    float r = fmaf(-kf, ln2_hi, x);
+    r = fmaf(-kf, ln2_lo, r);
+    float p = 1.98412698e-04f;                     /* 1/7! */
+    p = fmaf(p, r, 1.38888889e-03f);               /* 1/6! */
+    p = fmaf(p, r, 8.33333377e-03f);               /* 1/5! */
+    p = fmaf(p, r, 4.16666679e-02f);               /* 1/4! */
+    p = fmaf(p, r, 1.66666672e-01f);               /* 1/3! */
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    int k = (int)kf;
+    uint32_t bits = (uint32_t)(k + 127) << 23;     /* 2^k, normal for |k| <= 116 */
+    float scale;
+    memcpy(&scale, &bits, 4);
+    return p * scale;
+}
+
+static int f_isfinite(float v) { return isfinite(v) ? 1 : 0; }
+
+/* ------------------------------------------------------------------------- */
+/* The integer decisions, in FP32.  Each statement below is one correctly
+ * rounded IEEE operation; the order is part of the definition.
+ *
+ * Returns per Gaussian: visible (0/1), the FP32 depth key, the FP32 screen
+ * offsets (ubar, vbar), the radius, and the tile rectangle [x0,x1) x [y0,y1).
+ * status bit 1: a quaternion had zero norm; bit 2: a non-finite parameter.
+ */
+int orc_decide(int n, const float *means, const float *log_scales, const float *quats,
+               const orc_camera *cam, int tile, uint8_t *visible, float *depth,
+               float *ubar, float *vbar, int32_t *radius, int32_t *rect)
+{
+    int status = 0;
+    const float *W = cam->R;
+    const int gw = (cam->width + tile - 1) / tile;
+    const int gh = (cam->height + tile - 1) / tile;
+    const float limx = 1.3f * cam->tan_fovx;
+    const float limy = 1.3f * cam->tan_fovy;
+    for (int g = 0; g < n; ++g) {
+        visible[g] = 0; depth[g] = 0.f; ubar[g] = 0.f; vbar[g] = 0.f; radius[g] = 0;
+        rect[4 * g + 0] = rect[4 * g + 1] = rect[4 * g + 2] = rect[4 * g + 3] = 0;
+        const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
+        const float *ls = log_scales + 3 * g;
+        const float *q = quats + 4 * g;
+        int finite = f_isfinite(mx) & f_isfinite(my) & f_isfinite(mz) & f_isfinite(ls[0]) &
+                     f_isfinite(ls[1]) & f_isfinite(ls[2]) & f_isfinite(q[0]) & f_isfinite(q[1]) &
+                     f_isfinite(q[2]) & f_isfinite(q[3]);
+        if (!finite) { status |= 2; continue; }
+        /* scales */
+        float s0 = orc_exp32(ls[0]), s1 = orc_exp32(ls[1]), s2 = orc_exp32(ls[2]);
+        /* normalised quaternion (w, x, y, z) */
+        float qq = q[0] * q[0];
+        qq = qq + q[1] * q[1];
+        qq = qq + q[2] * q[2];
+        qq = qq + q[3] * q[3];
+        if (!(qq > 0.0f)) { status |= 1; continue; }
+        float qn = sqrtf(qq);
+        float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+        float wx = w * x, wy = w * y, wz = w * z;
+        float Rq[9];
+        Rq[0] = 1.0f - 2.0f * (yy + zz); Rq[1] = 2.0f * (xy - wz);        Rq[2] = 2.0f * (xz + wy);
+        Rq[3] = 2.0f * (xy + wz);        Rq[4] = 1.0f - 2.0f * (xx + zz); Rq[5] = 2.0f * (yz - wx);
+        Rq[6] = 2.0f * (xz - wy);        Rq[7] = 2.0f * (yz + wx);        Rq[8] = 1.0f - 2.0f * (xx + yy);
+        float s[3] = {s0, s1, s2};
+        float M[9];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) M[3 * k + j] = Rq[3 * k + j] * s[j];
+        /* camera-space mean */
+        float tc[3];
+        for (int r = 0; r < 3; ++r) {
+            float a = W[3 * r] * mx;
+            a = a + W[3 * r + 1] * my;
+            a = a + W[3 * r + 2] * mz;
+            tc[r] = a + cam->t[r];
+        }
+        const float tx = tc[0], ty = tc[1], tz = tc[2];
+        if (!(tz > cam->znear)) continue;
+        /* clamped projection Jacobian, rows of T = J W */
+        float txtz = tx / tz, tytz = ty / tz;
+        float cxz = fminf(limx, fmaxf(-limx, txtz)) * tz;
+        float cyz = fminf(limy, fmaxf(-limy, tytz)) * tz;
+        float j00 = cam->fx / tz, j11 = cam->fy / tz, tz2 = tz * tz;
+        float j02 = -((cam->fx * cxz) / tz2);
+        float j12 = -((cam->fy * cyz) / tz2);
+        float T0[3], T1[3];
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = j00 * W[k] + j02 * W[6 + k];
+            T1[k] = j11 * W[3 + k] + j12 * W[6 + k];
+        }
+        /* V = T M (2x3); projected covariance = V V^T + 0.3 I */
+        float v0[3], v1[3];
+        for (int j = 0; j < 3; ++j) {
+            float a = T0[0] * M[j];
+            a = a + T0[1] * M[3 + j];
+            v0[j] = a + T0[2] * M[6 + j];
+            float b = T1[0] * M[j];
+            b = b + T1[1] * M[3 + j];
+            v1[j] = b + T1[2] * M[6 + j];
+        }
+        float n0 = v0[0] * v0[0]; n0 = n0 + v0[1] * v0[1]; n0 = n0 + v0[2] * v0[2];
+        float n1 = v1[0] * v1[0]; n1 = n1 + v1[1] * v1[1]; n1 = n1 + v1[2] * v1[2];
+        /* det(V V^T) = |v0 x v1|^2, with v0 x v1 = diag(s1 s2, s0 s2, s0 s1) Rq^T (T0 x T1) */
+        float c0 = T0[1] * T1[2] - T0[2] * T1[1];
+        float c1 = T0[2] * T1[0] - T0[0] * T1[2];
+        float c2 = T0[0] * T1[1] - T0[1] * T1[0];
+        float e[3];
+        for (int j = 0; j < 3; ++j) {
+            float a = Rq[j] * c0;
+            a = a + Rq[3 + j] * c1;
+            e[j] = a + Rq[6 + j] * c2;
+        }
+        float g0 = (s1 * s2) * e[0], g1 = (s0 * s2) * e[1], g2 = (s0 * s1) * e[2];
+        float dvv = g0 * g0; dvv = dvv + g1 * g1; dvv = dvv + g2 * g2;
+        float a_ = n0 + 0.3f, c_ = n1 + 0.3f;
+        float det = (dvv + 0.3f * (n0 + n1)) + 0.09f;
+        if (!(det > 0.0f)) continue;
+        float mid = 0.5f * (a_ + c_);
+        float disc = fmaxf(0.1f, mid * mid - det);
+        float lam = mid + sqrtf(disc);
+        float rad = ceilf(3.0f * sqrtf(lam));
+        float ub = cam->fx * txtz, vb = cam->fy * tytz;
+        float xlo = ub - rad, xhi = ub + rad, ylo = vb - rad, yhi = vb + rad;
+        /* tile rectangle: floor of the exact value of (edge + principal point) / tile */
+        int x0 = (int)floor(((double)xlo + (double)cam->cx) / tile);
+        int x1 = (int)floor(((double)xhi + (double)cam->cx) / tile) + 1;
+        int y0 = (int)floor(((double)ylo + (double)cam->cy) / tile);
+        int y1 = (int)floor(((double)yhi + (double)cam->cy) / tile) + 1;
+        x0 = x0 < 0 ? 0 : (x0 > gw ? gw : x0);
+        x1 = x1 < 0 ? 0 : (x1 > gw ? gw : x1);
+        y0 = y0 < 0 ? 0 : (y0 > gh ? gh : y0);
+        y1 = y1 < 0 ? 0 : (y1 > gh ? gh : y1);
+        if ((x1 - x0) * (y1 - y0) == 0) continue;
+        visible[g] = 1;
+        depth[g] = tz;
+        ubar[g] = ub; vbar[g] = vb;
+        radius[g] = (int32_t)rad;
+        rect[4 * g + 0] = x0; rect[4 * g + 1] = x1; rect[4 * g + 2] = y0; rect[4 * g + 3] = y1;
+    }
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP64 projection of one Gaussian (the floating outputs of the preprocess). */
+
+static void quat_to_rot(const double *q, double *R)
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void project_one(const float *m, const float *ls, const float *qf, float logit,
+                        const float *sh, int K, const orc_camera *cam, orc_proj *o)
+{
+    double W[9], t[3];
+    for (int i = 0; i < 9; ++i) W[i] = cam->R[i];
+    for (int i = 0; i < 3; ++i) t[i] = cam->t[i];
+    double mu[3] = {m[0], m[1], m[2]};
+    /* 3D covariance  Sigma = R S S^T R^T */
+    double s[3] = {exp((double)ls[0]), exp((double)ls[1]), exp((double)ls[2])};
+    double q[4] = {qf[0], qf[1], qf[2], qf[3]};
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] /= qn;
+    double Rq[9];
+    quat_to_rot(q, Rq);
+    double M[9];
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) M[3 * k + j] = Rq[3 * k + j] * s[j];
+    double Sig[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double a = 0;
+            for (int k = 0; k < 3; ++k) a += M[3 * i + k] * M[3 * j + k];
+            Sig[3 * i + j] = a;
+        }
+    /* camera-space mean */
+    double tc[3];
+    for (int r = 0; r < 3; ++r) tc[r] = W[3 * r] * mu[0] + W[3 * r + 1] * mu[1] + W[3 * r + 2] * mu[2] + t[r];
+    double tx = tc[0], ty = tc[1], tz = tc[2];
+    /* Jacobian of the perspective projection, with the 1.3 x half-FOV guard */
+    double limx = 1.3 * cam->tan_fovx, limy = 1.3 * cam->tan_fovy;
+    double rx = tx / tz, ry = ty / tz;
+    o->clamp_x = (rx > limx || rx < -limx);
+    o->clamp_y = (ry > limy || ry < -limy);
+    double cxz = (rx > limx ? limx : (rx < -limx ? -limx : rx)) * tz;
+    double cyz = (ry > limy ? limy : (ry < -limy ? -limy : ry)) * tz;
+    double J[6] = {cam->fx / tz, 0.0, -cam->fx * cxz / (tz * tz),
+                   0.0, cam->fy / tz, -cam->fy * cyz / (tz * tz)};
+    /* T = J W ; Sigma' = T Sigma T^T + 0.3 I */
+    double T[6];
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0;
+            for (int k = 0; k < 3; ++k) v += J[3 * a + k] * W[3 * k + j];
+            T[3 * a + j] = v;
+        }
+    double S2[4];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            double v = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) v += T[3 * a + i] * Sig[3 * i + j] * T[3 * b + j];
+            S2[2 * a + b] = v;
+        }
+    double A = S2[0] + 0.3, B = S2[1], C = S2[3] + 0.3;
+    double det = A * C - B * B;
+    o->conic[0] = C / det;
+    o->conic[1] = -B / det;
+    o->conic[2] = A / det;
+    o->ubar = cam->fx * tx / tz;
+    o->vbar = cam->fy * ty / tz;
+    o->depth = tz;
+    o->opacity = 1.0 / (1.0 + exp(-(double)logit));
+    /* view-dependent colour: dir from the camera centre (-W^T t) to the mean */
+    double cc[3];
+    for (int i = 0; i < 3; ++i) cc[i] = -(W[i] * t[0] + W[3 + i] * t[1] + W[6 + i] * t[2]);
+    double d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int i = 0; i < 3; ++i) d[i] /= dn;
+    double Y[16];
+    orc_sh_basis_xyz(d[0], d[1], d[2], Y);
+    for (int ch = 0; ch < 3; ++ch) {
+        double v = 0;
+        for (int k = 0; k < K; ++k) v += Y[k] * sh[3 * k + ch];
+        v += 0.5;
+        o->clamp_rgb[ch] = v < 0.0;
+        o->rgb[ch] = v < 0.0 ? 0.0 : v;
+    }
+}
+
+void orc_project(int n, const float *means, const float *log_scales, const float *quats,
+                 const float *opacity_logits, const float *sh, int K, const orc_camera *cam,
+                 orc_proj *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < n; ++g)
+        project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
+                    sh + (size_t)3 * K * g, K, cam, out + g);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Compositing.  The candidate list of a pixel is every visible Gaussian whose
+ * tile rectangle holds the pixel's tile, ordered by (FP32 depth key, index):
+ * the tile's sorted instance list.  Front to back, each candidate gets
+ *   power = -1/2 (a dx^2 + c dy^2) - b dx dy ,  d = 2D mean - pixel centre,
+ *   alpha = min(0.99, opacity * exp(power)), skipped if power > 0 or alpha < 1/255;
+ *   T' = T (1 - alpha); if T' < 1e-4 the pixel stops without this candidate;
+ *   otherwise C += rgb alpha T, D += depth alpha T (Eq. 1), T = T'.
+ * n_contrib is the 1-based position of the last blended candidate.
+ * flags: bit 1 = some alpha within the relative window of 1/255,
+ *        bit 2 = some T' within the relative window of 1e-4.             */
+
+typedef struct { float key; int32_t idx; } cand_t;
+
+static int cand_cmp(const void *pa, const void *pb)
+{
+    const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
+    uint32_t ka, kb;
+    memcpy(&ka, &a->key, 4);
+    memcpy(&kb, &b->key, 4);
+    if (ka != kb) return ka < kb ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+typedef struct {
+    double alpha_win;   /* relative window around 1/255 that flags a pixel */
+    double t_win;       /* relative window around 1e-4 that flags a pixel */
+} orc_flag_opts;
+
+static void composite_pixel(const cand_t *cands, int nc, const orc_proj *P, double pxc, double pyc,
+                            const orc_flag_opts *fo, double *rgb, double *dep, double *Tout,
+                            int32_t *last_out, uint8_t *flag_out, int32_t *sig_out)
+{
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
+    int last = 0, nblend = 0, nclamp = 0;
+    uint8_t flag = 0;
+    for (int p = 0; p < nc; ++p) {
+        const orc_proj *g = P + cands[p].idx;
+        double dx = g->ubar - pxc, dy = g->vbar - pyc;
+        double power = -0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) - g->conic[1] * dx * dy;
+        if (power > 0.0) continue;
+        double raw = g->opacity * exp(power);
+        if (fabs(raw * 255.0 - 1.0) < fo->alpha_win) flag |= 1;
+        double alpha = raw < 0.99 ? raw : 0.99;
+        if (alpha < 1.0 / 255.0) continue;
+        double Tn = T * (1.0 - alpha);
+        if (fabs(Tn * 1e4 - 1.0) < fo->t_win) flag |= 2;
+        if (Tn < 1e-4) break;
+        double w = alpha * T;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * w;
+        D += g->depth * w;
+        T = Tn;
+        last = p + 1;
+        ++nblend;
+        if (raw >= 0.99) ++nclamp;
+    }
+    rgb[0] = C[0]; rgb[1] = C[1]; rgb[2] = C[2];
+    *dep = D;
+    *Tout = T;
+    *last_out = last;
+    *flag_out = flag;
+    /* signature of the blended set: changes when any discrete choice changes */
+    *sig_out = nblend + 65536 * nclamp;
+}
+
+/* Brute force: every pixel scans all n Gaussians.  Outputs are CHW. */
+void orc_render_brute(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
+                      const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
+                      double *rgb, double *depth, double *Tfin, int32_t *n_contrib, uint8_t *flags,
+                      int32_t *sig)
+{
+    const int W = cam->width, H = cam->height;
+    const size_t HW = (size_t)W * H;
+#pragma omp parallel
+    {
+        cand_t *cands = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int j = 0; j < H; ++j) {
+            for (int i = 0; i < W; ++i) {
+                int tx = i / tile, ty = j / tile, nc = 0;
+                for (int g = 0; g < n; ++g) {
+                    if (!visible[g]) continue;
+                    const int32_t *r = rect + 4 * g;
+                    if (tx < r[0] || tx >= r[1] || ty < r[2] || ty >= r[3]) continue;
+                    cands[nc].key = depth_key[g];
+                    cands[nc].idx = g;
+                    ++nc;
+                }
+                qsort(cands, nc, sizeof(cand_t), cand_cmp);
+                double c3[3], d, T;
+                int32_t last, sg;
+                uint8_t fl;
+                composite_pixel(cands, nc, P, i + 0.5 - cam->cx, j + 0.5 - cam->cy, fo, c3, &d, &T,
+                                &last, &fl, &sg);
+                size_t pix = (size_t)j * W + i;
+                rgb[pix] = c3[0]; rgb[HW + pix] = c3[1]; rgb[2 * HW + pix] = c3[2];
+                depth[pix] = d; Tfin[pix] = T; n_contrib[pix] = last; flags[pix] = fl; sig[pix] = sg;
+            }
+        }
+        free(cands);
+    }
+}
+
+/* Per-tile candidate lists, built by scanning each Gaussian's rectangle. */
+typedef struct { int32_t *start; int32_t *count; cand_t *items; int ntiles; } tile_lists;
+
+static void build_tile_lists(int n, const uint8_t *visible, const float *depth_key,
+                             const int32_t *rect, int gw, int gh, tile_lists *L)
+{
+    int nt = gw * gh;
+    L->ntiles = nt;
+    L->start = (int32_t *)calloc((size_t)nt + 1, sizeof(int32_t));
+    L->count = (int32_t *)calloc((size_t)nt, sizeof(int32_t));
+    int64_t total = 0;
+    for (int g = 0; g < n; ++g) {
+        if (!visible[g]) continue;
+        const int32_t *r = rect + 4 * g;
+        for (int y = r[2]; y < r[3]; ++y)
+            for (int x = r[0]; x < r[1]; ++x) { L->count[y * gw + x]++; ++total; }
+    }
+    int64_t acc = 0;
+    for (int t = 0; t < nt; ++t) { L->start[t] = (int32_t)acc; acc += L->count[t]; }
+    L->start[nt] = (int32_t)acc;
+    L->items = (cand_t *)malloc(sizeof(cand_t) * (size_t)(total > 0 ? total : 1));
+    int32_t *fill = (int32_t *)calloc((size_t)nt, sizeof(int32_t));
+    for (int g = 0; g < n; ++g) {
+        if (!visible[g]) continue;
+        const int32_t *r = rect + 4 * g;
+        for (int y = r[2]; y < r[3]; ++y)
+            for (int x = r[0]; x < r[1]; ++x) {
+                int t = y * gw + x;
+                cand_t *c = L->items + L->start[t] + fill[t]++;
+                c->key = depth_key[g];
+                c->idx = g;
+            }
+    }
+    free(fill);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < nt; ++t)
+        qsort(L->items + L->start[t], L->count[t], sizeof(cand_t), cand_cmp);
+}
+
+static void free_tile_lists(tile_lists *L) { free(L->start); free(L->count); free(L->items); }
+
+/* Bucketed: each pixel iterates its tile's list only; the same result as the
+ * brute force.  `tile_mask` (nullable, gw*gh bytes) restricts the work to the
+ * tiles marked 1; other pixels are left untouched (used for bounded timing). */
+void orc_render_bucketed(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
+                         const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
+                         const uint8_t *tile_mask, double *rgb, double *depth, double *Tfin,
+                         int32_t *n_contrib, uint8_t *flags, int32_t *sig)
+{
+    const int W = cam->width, H = cam->height;
+    const size_t HW = (size_t)W * H;
+    const int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
+    tile_lists L;
+    build_tile_lists(n, visible, depth_key, rect, gw, gh, &L);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < gw * gh; ++t) {
+        if (tile_mask && !tile_mask[t]) continue;
+        int tx = t % gw, ty = t / gw;
+        for (int j = ty * tile; j < (ty + 1) * tile && j < H; ++j)
+            for (int i = tx * tile; i < (tx + 1) * tile && i < W; ++i) {
+                double c3[3], d, T;
+                int32_t last, sg;
+                uint8_t fl;
+                composite_pixel(L.items + L.start[t], L.count[t], P, i + 0.5 - cam->cx,
+                                j + 0.5 - cam->cy, fo, c3, &d, &T, &last, &fl, &sg);
+                size_t pix = (size_t)j * W + i;
+                rgb[pix] = c3[0]; rgb[HW + pix] = c3[1]; rgb[2 * HW + pix] = c3[2];
+                depth[pix] = d; Tfin[pix] = T; n_contrib[pix] = last; flags[pix] = fl; sig[pix] = sg;
+            }
+    }
+    free_tile_lists(&L);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reverse pass.  For each pixel the forward list is recomputed; with
+ * w_i = alpha_i T_i, T_i = prod_{m<i} (1 - alpha_m) (a prefix product, no
+ * division), and the explicit suffix sums S_C,i = sum_{j>i} rgb_j w_j,
+ * S_D,i = sum_{j>i} d_j w_j over the blended candidates:
+ *   dL/drgb_i   += g_C w_i ,   dL/ddepth_i += g_D w_i ,
+ *   dL/dalpha_i  = T_i (g_C . rgb_i + g_D d_i) - (g_C . S_C,i + g_D S_D,i + g_T T_final) / (1 - alpha_i),
+ * and, where alpha was not clamped at 0.99, through alpha = o exp(power):
+ *   dL/do += dL/dalpha exp(power);  dL/dpower = dL/dalpha alpha.
+ * Per-Gaussian 2D gradients (FP64), 10 per Gaussian:
+ *   [d ubar, d vbar, d conic_a, d conic_b, d conic_c, d opacity, d r, d g, d b, d depth]. */
+
+#define G2_N 10
+
+static void reverse_pixel(const cand_t *cands, int nc, const orc_proj *P, double pxc, double pyc,
+                          const double *gC, double gD, double gT, double *g2, int *blend_idx,
+                          double *alpha_s, double *Tpre, double *powr)
+{
+    /* forward again, recording the blended candidates */
+    double T = 1.0;
+    int nb = 0;
+    for (int p = 0; p < nc; ++p) {
+        const orc_proj *g = P + cands[p].idx;
+        double dx = g->ubar - pxc, dy = g->vbar - pyc;
+        double power = -0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) - g->conic[1] * dx * dy;
+        if (power > 0.0) continue;
+        double raw = g->opacity * exp(power);
+        double alpha = raw < 0.99 ? raw : 0.99;
+        if (alpha < 1.0 / 255.0) continue;
+        double Tn = T * (1.0 - alpha);
+        if (Tn < 1e-4) break;
+        blend_idx[nb] = p;
+        alpha_s[nb] = alpha;
+        powr[nb] = power;
+        Tpre[nb] = T;
+        ++nb;
+        T = Tn;
+    }
+    const double Tfinal = T;
+    /* suffix sums by an explicit backward accumulation over the blended list */
+    double SC[3] = {0, 0, 0}, SD = 0.0;
+    for (int b = nb - 1; b >= 0; --b) {
+        const int gi = cands[blend_idx[b]].idx;
+        const orc_proj *g = P + gi;
+        const double a = alpha_s[b], Ti = Tpre[b], w = a * Ti;
+        double *o = g2 + (size_t)G2_N * gi;
+        for (int ch = 0; ch < 3; ++ch) o[6 + ch] += gC[ch] * w;
+        o[9] += gD * w;
+        double dot_c = gC[0] * g->rgb[0] + gC[1] * g->rgb[1] + gC[2] * g->rgb[2];
+        double dot_s = gC[0] * SC[0] + gC[1] * SC[1] + gC[2] * SC[2];
+        double dL_da = Ti * (dot_c + gD * g->depth) - (dot_s + gD * SD + gT * Tfinal) / (1.0 - a);
+        double raw = g->opacity * exp(powr[b]);
+        if (raw < 0.99) {
+            double ex = exp(powr[b]);
+            o[5] += dL_da * ex;
+            double dL_dp = dL_da * a;
+            double dx = g->ubar - pxc, dy = g->vbar - pyc;
+            o[0] += dL_dp * (-(g->conic[0] * dx + g->conic[1] * dy));
+            o[1] += dL_dp * (-(g->conic[2] * dy + g->conic[1] * dx));
+            o[2] += dL_dp * (-0.5 * dx * dx);
+            o[3] += dL_dp * (-dx * dy);
+            o[4] += dL_dp * (-0.5 * dy * dy);
+        }
+        for (int ch = 0; ch < 3; ++ch) SC[ch] += g->rgb[ch] * w;
+        SD += g->depth * w;
+    }
+}
+
+/* dL_drgb [3,H,W], dL_ddepth [H,W], dL_dT [H,W] (nullable); g2 is [n, 10], accumulated. */
+void orc_render_bwd(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
+                    const orc_proj *P, const orc_camera *cam, int tile, const double *dL_drgb,
+                    const double *dL_ddepth, const double *dL_dT, double *g2)
+{
+    const int W = cam->width, H = cam->height;
+    const size_t HW = (size_t)W * H;
+    const int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
+    tile_lists L;
+    build_tile_lists(n, visible, depth_key, rect, gw, gh, &L);
+    int maxc = 1;
+    for (int t = 0; t < gw * gh; ++t) if (L.count[t] > maxc) maxc = L.count[t];
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double *acc = (double *)calloc((size_t)nthreads * G2_N * (size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = acc + (size_t)tid * G2_N * (size_t)(n > 0 ? n : 1);
+        int *bi = (int *)malloc(sizeof(int) * maxc);
+        double *as = (double *)malloc(sizeof(double) * maxc);
+        double *tp = (double *)malloc(sizeof(double) * maxc);
+        double *pw = (double *)malloc(sizeof(double) * maxc);
+#pragma omp for schedule(dynamic, 1)
+        for (int t = 0; t < gw * gh; ++t) {
+            int tx = t % gw, ty = t / gw;
+            for (int j = ty * tile; j < (ty + 1) * tile && j < H; ++j)
+                for (int i = tx * tile; i < (tx + 1) * tile && i < W; ++i) {
+                    size_t pix = (size_t)j * W + i;
+                    double gC[3] = {dL_drgb[pix], dL_drgb[HW + pix], dL_drgb[2 * HW + pix]};
+                    reverse_pixel(L.items + L.start[t], L.count[t], P, i + 0.5 - cam->cx,
+                                  j + 0.5 - cam->cy, gC, dL_ddepth[pix], dL_dT ? dL_dT[pix] : 0.0,
+                                  mine, bi, as, tp, pw);
+                }
+        }
+        free(bi); free(as); free(tp); free(pw);
+    }
+    for (int th = 0; th < nthreads; ++th)
+        for (size_t k = 0; k < (size_t)G2_N * n; ++k) g2[k] += acc[(size_t)th * G2_N * n + k];
+    free(acc);
+    free_tile_lists(&L);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chain rule from the 2D gradients of one view to the Gaussian parameters, in
+ * FP64.  Accumulates (+=) into the parameter gradients.  Gaussians that are not
+ * visible in the view get nothing. */
+
+void orc_param_grads(int n, const float *means, const float *log_scales, const float *quats,
+                     const float *opacity_logits, const float *sh, int K, const orc_camera *cam,
+                     const uint8_t *visible, const double *g2, double *g_means, double *g_log_scales,
+                     double *g_quats, double *g_logits, double *g_sh)
+{
+#pragma omp parallel for schedule(static)
+    for (int gi = 0; gi < n; ++gi) {
+        if (!visible[gi]) continue;
+        const double *G = g2 + (size_t)G2_N * gi;
+        const float *m = means + 3 * gi, *ls = log_scales + 3 * gi, *qf = quats + 4 * gi;
+        const float *shg = sh + (size_t)3 * K * gi;
+        orc_proj pr;
+        project_one(m, ls, qf, opacity_logits[gi], shg, K, cam, &pr);
+        double W[9], t[3];
+        for (int i = 0; i < 9; ++i) W[i] = cam->R[i];
+        for (int i = 0; i < 3; ++i) t[i] = cam->t[i];
+        double mu[3] = {m[0], m[1], m[2]};
+        double dmu[3] = {0, 0, 0};
+
+        /* opacity = sigmoid(logit) */
+        g_logits[gi] += G[5] * pr.opacity * (1.0 - pr.opacity);
+
+        /* colour: rgb_ch = max(0, sum_k Y_k(dir) sh_k,ch + 0.5), dir = (mu - c)/|mu - c| */
+        double cc[3];
+        for (int i = 0; i < 3; ++i) cc[i] = -(W[i] * t[0] + W[3 + i] * t[1] + W[6 + i] * t[2]);
+        double v[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+        double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double d[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+        double Y[16], Yx[16], Yy[16], Yz[16];
+        orc_sh_basis_xyz(d[0], d[1], d[2], Y);
+        sh_basis_grad(d[0], d[1], d[2], Yx, Yy, Yz);
+        double gdir[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ++ch) {
+            if (pr.clamp_rgb[ch]) continue;
+            double gc = G[6 + ch];
+            for (int k = 0; k < K; ++k) {
+                g_sh[(size_t)3 * K * gi + 3 * k + ch] += gc * Y[k];
+                gdir[0] += gc * shg[3 * k + ch] * Yx[k];
+                gdir[1] += gc * shg[3 * k + ch] * Yy[k];
+                gdir[2] += gc * shg[3 * k + ch] * Yz[k];
+            }
+        }
+        double dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
+        for (int i = 0; i < 3; ++i) dmu[i] += (gdir[i] - d[i] * dd) / vn;
+
+        /* camera-space mean and projection */
+        double tc[3];
+        for (int r = 0; r < 3; ++r) tc[r] = W[3 * r] * mu[0] + W[3 * r + 1] * mu[1] + W[3 * r + 2] * mu[2] + t[r];
+        double tx = tc[0], ty = tc[1], tz = tc[2];
+        double dtc[3] = {0, 0, 0};
+        /* ubar = fx tx / tz, vbar = fy ty / tz, depth = tz */
+        dtc[0] += G[0] * cam->fx / tz;
+        dtc[1] += G[1] * cam->fy / tz;
+        dtc[2] += -G[0] * cam->fx * tx / (tz * tz) - G[1] * cam->fy * ty / (tz * tz);
+        dtc[2] += G[9];
+
+        /* rebuild Sigma, J, T and Sigma' */
+        double s[3] = {exp((double)ls[0]), exp((double)ls[1]), exp((double)ls[2])};
+        double q[4] = {qf[0], qf[1], qf[2], qf[3]};
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qh[4] = {q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn};
+        double Rq[9];
+        quat_to_rot(qh, Rq);
+        double M[9];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) M[3 * k + j] = Rq[3 * k + j] * s[j];
+        double Sig[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double a = 0;
+                for (int k = 0; k < 3; ++k) a += M[3 * i + k] * M[3 * j + k];
+                Sig[3 * i + j] = a;
+            }
+        double limx = 1.3 * cam->tan_fovx, limy = 1.3 * cam->tan_fovy;
+        double rx = tx / tz, ry = ty / tz;
+        double Lx = rx > limx ? limx : (rx < -limx ? -limx : rx);
+        double Ly = ry > limy ? limy : (ry < -limy ? -limy : ry);
+        double J00 = cam->fx / tz, J11 = cam->fy / tz;
+        double J02 = -cam->fx * Lx * tz / (tz * tz), J12 = -cam->fy * Ly * tz / (tz * tz);
+        double T0[3], T1[3];
+        for (int j = 0; j < 3; ++j) {
+            T0[j] = J00 * W[j] + J02 * W[6 + j];
+            T1[j] = J11 * W[3 + j] + J12 * W[6 + j];
+        }
+        double ST0[3], ST1[3];
+        for (int i = 0; i < 3; ++i) {
+            ST0[i] = Sig[3 * i] * T0[0] + Sig[3 * i + 1] * T0[1] + Sig[3 * i + 2] * T0[2];
+            ST1[i] = Sig[3 * i] * T1[0] + Sig[3 * i + 1] * T1[1] + Sig[3 * i + 2] * T1[2];
+        }
+        double A = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + 0.3;
+        double B = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+        double C = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + 0.3;
+        double det = A * C - B * B, det2 = det * det;
+        /* conic = (C/det, -B/det, A/det): partials w.r.t. (A, B, C) */
+        double dca_dA = -C * C / det2, dca_dB = 2.0 * B * C / det2, dca_dC = -B * B / det2;
+        double dcb_dA = B * C / det2, dcb_dB = -(A * C + B * B) / det2, dcb_dC = A * B / det2;
+        double dcc_dA = -B * B / det2, dcc_dB = 2.0 * A * B / det2, dcc_dC = -A * A / det2;
+        double gA = G[2] * dca_dA + G[3] * dcb_dA + G[4] * dcc_dA;
+        double gB = G[2] * dca_dB + G[3] * dcb_dB + G[4] * dcc_dB;
+        double gC = G[2] * dca_dC + G[3] * dcb_dC + G[4] * dcc_dC;
+        /* A = T0' Sig T0 + .3, B = T0' Sig T1, C = T1' Sig T1 + .3 */
+        double gSig[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                gSig[3 * i + j] = gA * T0[i] * T0[j] + gB * T0[i] * T1[j] + gC * T1[i] * T1[j];
+        double gT0[3], gT1[3];
+        for (int i = 0; i < 3; ++i) {
+            gT0[i] = 2.0 * gA * ST0[i] + gB * ST1[i];
+            gT1[i] = gB * ST0[i] + 2.0 * gC * ST1[i];
+        }
+        /* T0 = J00 W0 + J02 W2 ; T1 = J11 W1 + J12 W2 */
+        double gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+        for (int j = 0; j < 3; ++j) {
+            gJ00 += gT0[j] * W[j];
+            gJ02 += gT0[j] * W[6 + j];
+            gJ11 += gT1[j] * W[3 + j];
+            gJ12 += gT1[j] * W[6 + j];
+        }
+        dtc[2] += gJ00 * (-cam->fx / (tz * tz)) + gJ11 * (-cam->fy / (tz * tz));
+        if (!pr.clamp_x) {   /* J02 = -fx tx / tz^2 */
+            dtc[0] += gJ02 * (-cam->fx / (tz * tz));
+            dtc[2] += gJ02 * (2.0 * cam->fx * tx / (tz * tz * tz));
+        } else {             /* J02 = -fx L / tz */
+            dtc[2] += gJ02 * (cam->fx * Lx / (tz * tz));
+        }
+        if (!pr.clamp_y) {
+            dtc[1] += gJ12 * (-cam->fy / (tz * tz));
+            dtc[2] += gJ12 * (2.0 * cam->fy * ty / (tz * tz * tz));
+        } else {
+            dtc[2] += gJ12 * (cam->fy * Ly / (tz * tz));
+        }
+        /* tc = W mu + t */
+        for (int i = 0; i < 3; ++i) dmu[i] += W[i] * dtc[0] + W[3 + i] * dtc[1] + W[6 + i] * dtc[2];
+        for (int i = 0; i < 3; ++i) g_means[3 * gi + i] += dmu[i];
+
+        /* Sigma = M M^T (gSig taken as the gradient w.r.t. a general matrix) */
+        double gM[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double a = 0;
+                for (int k = 0; k < 3; ++k) a += (gSig[3 * i + k] + gSig[3 * k + i]) * M[3 * k + j];
+                gM[3 * i + j] = a;
+            }
+        /* M = Rq S */
+        double gR[9];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) gR[3 * k + j] = gM[3 * k + j] * s[j];
+        for (int j = 0; j < 3; ++j) {
+            double gs = 0;
+            for (int k = 0; k < 3; ++k) gs += gM[3 * k + j] * Rq[3 * k + j];
+            g_log_scales[3 * gi + j] += gs * s[j];
+        }
+        /* Rq(w, x, y, z): explicit partial derivatives of each entry */
+        double w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+        double dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+        double dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+        double dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+        double dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+        double gq[4] = {0, 0, 0, 0};
+        for (int i = 0; i < 9; ++i) {
+            gq[0] += gR[i] * dRw[i];
+            gq[1] += gR[i] * dRx[i];
+            gq[2] += gR[i] * dRy[i];
+            gq[3] += gR[i] * dRz[i];
+        }
+        /* q_hat = q / |q| */
+        double dot = gq[0] * qh[0] + gq[1] * qh[1] + gq[2] * qh[2] + gq[3] * qh[3];
+        for (int i = 0; i < 4; ++i) g_quats[4 * gi + i] += (gq[i] - qh[i] * dot) / qn;
+    }
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
