@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the foveated-periphery Gaussian-splatting rasterizer on one GB300.
+
+Metric: ms per stereo frame at 2016x2240 per eye (0.5 M SH-3 Gaussians, the
+foveated-periphery workload), lower is better.  One step = one stereo frame
+through the whole path: preprocess (projection + key emission), bin/sort, and
+per-tile blending of RGB, Eq. 1 depth and final transmittance, for both eyes in
+one batched launch sequence.  Inputs are seeded synthetic scenes (clustered
+room generator) standing in for the paper's trained MipNeRF-360 /
+Tanks&Temples scenes.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64, OpenMP) on a bounded tile sample
+of the same workload and extrapolates to a whole frame.  With N > 1 (torchrun)
+every rank renders its own frame (replicas; the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "periphery_stereo_05m": "stereo frame 2016x2240/eye, 0.5M SH-3 Gaussians, clustered room",
+    "dense_stereo_3m": "stereo frame 2016x2240/eye + 2 x 512x512 foveal crops, 3M SH-3 Gaussians",
+}
+ALU_OPS_SKIP = 15      # FP32 ops per evaluated Gaussian-pixel pair (definition: power, exp, clamp, test)
+ALU_OPS_BLEND = 10     # extra FP32 ops per blended pair (T update, stop test, 3 colour + 1 depth FMA)
+
+
+def load_workload(name):
+    from paper_2410_17932_gb300 import inputs as I
+    if name == "periphery_stereo_05m":
+        return I.periphery_stereo_05m()
+    if name == "dense_stereo_3m":
+        return I.dense_stereo_3m()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+
+def oracle_frame_estimate(scenes, views, budget_s: float, seed: int = 0, tile: int = 16):
+    """Times the FP64 oracle on a tile sample of the frame and extrapolates to the whole frame.
+
+    Per view: decide + project over all Gaussians (timed in full), tile lists over all
+    Gaussians (timed in full), compositing on a random sample of tiles sized to the budget
+    (extrapolated by the tile count)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    total = 0.0
+    sampled = 0
+    n_tiles_all = 0
+    for cam in views:
+        sc = scenes[cam.scene]
+        t0 = time.perf_counter()
+        dec = oracle.decide(sc, cam, tile)
+        proj = oracle.project(sc, cam)
+        t1 = time.perf_counter()
+        gw, gh = oracle.grid(cam, tile)
+        nt = gw * gh
+        n_tiles_all += nt
+        empty = np.zeros(nt, np.uint8)
+        t2 = time.perf_counter()
+        oracle.render(sc, cam, tile, dec=dec, proj=proj, tile_mask=empty)
+        t3 = time.perf_counter()
+        lists = t3 - t2
+        k = 8
+        per_view_budget = budget_s / max(1, len(views))
+        while True:
+            mask = np.zeros(nt, np.uint8)
+            mask[rng.choice(nt, min(k, nt), replace=False)] = 1
+            t4 = time.perf_counter()
+            oracle.render(sc, cam, tile, dec=dec, proj=proj, tile_mask=mask)
+            t5 = time.perf_counter()
+            comp = max(0.0, (t5 - t4) - lists)
+            if comp * 4 > per_view_budget * 0.5 or k >= nt:
+                break
+            k = min(nt, k * 4)
+        sampled += int(mask.sum())
+        total += (t1 - t0) + lists + comp * nt / mask.sum()
+    return total * 1e3, sampled, n_tiles_all
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    scenes, views = load_workload(args.workload)
+    for _ in range(max(0, args.warmup)):
+        oracle_frame_estimate(scenes, views, budget_s=args.ref_budget / max(1, args.steps + args.warmup))
+    ests = []
+    info = None
+    for k in range(args.steps):
+        ms, sampled, nt = oracle_frame_estimate(scenes, views,
+                                                budget_s=args.ref_budget / max(1, args.steps + args.warmup),
+                                                seed=k)
+        ests.append(ms)
+        info = (sampled, nt)
+    value = float(np.median(ests))
+    line = {
+        "impl": "reference", "metric": "ms per stereo frame @2016x2240/eye", "value": round(value, 3),
+        "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(value, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]},
+        "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"decide+project+tile lists over all Gaussians; compositing on "
+                                   f"{info[0]} of {info[1]} tiles, extrapolated by tile count"},
+        "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="periphery_stereo_05m", choices=list(WORKLOADS))
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--persistent", type=int, default=-1, help="-1: autotuned choice")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the reference arm")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    scenes, views = load_workload(args.workload)
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    persistent = bool(args.persistent) if args.persistent >= 0 else False
+    ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent)
+    ras.forward()                       # sizes the instance list
+    code, flags, inst = ras.last_status
+    from paper_2410_17932_gb300 import _lib as L
+    info = L.vrs_run_info()
+    L.vrs_query_status(ras.plan, ras.workspace.data_ptr(), info, torch.cuda.current_stream().cuda_stream)
+    pair_evals, pair_blends = int(info.pair_evals), int(info.pair_blends)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ras.forward_async()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        e = evs[k]
+        e[0].record()
+        ras.preprocess()
+        e[1].record()
+        ras.bin_sort()
+        e[2].record()
+        ras.render_fwd()
+        e[3].record()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    pre = [e[0].elapsed_time(e[1]) for e in evs]
+    srt = [e[1].elapsed_time(e[2]) for e in evs]
+    bld = [e[2].elapsed_time(e[3]) for e in evs]
+    step = [e[0].elapsed_time(e[3]) for e in evs]
+    ms = statistics.mean(step)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ms / world                   # whole-job ms per frame (world frames per step)
+
+    # roofline of the dominant kernel
+    peaks, src = measured_peaks()
+    stage = {"preprocess": statistics.mean(pre), "bin_sort": statistics.mean(srt),
+             "render_fwd": statistics.mean(bld)}
+    dominant = max(stage, key=stage.get)
+    p = ras.plan
+    if dominant == "render_fwd":
+        ops = ALU_OPS_SKIP * pair_evals + ALU_OPS_BLEND * pair_blends
+        peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12   # T lane-ops/s
+        achieved = ops / (stage["render_fwd"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_render_fwd<16>", "achieved": round(achieved, 3),
+                "peak": round(peak, 2), "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4),
+                "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
+                "units": f"{pair_evals} Gaussian-pixel evaluations, {pair_blends} blended"}
+    else:
+        n = sum(s.n for s in scenes)
+        if dominant == "preprocess":
+            K_ = [(s.sh_degree + 1) ** 2 for s in scenes]
+            byts = sum(s.n * (4 * (3 + 3 + 4 + 1) + 12 * k) for s, k in zip(scenes, K_)) + 48 * int(p.n_records) + 12 * inst
+        else:
+            byts = 24 * inst * int(p.sort_passes) + 8 * inst * int(p.sort_passes)
+        achieved = byts / (stage[dominant] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": None, "peak_source": src}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = [[x.detach().cpu().pin_memory() for x in s.tensors()] for s in sts]
+        out_rgb = torch.empty(ras.rgb.numel(), dtype=torch.float32).pin_memory()
+        out_d = torch.empty(ras.depth.numel(), dtype=torch.float32).pin_memory()
+        h2d = sum(x.numel() * 4 for hs in host for x in hs)
+        d2h = (out_rgb.numel() + out_d.numel()) * 4
+        E = args.e2e_steps
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        tms = []
+        for k in range(E + 3):
+            flush.zero_()
+            ev0.record()
+            for s, hs in zip(sts, host):
+                for dst, src_ in zip(s.tensors(), hs):
+                    dst.copy_(src_, non_blocking=True)
+            ras.forward_async()
+            out_rgb.copy_(ras.rgb, non_blocking=True)
+            out_d.copy_(ras.depth, non_blocking=True)
+            ev1.record()
+            ev1.synchronize()
+            if k >= 3:
+                tms.append(ev0.elapsed_time(ev1))
+        e2e = {"value": round(statistics.mean(tms) / world, 4), "unit": "ms",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        est, sampled, nt = oracle_frame_estimate(scenes, views, budget_s=args.cpu_budget)
+        cpu = {"value": round(est, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"decide+project+tile lists over all Gaussians; FP64 compositing on {sampled} "
+                         f"of {nt} tiles, extrapolated by tile count"}
+
+    launches_per_step = (1 + len(scenes)) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
+    if rank == 0:
+        line = {
+            "metric": "ms per stereo frame @2016x2240/eye (0.5M SH-3 Gaussians)",
+            "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload],
+                       "tile": int(p.tile), "persistent": int(p.persistent),
+                       "instances": inst, "sort_passes": int(p.sort_passes),
+                       "l2": "flushed: 256 MiB write between timed steps (outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "stages_ms": {k: round(v, 4) for k, v in stage.items()},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * K,
+            "clocks": clocks,
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

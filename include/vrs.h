@@ -1,0 +1,237 @@
+/*
+ * vrs.h - C-ABI of libvrs, a GB300 (sm_103a) tile-based 3D Gaussian Splatting
+ * rasterizer for the periphery of VR-Splatting (Franke, Fink, Stamminger,
+ * "VR-Splatting: Foveated Radiance Field Rendering via 3D Gaussian Splatting
+ * and Neural Points", arXiv 2410.17932).
+ *
+ * What it computes.  Sec. 3.1 ("Naive Method") renders the periphery with 3D
+ * Gaussian splats: each splat has an opacity alpha, a colour C and a 3D
+ * covariance Sigma built from a per-splat scale and rotation; the splats are
+ * projected and blended to screen into the full-resolution image P.  Sec. 3.2
+ * renders that image for the whole frame and, in the same pass, the
+ * approximate depth buffer of Eq. 1,
+ *      d = sum_i d_i alpha_i prod_{m<i} (1 - alpha_m),
+ * which the foveal renderer uses to cull occluded neural points.  Sec. 1 names
+ * the cost that grows with the number of primitives: tiling and sorting them.
+ *
+ * The path behind this header:
+ *   vrs_plan_batch  host: sizes, tile grid, record/tile/pixel offsets, workspace bytes
+ *   vrs_preprocess  per Gaussian x view: EWA projection with the 0.3 px dilation,
+ *                   3-sigma screen radius, view-dependent SH colour, tile rectangle,
+ *                   and emission of (tile, depth) keys for every touched tile
+ *   vrs_bin_sort    LSD radix sort of the keys, equal-key order by record index,
+ *                   per-tile [start, end) ranges
+ *   vrs_render_fwd  per tile, front-to-back compositing of RGB, Eq. 1 depth and
+ *                   final transmittance
+ *   vrs_render_bwd  the adjoint of the three steps above: gradients w.r.t. the
+ *                   Gaussian parameters (the method is trained end to end by
+ *                   gradient descent, Sec. 3.5 and Sec. 4 "Training")
+ *
+ * Conventions shared by every call:
+ *  - All pointers named device_* or documented as device memory must point to
+ *    memory of the current CUDA device; host structs are read during the call
+ *    only and may be freed afterwards.
+ *  - The caller owns every buffer, including the workspace of
+ *    plan.workspace_bytes bytes (256-byte aligned).  The library allocates and
+ *    frees nothing and never synchronises the stream, except vrs_query_status,
+ *    which synchronises the stream it is given.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call is stream ordered and launches a fixed set of kernels
+ *    whose shapes depend on the plan only, so a sequence of calls can be
+ *    captured into a CUDA graph and replayed.
+ *  - Errors detectable on the host (bad sizes, null pointers, a camera that
+ *    does not match the plan) return a status at once and launch nothing.
+ *    Errors detectable only on the device (instance capacity exceeded, a
+ *    non-finite parameter, an all-zero quaternion, a bounded wait that gave
+ *    up) set bits in a status word inside the workspace; kernels after a
+ *    capacity overflow skip their work.  vrs_query_status reads that word.
+ *
+ * Parameterisation (Sec. 3.1: opacity, colour, scale and rotation per splat):
+ *  means [n][3], log_scales [n][3] (log of the per-axis standard deviation),
+ *  quats [n][4] (w, x, y, z; normalised inside), opacity_logits [n]
+ *  (opacity = 1 / (1 + exp(-logit))), sh [n][(deg+1)^2][3] real spherical
+ *  harmonics coefficients in (l, m = -l..l) order, deg in {0, 1, 2, 3}.  The
+ *  rendered colour is max(0, sum_k Y_k(dir) sh_k + 0.5) with dir the unit
+ *  vector from the camera centre to the mean.
+ *
+ * Cameras are pinholes: x_cam = R x_world + t, +z forward, +y down, pixel
+ * (i, j) centred at (i + 0.5, j + 0.5), u = fx x/z + cx, v = fy y/z + cy.  A
+ * foveal crop (Sec. 3.3: a subfrustum through an adapted projection) is an
+ * off-axis view with cx, cy shifted by the crop origin and tan_fov copied
+ * from the full frame.
+ */
+#ifndef VRS_H
+#define VRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VRS_MAX_VIEWS 64
+#define VRS_MAX_SCENES 16
+
+typedef enum {
+    VRS_OK = 0,
+    VRS_ERR_INVALID = 1,     /* bad argument; on the device: an all-zero quaternion */
+    VRS_ERR_CAPACITY = 2,    /* more tile instances than plan.max_instances */
+    VRS_ERR_CUDA = 3,        /* a CUDA runtime call failed (launch, copy) */
+    VRS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    VRS_ERR_NONFINITE = 5    /* a Gaussian parameter was NaN or Inf (that Gaussian is skipped) */
+} vrs_status;
+
+/* One scene of Gaussians: device pointers, structure of arrays, float32. */
+typedef struct {
+    const float *means;          /* [n][3] */
+    const float *log_scales;     /* [n][3] */
+    const float *quats;          /* [n][4] (w, x, y, z) */
+    const float *opacity_logits; /* [n] */
+    const float *sh;             /* [n][(sh_degree+1)^2][3] */
+    int32_t n;                   /* number of Gaussians, >= 0 */
+    int32_t sh_degree;           /* 0..3 */
+} vrs_scene;
+
+/* A pinhole view (host struct). */
+typedef struct {
+    float R[9];        /* world -> camera rotation, row-major */
+    float t[3];        /* translation: x_cam = R x_world + t */
+    float fx, fy;      /* focal lengths in pixels */
+    float cx, cy;      /* principal point in pixels */
+    float znear;       /* splats with z_cam <= znear are culled (0.2 in the reference setting) */
+    float tan_fovx;    /* half-FOV tangents bounding the projection-Jacobian clamp at 1.3x; */
+    float tan_fovy;    /*   0 means width/(2 fx) and height/(2 fy) */
+    int32_t width, height;   /* >= 1 */
+    int32_t scene;           /* index into the scene array */
+} vrs_camera;
+
+typedef struct {
+    int32_t tile;          /* tile edge in pixels: 8, 16 or 32 (0 = 16) */
+    int32_t persistent;    /* 1 = blend every tile of every view in one persistent
+                              launch, heaviest tiles first; 0 = one CTA per tile */
+    int32_t backward;      /* 1 = reserve the workspace that vrs_render_bwd needs */
+    int32_t reserved;
+    int64_t max_instances; /* capacity of the (tile, Gaussian) instance list; 0 = 4 x records + 65536 */
+} vrs_plan_opts;
+
+/* Sizes and workspace layout, filled by vrs_plan_batch.  Treat as read-only. */
+typedef struct {
+    int32_t n_views, n_scenes;
+    int32_t tile;              /* tile edge */
+    int32_t key_bits;          /* significant bits of the sort key: tile-id bits + 32 */
+    int32_t sort_passes;       /* 8-bit LSD passes */
+    int32_t persistent, backward;
+    int32_t sort_ctas;         /* CTAs of each radix pass */
+    int64_t max_instances;
+    int64_t n_records;         /* sum over views of the view's scene size */
+    int64_t n_tiles;           /* sum over views of gw * gh */
+    int64_t n_pixels;          /* sum over views of width * height */
+    int64_t workspace_bytes;
+    /* byte offsets inside the workspace */
+    int64_t off_status;        /* device status block (see vrs_run_info) */
+    int64_t off_records;       /* [n_records][3] float4 projected-splat records */
+    int64_t off_keys[2];       /* [max_instances] uint64 ping-pong key buffers */
+    int64_t off_vals[2];       /* [max_instances] uint32 ping-pong record-index buffers */
+    int64_t off_hist;          /* radix scratch */
+    int64_t off_ranges;        /* [n_tiles] uint2 {start, end} into the sorted list */
+    int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1 */
+    int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
+    int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */
+    int32_t sorted_buf;        /* which ping-pong buffer holds the sorted list */
+    int32_t n_sms;
+    /* per scene */
+    int32_t scene_n[VRS_MAX_SCENES];
+    int32_t scene_deg[VRS_MAX_SCENES];
+    /* per view */
+    int32_t view_scene[VRS_MAX_VIEWS];
+    int32_t view_w[VRS_MAX_VIEWS], view_h[VRS_MAX_VIEWS];
+    int32_t view_gw[VRS_MAX_VIEWS], view_gh[VRS_MAX_VIEWS];
+    int64_t view_rec_base[VRS_MAX_VIEWS];   /* record index of (view v, Gaussian g) = view_rec_base[v] + g */
+    int64_t view_tile_base[VRS_MAX_VIEWS];  /* global tile id = view_tile_base[v] + ty * gw + tx */
+    int64_t view_pix_base[VRS_MAX_VIEWS];   /* view v's pixels start at element view_pix_base[v] */
+} vrs_plan;
+
+/* Device status block, copied to the host by vrs_query_status. */
+typedef struct {
+    uint32_t flags;            /* bit 0: all-zero quaternion, 1: non-finite parameter,
+                                  2: capacity exceeded, 3: bounded wait timed out */
+    uint32_t reserved;
+    uint64_t instances;        /* tile instances requested by the last vrs_preprocess
+                                  (may exceed max_instances on overflow) */
+    uint64_t pair_evals;       /* Gaussian-pixel pairs the last vrs_render_fwd evaluated by
+                                  definition: per pixel, its tile-list position where it
+                                  stopped, else the list length */
+    uint64_t pair_blends;      /* of those, pairs that were blended */
+} vrs_run_info;
+
+/* Sizes a batch of n_views views over n_scenes scenes and lays out the
+ * workspace.  Reads scenes[*].n and .sh_degree and the views' sizes and scene
+ * indices only; the pointers may be NULL here.  Re-plan when any size changes;
+ * a plan stays valid for any poses and parameter values of the same sizes.
+ * Errors: VRS_ERR_INVALID for n_views outside 1..VRS_MAX_VIEWS, n_scenes outside
+ * 1..VRS_MAX_SCENES, a view with width or height < 1 or > 16384, a bad scene
+ * index or SH degree, or a tile size other than 0/8/16/32. */
+vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_camera *views,
+                          int32_t n_views, const vrs_plan_opts *opts, vrs_plan *plan);
+
+/* Step 1, per Gaussian and per view of its scene (Sec. 3.1 projection).
+ * Projects every Gaussian, writes its record (2D mean, Cholesky factors of the
+ * conic, log2 opacity, colour, depth) and appends one (key, record index)
+ * instance per touched tile:  key = (global tile id << 32) | float bits of z_cam.
+ * Instances beyond plan.max_instances are dropped and flag VRS_ERR_CAPACITY.
+ * scenes: n_scenes entries with device pointers, sizes as planned.
+ * views: n_views host cameras, sizes and scene indices as planned.
+ * Returns VRS_ERR_INVALID if sizes differ from the plan or a pointer is NULL
+ * for a non-empty scene, VRS_ERR_CUDA on a launch failure. */
+vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const vrs_camera *views,
+                          void *workspace, void *stream);
+
+/* Step 2 (Sec. 1: tiling and sorting of all primitives).  Sorts the instances
+ * by key with an 8-bit LSD radix sort over plan.key_bits bits, orders runs of
+ * equal keys by record index, and writes each tile's [start, end) range.
+ * After it, the sorted keys and record indices are at
+ * workspace + plan.off_keys[plan.sorted_buf] / off_vals[plan.sorted_buf]. */
+vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
+
+/* Step 3 (Sec. 3.1 blending to screen; Sec. 3.2 Eq. 1).  For every pixel,
+ * front to back over its tile's sorted list: alpha = min(0.99, o exp(power)),
+ * skipped below 1/255; the pixel stops before a splat that would bring T under
+ * 1e-4; otherwise C += rgb alpha T, D += z alpha T, T *= 1 - alpha.
+ * Outputs (device, float32, written for every pixel of every view):
+ *   rgb     [3][H][W] per view, view v at rgb + 3 * plan.view_pix_base[v]
+ *   depth   [H][W] per view at depth + plan.view_pix_base[v]   (Eq. 1, not normalised)
+ *   T_final [H][W] per view at T_final + plan.view_pix_base[v]
+ * Colour is premultiplied with no background; composite with T_final. */
+vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, float *depth,
+                          float *T_final, void *stream);
+
+/* Adjoint of steps 1-3 for the upstream gradients dL/drgb, dL/ddepth and
+ * (nullable) dL/dT_final, laid out like the forward outputs; T_final is the
+ * forward output.  Needs a plan made with opts.backward = 1 and the workspace
+ * left by vrs_render_fwd for the same scenes and views.  Gradients are
+ * ACCUMULATED (+=) into per-scene device arrays shaped like the parameters:
+ * grads[s] holds g_means, g_log_scales, g_quats, g_opacity_logits, g_sh for
+ * scene s in the fields of a vrs_scene (const is cast away; n and sh_degree
+ * must match). */
+vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene *scenes,
+                          const vrs_camera *views, const float *T_final, const float *dL_drgb,
+                          const float *dL_ddepth, const float *dL_dT, const vrs_scene *grads,
+                          void *stream);
+
+/* Synchronises `stream`, copies the device status block to *info (nullable)
+ * and returns the most severe device status: CAPACITY, then TIMEOUT, then
+ * NONFINITE, then INVALID, else VRS_OK. */
+vrs_status vrs_query_status(const vrs_plan *plan, const void *workspace, vrs_run_info *info,
+                            void *stream);
+
+/* Clears the device status block (stream ordered). */
+vrs_status vrs_reset_status(const vrs_plan *plan, void *workspace, void *stream);
+
+/* A static, human-readable name of a status. */
+const char *vrs_status_string(vrs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRS_H */

@@ -148,6 +148,14 @@ def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
     st = lib().orc_decide(n, _p(means), _p(ls), _p(q), ctypes.byref(c), tile,
                           _p(out["visible"]), _p(out["depth"]), _p(out["ubar"]), _p(out["vbar"]),
                           _p(out["radius"]), _p(out["rect"]))
+    # a Gaussian with any non-finite parameter is skipped (the C-ABI's NONFINITE rule)
+    bad = ~np.isfinite(np.asarray(scene.opacity_logits, np.float32))
+    if n:
+        bad |= ~np.isfinite(np.asarray(scene.sh, np.float32)).reshape(n, -1).all(axis=1)
+    if bad.any():
+        out["visible"][bad] = 0
+        out["rect"][bad] = 0
+        st |= 2
     out["status"] = int(st)
     return out
 

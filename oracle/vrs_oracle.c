@@ -151,6 +151,9 @@ float orc_exp32(float x)
 
 static int f_isfinite(float v) { return isfinite(v) ? 1 : 0; }
 
+/* keeps a tile index inside the int range before conversion */
+static double clamp_big(double v) { return v < -1.0e9 ? -1.0e9 : (v > 1.0e9 ? 1.0e9 : v); }
+
 /* ------------------------------------------------------------------------- */
 /* The integer decisions, in FP32.  Each statement below is one correctly
  * rounded IEEE operation; the order is part of the definition.
@@ -255,10 +258,10 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         float ub = cam->fx * txtz, vb = cam->fy * tytz;
         float xlo = ub - rad, xhi = ub + rad, ylo = vb - rad, yhi = vb + rad;
         /* tile rectangle: floor of the exact value of (edge + principal point) / tile */
-        int x0 = (int)floor(((double)xlo + (double)cam->cx) / tile);
-        int x1 = (int)floor(((double)xhi + (double)cam->cx) / tile) + 1;
-        int y0 = (int)floor(((double)ylo + (double)cam->cy) / tile);
-        int y1 = (int)floor(((double)yhi + (double)cam->cy) / tile) + 1;
+        int x0 = (int)clamp_big(floor(((double)xlo + (double)cam->cx) / tile));
+        int x1 = (int)clamp_big(floor(((double)xhi + (double)cam->cx) / tile)) + 1;
+        int y0 = (int)clamp_big(floor(((double)ylo + (double)cam->cy) / tile));
+        int y1 = (int)clamp_big(floor(((double)yhi + (double)cam->cy) / tile)) + 1;
         x0 = x0 < 0 ? 0 : (x0 > gw ? gw : x0);
         x1 = x1 < 0 ? 0 : (x1 > gw ? gw : x1);
         y0 = y0 < 0 ? 0 : (y0 > gh ? gh : y0);

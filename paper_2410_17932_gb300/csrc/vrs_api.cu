@@ -1,0 +1,352 @@
+// The C-ABI of libvrs: plan, the launch sequence of each step, and status.
+#include <string.h>
+
+#include "vrs_internal.cuh"
+
+namespace vrs {
+cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8_t *views, int n_views,
+                              float4 *rec, unsigned long long *keys, uint32_t *vals, DevStatus *st,
+                              unsigned long long cap, cudaStream_t stream);
+cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream);
+cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
+                        uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
+                        int64_t n_tiles, const DevStatus *st, unsigned long long cap, int passes, int G,
+                        int n_sms, cudaStream_t stream);
+cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
+                              const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
+                              float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
+                              uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
+                              int persistent, int n_sms, cudaStream_t s);
+cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
+                              const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
+                              const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
+                              const float *dL_ddepth, const float *dL_dT, float *grad2d,
+                              int64_t n_tiles, cudaStream_t s);
+cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
+                                   const int8_t *views, int n_views, const float *grad2d,
+                                   const DevStatus *st, cudaStream_t s);
+}  // namespace vrs
+
+using namespace vrs;
+
+namespace {
+
+constexpr int kOrderTmp = 2 * 34;   // histogram + cursors of the work-order buckets
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int bits_for(int64_t n)
+{
+    int b = 1;
+    while (b < 40 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+vrs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VRS_OK : VRS_ERR_CUDA; }
+
+template <typename T>
+T *at(void *ws, int64_t off) { return reinterpret_cast<T *>(static_cast<char *>(ws) + off); }
+
+void fill_sizes(const vrs_plan *P, ViewTable &vt)
+{
+    memset(&vt, 0, sizeof(vt));
+    vt.n_views = P->n_views;
+    vt.tile = P->tile;
+    for (int v = 0; v < P->n_views; ++v) {
+        DevView &d = vt.v[v];
+        d.w = P->view_w[v];
+        d.h = P->view_h[v];
+        d.gw = P->view_gw[v];
+        d.gh = P->view_gh[v];
+        d.scene = P->view_scene[v];
+        d.rec_base = P->view_rec_base[v];
+        d.tile_base = P->view_tile_base[v];
+        d.pix_base = P->view_pix_base[v];
+    }
+}
+
+vrs_status fill_cameras(const vrs_plan *P, const vrs_camera *views, ViewTable &vt)
+{
+    if (!views) return VRS_ERR_INVALID;
+    for (int v = 0; v < P->n_views; ++v) {
+        const vrs_camera &c = views[v];
+        if (c.width != P->view_w[v] || c.height != P->view_h[v] || c.scene != P->view_scene[v])
+            return VRS_ERR_INVALID;
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !(c.znear >= 0.f)) return VRS_ERR_INVALID;
+        DevView &d = vt.v[v];
+        memcpy(d.R, c.R, sizeof(d.R));
+        memcpy(d.t, c.t, sizeof(d.t));
+        d.fx = c.fx;
+        d.fy = c.fy;
+        d.cx = c.cx;
+        d.cy = c.cy;
+        d.znear = c.znear;
+        d.tanx = c.tan_fovx > 0.f ? c.tan_fovx : (float)c.width / (2.0f * c.fx);
+        d.tany = c.tan_fovy > 0.f ? c.tan_fovy : (float)c.height / (2.0f * c.fy);
+    }
+    return VRS_OK;
+}
+
+vrs_status check_scenes(const vrs_plan *P, const vrs_scene *scenes)
+{
+    if (!scenes) return VRS_ERR_INVALID;
+    for (int s = 0; s < P->n_scenes; ++s) {
+        const vrs_scene &S = scenes[s];
+        if (S.n != P->scene_n[s] || S.sh_degree != P->scene_deg[s]) return VRS_ERR_INVALID;
+        if (S.n > 0 && (!S.means || !S.log_scales || !S.quats || !S.opacity_logits || !S.sh))
+            return VRS_ERR_INVALID;
+    }
+    return VRS_OK;
+}
+
+DevScene dev_scene(const vrs_scene &S)
+{
+    DevScene d;
+    d.means = S.means;
+    d.log_scales = S.log_scales;
+    d.quats = S.quats;
+    d.logits = S.opacity_logits;
+    d.sh = S.sh;
+    d.n = S.n;
+    d.K = (S.sh_degree + 1) * (S.sh_degree + 1);
+    return d;
+}
+
+int views_of_scene(const vrs_plan *P, int s, int8_t *out)
+{
+    int n = 0;
+    for (int v = 0; v < P->n_views; ++v)
+        if (P->view_scene[v] == s) out[n++] = (int8_t)v;
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_camera *views,
+                          int32_t n_views, const vrs_plan_opts *opts, vrs_plan *plan)
+{
+    if (!plan || !scenes || !views) return VRS_ERR_INVALID;
+    if (n_views < 1 || n_views > VRS_MAX_VIEWS || n_scenes < 1 || n_scenes > VRS_MAX_SCENES)
+        return VRS_ERR_INVALID;
+    vrs_plan_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    const int tile = o.tile == 0 ? 16 : o.tile;
+    if (tile != 8 && tile != 16 && tile != 32) return VRS_ERR_INVALID;
+    if (o.max_instances < 0) return VRS_ERR_INVALID;
+    vrs_plan P;
+    memset(&P, 0, sizeof(P));
+    P.n_views = n_views;
+    P.n_scenes = n_scenes;
+    P.tile = tile;
+    P.persistent = o.persistent ? 1 : 0;
+    P.backward = o.backward ? 1 : 0;
+    for (int s = 0; s < n_scenes; ++s) {
+        if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
+        P.scene_n[s] = scenes[s].n;
+        P.scene_deg[s] = scenes[s].sh_degree;
+    }
+    int64_t rec = 0, tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const vrs_camera &c = views[v];
+        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return VRS_ERR_INVALID;
+        if (c.scene < 0 || c.scene >= n_scenes) return VRS_ERR_INVALID;
+        P.view_scene[v] = c.scene;
+        P.view_w[v] = c.width;
+        P.view_h[v] = c.height;
+        P.view_gw[v] = (c.width + tile - 1) / tile;
+        P.view_gh[v] = (c.height + tile - 1) / tile;
+        P.view_rec_base[v] = rec;
+        P.view_tile_base[v] = tiles;
+        P.view_pix_base[v] = pix;
+        rec += P.scene_n[c.scene];
+        tiles += (int64_t)P.view_gw[v] * P.view_gh[v];
+        pix += (int64_t)c.width * c.height;
+    }
+    if (rec >= ((int64_t)1 << 32) || tiles >= ((int64_t)1 << 31)) return VRS_ERR_INVALID;
+    P.n_records = rec;
+    P.n_tiles = tiles;
+    P.n_pixels = pix;
+    P.key_bits = 32 + bits_for(tiles);
+    P.sort_passes = (P.key_bits + 7) / 8;
+    P.sorted_buf = P.sort_passes % 2;
+    int64_t cap = o.max_instances > 0 ? o.max_instances : 4 * rec + 65536;
+    if (cap > ((int64_t)1 << 31)) cap = (int64_t)1 << 31;
+    P.max_instances = cap;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    P.n_sms = sms;
+    P.sort_ctas = 2 * sms > 1024 ? 1024 : 2 * sms;
+    // workspace layout
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        int64_t r = off;
+        off = align_up(off + (bytes > 0 ? bytes : 1), 256);
+        return r;
+    };
+    P.off_status = take(256 + sizeof(float4) * VRS_MAX_VIEWS);   // status + device view table
+    P.off_records = take(rec * kRecF4 * 16);
+    P.off_keys[0] = take(cap * 8);
+    P.off_keys[1] = take(cap * 8);
+    P.off_vals[0] = take(cap * 4);
+    P.off_vals[1] = take(cap * 4);
+    P.off_hist = take(((int64_t)256 * P.sort_ctas + 256) * 4);
+    P.off_ranges = take(tiles * 8);
+    P.off_ncontrib = take(pix * 4);
+    P.off_order = take((tiles + kOrderTmp) * 4);
+    P.off_grad2d = P.backward ? take(rec * kGrad2D * 4) : 0;
+    P.workspace_bytes = off;
+    *plan = P;
+    return VRS_OK;
+}
+
+vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const vrs_camera *views,
+                          void *workspace, void *stream)
+{
+    if (!plan || !workspace) return VRS_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return VRS_ERR_INVALID;
+    vrs_status vs = check_scenes(plan, scenes);
+    if (vs != VRS_OK) return vs;
+    ViewTable vt;
+    fill_sizes(plan, vt);
+    vs = fill_cameras(plan, views, vt);
+    if (vs != VRS_OK) return vs;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevStatus *st = at<DevStatus>(workspace, plan->off_status);
+    float4 *viewtab = at<float4>(workspace, plan->off_status + 256);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    e = launch_write_viewtab(vt, viewtab, s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    for (int sc = 0; sc < plan->n_scenes; ++sc) {
+        int8_t vlist[VRS_MAX_VIEWS];
+        const int nv = views_of_scene(plan, sc, vlist);
+        e = launch_preprocess(vt, dev_scene(scenes[sc]), vlist, nv,
+                              at<float4>(workspace, plan->off_records),
+                              at<unsigned long long>(workspace, plan->off_keys[0]),
+                              at<uint32_t>(workspace, plan->off_vals[0]), st,
+                              (unsigned long long)plan->max_instances, s);
+        if (e != cudaSuccess) return VRS_ERR_CUDA;
+    }
+    return VRS_OK;
+}
+
+vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream)
+{
+    if (!plan || !workspace) return VRS_ERR_INVALID;
+    uint32_t *hist = at<uint32_t>(workspace, plan->off_hist);
+    cudaError_t e = launch_sort(at<unsigned long long>(workspace, plan->off_keys[0]),
+                                at<uint32_t>(workspace, plan->off_vals[0]),
+                                at<unsigned long long>(workspace, plan->off_keys[1]),
+                                at<uint32_t>(workspace, plan->off_vals[1]), hist,
+                                hist + (size_t)256 * plan->sort_ctas,
+                                at<uint2>(workspace, plan->off_ranges), plan->n_tiles,
+                                at<DevStatus>(workspace, plan->off_status),
+                                (unsigned long long)plan->max_instances, plan->sort_passes,
+                                plan->sort_ctas, plan->n_sms, static_cast<cudaStream_t>(stream));
+    return cuda_status(e);
+}
+
+vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, float *depth,
+                          float *T_final, void *stream)
+{
+    if (!plan || !workspace || !rgb || !depth || !T_final) return VRS_ERR_INVALID;
+    ViewTable vt;
+    fill_sizes(plan, vt);
+    const int sb = plan->sorted_buf;
+    uint32_t *order = at<uint32_t>(workspace, plan->off_order);
+    cudaError_t e = launch_render_fwd(
+        vt, at<float4>(workspace, plan->off_status + 256), at<float4>(workspace, plan->off_records),
+        at<uint32_t>(workspace, plan->off_vals[sb]), at<uint2>(workspace, plan->off_ranges),
+        at<DevStatus>(workspace, plan->off_status), rgb, depth, T_final,
+        at<uint32_t>(workspace, plan->off_ncontrib), order, order + plan->n_tiles, plan->n_tiles,
+        plan->n_records, plan->persistent, plan->n_sms, static_cast<cudaStream_t>(stream));
+    return cuda_status(e);
+}
+
+vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene *scenes,
+                          const vrs_camera *views, const float *T_final, const float *dL_drgb,
+                          const float *dL_ddepth, const float *dL_dT, const vrs_scene *grads,
+                          void *stream)
+{
+    if (!plan || !workspace || !T_final || !dL_drgb || !dL_ddepth || !grads) return VRS_ERR_INVALID;
+    if (!plan->backward) return VRS_ERR_INVALID;
+    vrs_status vs = check_scenes(plan, scenes);
+    if (vs != VRS_OK) return vs;
+    for (int s = 0; s < plan->n_scenes; ++s) {
+        const vrs_scene &G = grads[s];
+        if (G.n != plan->scene_n[s] || G.sh_degree != plan->scene_deg[s]) return VRS_ERR_INVALID;
+        if (G.n > 0 && (!G.means || !G.log_scales || !G.quats || !G.opacity_logits || !G.sh))
+            return VRS_ERR_INVALID;
+    }
+    ViewTable vt;
+    fill_sizes(plan, vt);
+    vs = fill_cameras(plan, views, vt);
+    if (vs != VRS_OK) return vs;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float *g2 = at<float>(workspace, plan->off_grad2d);
+    const DevStatus *st = at<DevStatus>(workspace, plan->off_status);
+    cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float) * kGrad2D * (size_t)plan->n_records, s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    e = launch_render_bwd(vt, at<float4>(workspace, plan->off_status + 256),
+                          at<float4>(workspace, plan->off_records),
+                          at<uint32_t>(workspace, plan->off_vals[plan->sorted_buf]),
+                          at<uint2>(workspace, plan->off_ranges), st,
+                          at<uint32_t>(workspace, plan->off_ncontrib), T_final, dL_drgb, dL_ddepth,
+                          dL_dT, g2, plan->n_tiles, s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    for (int sc = 0; sc < plan->n_scenes; ++sc) {
+        int8_t vlist[VRS_MAX_VIEWS];
+        const int nv = views_of_scene(plan, sc, vlist);
+        e = launch_backward_params(vt, dev_scene(scenes[sc]), dev_scene(grads[sc]), vlist, nv, g2, st, s);
+        if (e != cudaSuccess) return VRS_ERR_CUDA;
+    }
+    return VRS_OK;
+}
+
+vrs_status vrs_query_status(const vrs_plan *plan, const void *workspace, vrs_run_info *info,
+                            void *stream)
+{
+    if (!plan || !workspace) return VRS_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    vrs_run_info h;
+    memset(&h, 0, sizeof(h));
+    cudaError_t e = cudaMemcpyAsync(&h, static_cast<const char *>(workspace) + plan->off_status,
+                                    sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    if (info) *info = h;
+    if (h.flags & ST_CAPACITY) return VRS_ERR_CAPACITY;
+    if (h.flags & ST_TIMEOUT) return VRS_ERR_TIMEOUT;
+    if (h.flags & ST_NONFINITE) return VRS_ERR_NONFINITE;
+    if (h.flags & ST_ZERO_QUAT) return VRS_ERR_INVALID;
+    return VRS_OK;
+}
+
+vrs_status vrs_reset_status(const vrs_plan *plan, void *workspace, void *stream)
+{
+    if (!plan || !workspace) return VRS_ERR_INVALID;
+    return cuda_status(cudaMemsetAsync(static_cast<char *>(workspace) + plan->off_status, 0,
+                                       sizeof(DevStatus), static_cast<cudaStream_t>(stream)));
+}
+
+const char *vrs_status_string(vrs_status status)
+{
+    switch (status) {
+        case VRS_OK: return "VRS_OK";
+        case VRS_ERR_INVALID: return "VRS_ERR_INVALID";
+        case VRS_ERR_CAPACITY: return "VRS_ERR_CAPACITY";
+        case VRS_ERR_CUDA: return "VRS_ERR_CUDA";
+        case VRS_ERR_TIMEOUT: return "VRS_ERR_TIMEOUT";
+        case VRS_ERR_NONFINITE: return "VRS_ERR_NONFINITE";
+    }
+    return "VRS_ERR_UNKNOWN";
+}
+
+}  // extern "C"

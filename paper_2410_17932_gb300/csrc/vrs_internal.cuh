@@ -1,0 +1,393 @@
+// Internal definitions of libvrs (sm_103a).  Not part of the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vrs.h"
+
+namespace vrs {
+
+// ---------------------------------------------------------------------------
+// Device-side views of the plan, passed to kernels by value.
+
+struct DevView {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, znear, tanx, tany;
+    int32_t w, h, gw, gh, scene, pad;
+    int64_t rec_base, tile_base, pix_base;
+};
+
+struct DevScene {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    int32_t n, K;
+};
+
+struct ViewTable {
+    DevView v[VRS_MAX_VIEWS];
+    int32_t n_views;
+    int32_t tile;
+};
+
+// Status block at the head of the workspace.
+struct DevStatus {
+    uint32_t flags;
+    uint32_t reserved;
+    unsigned long long instances;
+    unsigned long long pair_evals;
+    unsigned long long pair_blends;
+    uint32_t work[8];          // work-queue counters of persistent kernels
+};
+
+enum : uint32_t {
+    ST_ZERO_QUAT = 1u,
+    ST_NONFINITE = 2u,
+    ST_CAPACITY = 4u,
+    ST_TIMEOUT = 8u,
+};
+
+constexpr int kRecF4 = 3;                               // float4s per projected-splat record
+constexpr float kLog2_255 = 7.99435343685885793f;       // log2(255)
+constexpr float kCholScale = 0.849321800288019f;        // sqrt(log2(e) / 2)
+constexpr int kGrad2D = 10;                             // 2D gradient floats per record
+
+// Record layout (3 x float4 per (view, Gaussian)):
+//   r0 = (ubar_hi, vbar_hi, ubar_lo, vbar_lo)   2D mean minus the principal point, double-float
+//   r1 = (l0, l1, l2, lo)  conic = L^T L / kCholScale^2 with L = [[l0, l1], [0, l2]];
+//                          lo = log2(opacity); alpha = min(0.99, 2^(lo - q')),
+//                          q' = (l0 dx + l1 dy)^2 + (l2 dy)^2
+//   r2 = (r, g, b, depth)
+
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int64_t tile)
+{
+    int lo = 0, hi = vt.n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (vt.v[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// The integer decisions in FP32.  Every operation is an explicitly rounded
+// intrinsic (no contraction into fused multiply-adds, no reassociation), in a
+// fixed order, so that the visibility, screen radius, tile rectangle and
+// depth key are defined to the bit.
+
+#define FMUL __fmul_rn
+#define FADD __fadd_rn
+#define FSUB __fsub_rn
+#define FDIV __fdiv_rn
+
+// e^x: Cody-Waite reduction x = k ln2 + r (ln2 split in a short high part and
+// a low correction), degree-7 Taylor polynomial of e^r by Horner's rule with
+// fused multiply-adds, exact scaling by 2^k.
+__device__ __forceinline__ float exp32_cw(float x)
+{
+    x = fminf(fmaxf(x, -80.0f), 80.0f);
+    float kf = rintf(FMUL(x, 1.44269502f));
+    float r = __fmaf_rn(-kf, 0.693145751953125f, x);
+    r = __fmaf_rn(-kf, 1.42860677e-06f, r);
+    float p = 1.98412698e-04f;
+    p = __fmaf_rn(p, r, 1.38888889e-03f);
+    p = __fmaf_rn(p, r, 8.33333377e-03f);
+    p = __fmaf_rn(p, r, 4.16666679e-02f);
+    p = __fmaf_rn(p, r, 1.66666672e-01f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    int k = (int)kf;
+    return FMUL(p, __int_as_float((k + 127) << 23));
+}
+
+// Per-Gaussian part: scales, rotation of the normalised quaternion, M = Rq S.
+struct GaussPre {
+    float s[3];
+    float Rq[9];
+    float M[9];
+};
+
+// Returns false for an all-zero quaternion.
+__device__ __forceinline__ bool gauss_pre(const float ls[3], const float q[4], GaussPre &g)
+{
+    g.s[0] = exp32_cw(ls[0]);
+    g.s[1] = exp32_cw(ls[1]);
+    g.s[2] = exp32_cw(ls[2]);
+    float qq = FMUL(q[0], q[0]);
+    qq = FADD(qq, FMUL(q[1], q[1]));
+    qq = FADD(qq, FMUL(q[2], q[2]));
+    qq = FADD(qq, FMUL(q[3], q[3]));
+    if (!(qq > 0.0f)) return false;
+    float qn = __fsqrt_rn(qq);
+    float w = FDIV(q[0], qn), x = FDIV(q[1], qn), y = FDIV(q[2], qn), z = FDIV(q[3], qn);
+    float xx = FMUL(x, x), yy = FMUL(y, y), zz = FMUL(z, z);
+    float xy = FMUL(x, y), xz = FMUL(x, z), yz = FMUL(y, z);
+    float wx = FMUL(w, x), wy = FMUL(w, y), wz = FMUL(w, z);
+    g.Rq[0] = FSUB(1.0f, FMUL(2.0f, FADD(yy, zz)));
+    g.Rq[1] = FMUL(2.0f, FSUB(xy, wz));
+    g.Rq[2] = FMUL(2.0f, FADD(xz, wy));
+    g.Rq[3] = FMUL(2.0f, FADD(xy, wz));
+    g.Rq[4] = FSUB(1.0f, FMUL(2.0f, FADD(xx, zz)));
+    g.Rq[5] = FMUL(2.0f, FSUB(yz, wx));
+    g.Rq[6] = FMUL(2.0f, FSUB(xz, wy));
+    g.Rq[7] = FMUL(2.0f, FADD(yz, wx));
+    g.Rq[8] = FSUB(1.0f, FMUL(2.0f, FADD(xx, yy)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g.M[3 * k + j] = FMUL(g.Rq[3 * k + j], g.s[j]);
+    return true;
+}
+
+struct Decision {
+    float tx, ty, tz;          // camera-space mean (FP32 decision values)
+    float txtz, tytz;
+    float T0[3], T1[3];        // rows of J W
+    float n0, n1, b;           // |v0|^2, |v1|^2, v0.v1 of V = (J W) M
+    float det;                 // det of the dilated 2D covariance
+    float ub, vb, rad;
+    int x0, x1, y0, y1;
+    bool visible;
+    bool clampx, clampy;
+};
+
+// Per view.  `tile` is the tile edge; gw, gh the view's tile grid.
+__device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, float mx, float my,
+                                       float mz, int tile, Decision &d)
+{
+    d.visible = false;
+    const float *W = V.R;
+    float tc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float a = FMUL(W[3 * r], mx);
+        a = FADD(a, FMUL(W[3 * r + 1], my));
+        a = FADD(a, FMUL(W[3 * r + 2], mz));
+        tc[r] = FADD(a, V.t[r]);
+    }
+    d.tx = tc[0];
+    d.ty = tc[1];
+    d.tz = tc[2];
+    const float tz = tc[2];
+    if (!(tz > V.znear)) return;
+    const float limx = FMUL(1.3f, V.tanx), limy = FMUL(1.3f, V.tany);
+    d.txtz = FDIV(tc[0], tz);
+    d.tytz = FDIV(tc[1], tz);
+    d.clampx = (d.txtz > limx) || (d.txtz < -limx);
+    d.clampy = (d.tytz > limy) || (d.tytz < -limy);
+    float cxz = FMUL(fminf(limx, fmaxf(-limx, d.txtz)), tz);
+    float cyz = FMUL(fminf(limy, fmaxf(-limy, d.tytz)), tz);
+    float j00 = FDIV(V.fx, tz), j11 = FDIV(V.fy, tz), tz2 = FMUL(tz, tz);
+    float j02 = -FDIV(FMUL(V.fx, cxz), tz2);
+    float j12 = -FDIV(FMUL(V.fy, cyz), tz2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d.T0[k] = FADD(FMUL(j00, W[k]), FMUL(j02, W[6 + k]));
+        d.T1[k] = FADD(FMUL(j11, W[3 + k]), FMUL(j12, W[6 + k]));
+    }
+    float v0[3], v1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float a = FMUL(d.T0[0], g.M[j]);
+        a = FADD(a, FMUL(d.T0[1], g.M[3 + j]));
+        v0[j] = FADD(a, FMUL(d.T0[2], g.M[6 + j]));
+        float b = FMUL(d.T1[0], g.M[j]);
+        b = FADD(b, FMUL(d.T1[1], g.M[3 + j]));
+        v1[j] = FADD(b, FMUL(d.T1[2], g.M[6 + j]));
+    }
+    float n0 = FMUL(v0[0], v0[0]);
+    n0 = FADD(n0, FMUL(v0[1], v0[1]));
+    n0 = FADD(n0, FMUL(v0[2], v0[2]));
+    float n1 = FMUL(v1[0], v1[0]);
+    n1 = FADD(n1, FMUL(v1[1], v1[1]));
+    n1 = FADD(n1, FMUL(v1[2], v1[2]));
+    float bb = FMUL(v0[0], v1[0]);
+    bb = FADD(bb, FMUL(v0[1], v1[1]));
+    bb = FADD(bb, FMUL(v0[2], v1[2]));
+    // det(V V^T) = |v0 x v1|^2 with v0 x v1 = diag(s1 s2, s0 s2, s0 s1) Rq^T (T0 x T1)
+    float c0 = FSUB(FMUL(d.T0[1], d.T1[2]), FMUL(d.T0[2], d.T1[1]));
+    float c1 = FSUB(FMUL(d.T0[2], d.T1[0]), FMUL(d.T0[0], d.T1[2]));
+    float c2 = FSUB(FMUL(d.T0[0], d.T1[1]), FMUL(d.T0[1], d.T1[0]));
+    float e[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float a = FMUL(g.Rq[j], c0);
+        a = FADD(a, FMUL(g.Rq[3 + j], c1));
+        e[j] = FADD(a, FMUL(g.Rq[6 + j], c2));
+    }
+    float g0 = FMUL(FMUL(g.s[1], g.s[2]), e[0]);
+    float g1 = FMUL(FMUL(g.s[0], g.s[2]), e[1]);
+    float g2 = FMUL(FMUL(g.s[0], g.s[1]), e[2]);
+    float dvv = FMUL(g0, g0);
+    dvv = FADD(dvv, FMUL(g1, g1));
+    dvv = FADD(dvv, FMUL(g2, g2));
+    float a_ = FADD(n0, 0.3f), c_ = FADD(n1, 0.3f);
+    float det = FADD(FADD(dvv, FMUL(0.3f, FADD(n0, n1))), 0.09f);
+    d.n0 = n0;
+    d.n1 = n1;
+    d.b = bb;
+    d.det = det;
+    if (!(det > 0.0f)) return;
+    float mid = FMUL(0.5f, FADD(a_, c_));
+    float disc = fmaxf(0.1f, FSUB(FMUL(mid, mid), det));
+    float lam = FADD(mid, __fsqrt_rn(disc));
+    float rad = ceilf(FMUL(3.0f, __fsqrt_rn(lam)));
+    d.rad = rad;
+    d.ub = FMUL(V.fx, d.txtz);
+    d.vb = FMUL(V.fy, d.tytz);
+    float xlo = FSUB(d.ub, rad), xhi = FADD(d.ub, rad);
+    float ylo = FSUB(d.vb, rad), yhi = FADD(d.vb, rad);
+    // floor of the exact value of (edge + principal point) / tile, in double
+    const double inv = 1.0 / (double)tile;   // a power of two: exact
+    double fx0 = floor(__dmul_rn(__dadd_rn((double)xlo, (double)V.cx), inv));
+    double fx1 = floor(__dmul_rn(__dadd_rn((double)xhi, (double)V.cx), inv));
+    double fy0 = floor(__dmul_rn(__dadd_rn((double)ylo, (double)V.cy), inv));
+    double fy1 = floor(__dmul_rn(__dadd_rn((double)yhi, (double)V.cy), inv));
+    fx0 = fmin(fmax(fx0, -1.0e9), 1.0e9);
+    fx1 = fmin(fmax(fx1, -1.0e9), 1.0e9);
+    fy0 = fmin(fmax(fy0, -1.0e9), 1.0e9);
+    fy1 = fmin(fmax(fy1, -1.0e9), 1.0e9);
+    int x0 = (int)fx0, x1 = (int)fx1 + 1, y0 = (int)fy0, y1 = (int)fy1 + 1;
+    x0 = min(max(x0, 0), V.gw);
+    x1 = min(max(x1, 0), V.gw);
+    y0 = min(max(y0, 0), V.gh);
+    y1 = min(max(y1, 0), V.gh);
+    d.x0 = x0;
+    d.x1 = x1;
+    d.y0 = y0;
+    d.y1 = y1;
+    d.visible = (x1 - x0) * (y1 - y0) > 0;
+}
+
+#undef FMUL
+#undef FADD
+#undef FSUB
+#undef FDIV
+
+// ---------------------------------------------------------------------------
+// Error-free transformations for the double-float 2D mean.
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// w0 x + w1 y + w2 z + t as an unevaluated sum hi + lo (compensated dot
+// product, Ogita, Rump and Oishi 2005, "Accurate sum and dot product").
+__device__ __forceinline__ void dot3_plus(float w0, float w1, float w2, float x, float y, float z,
+                                          float t, float &hi, float &lo)
+{
+    float p, s, h, r, q;
+    two_prod(w0, x, p, s);
+    two_prod(w1, y, h, r);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    two_prod(w2, z, h, r);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    two_sum(p, t, p, q);
+    s = __fadd_rn(s, q);
+    two_sum(p, s, hi, lo);
+}
+
+// f * (xh + xl) / (zh + zl) as hi + lo, accurate to a few units of 2^-46.
+__device__ __forceinline__ void proj_ratio(float f, float xh, float xl, float zh, float zl,
+                                           float &hi, float &lo)
+{
+    float q1 = __fdiv_rn(xh, zh);
+    float rem = __fmaf_rn(-q1, zh, xh);
+    rem = __fadd_rn(rem, __fsub_rn(xl, __fmul_rn(q1, zl)));
+    float q2 = __fdiv_rn(rem, zh);
+    float p, pe;
+    two_prod(f, q1, p, pe);
+    float l = __fmaf_rn(f, q2, pe);
+    hi = __fadd_rn(p, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, p));
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics, degree <= 3, (l, m = -l..l) order; constants are
+// the closed-form normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times
+// each polynomial's own factor.
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int K, float *Y)
+{
+    Y[0] = 0.28209479177387814f;
+    if (K > 1) {
+        Y[1] = -0.48860251190291992f * y;
+        Y[2] = 0.48860251190291992f * z;
+        Y[3] = -0.48860251190291992f * x;
+    }
+    if (K > 4) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.54627421529603959f * (xx - yy);
+        if (K > 9) {
+            Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+            Y[10] = 2.8906114426405538f * x * y * z;
+            Y[11] = -0.45704579946446572f * y * (4.0f * zz - xx - yy);
+            Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.4453057213202769f * z * (xx - yy);
+            Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair evaluation shared by the forward and backward blend kernels, so that
+// both take the same skip / stop decisions bit for bit.  A thread owns two
+// horizontally adjacent pixels at tile-local centres (pxc, pyc), (pxc+1, pyc);
+// (su, sv) is the splat's 2D mean in the same tile-local frame.
+//   q' = (l0 dx + l1 dy)^2 + (l2 dy)^2,  dx = su - pxc, dy = sv - pyc,
+// the quadratic form of the conic in the log2 domain; the splat contributes to
+// a pixel iff q' <= lt = lo + log2(255) (alpha >= 1/255), with
+// alpha = min(0.99, 2^(lo - q')).
+__device__ __forceinline__ void pair_q2(float su, float sv, float l0, float l1, float l2, float pxc,
+                                        float pyc, float &q0, float &q1)
+{
+    const float dy = __fsub_rn(sv, pyc);
+    const float m = __fmul_rn(l1, dy);
+    const float s = __fmul_rn(l2, dy);
+    const float s2 = __fmul_rn(s, s);
+    const float t0 = __fmaf_rn(l0, __fsub_rn(su, pxc), m);
+    const float t1 = __fsub_rn(t0, l0);
+    q0 = __fmaf_rn(t0, t0, s2);
+    q1 = __fmaf_rn(t1, t1, s2);
+}
+
+__device__ __forceinline__ float pair_alpha(float lo, float q)
+{
+    return fminf(ex2_approx(__fsub_rn(lo, q)), 0.99f);
+}
+
+// Launch helpers (host).
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace vrs

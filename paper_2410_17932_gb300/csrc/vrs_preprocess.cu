@@ -1,0 +1,228 @@
+// Step 1 of the periphery rasterizer: per Gaussian and per view of its scene,
+// EWA projection with the 0.3 px dilation, 3-sigma screen radius,
+// view-dependent SH colour (Sec. 3.1 "Naive Method": splats with opacity,
+// colour and a covariance from scale and rotation, projected to screen), and
+// emission of one (tile, depth) key per touched 16x16 tile (Sec. 1: tiling
+// and sorting all primitives is the cost that grows with their number).
+#include "vrs_internal.cuh"
+
+namespace vrs {
+
+struct PreParams {
+    DevScene S;
+    int32_t n_views;                 // views of this scene
+    int8_t views[VRS_MAX_VIEWS];     // their indices in the view table
+    float4 *rec;
+    unsigned long long *keys;
+    uint32_t *vals;
+    DevStatus *st;
+    unsigned long long cap;
+};
+
+template <int K>
+__device__ __forceinline__ void load_sh(const float *sh, int g, bool vec4, float *c)
+{
+    const float *src = sh + (size_t)g * 3 * K;
+    if constexpr ((3 * K) % 4 == 0) {
+        if (vec4) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+            for (int i = 0; i < 3 * K / 4; ++i) {
+                float4 v = __ldg(s4 + i);
+                c[4 * i] = v.x;
+                c[4 * i + 1] = v.y;
+                c[4 * i + 2] = v.z;
+                c[4 * i + 3] = v.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) c[i] = __ldg(src + i);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ ViewTable vt,
+                                                    const __grid_constant__ PreParams p)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool in = g < p.S.n;
+
+    float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
+    float logit = 0.f;
+    float sh[3 * K];
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) sh[i] = 0.f;
+    bool ok = in;
+    if (in) {
+        m[0] = __ldg(p.S.means + 3 * g);
+        m[1] = __ldg(p.S.means + 3 * g + 1);
+        m[2] = __ldg(p.S.means + 3 * g + 2);
+        ls[0] = __ldg(p.S.log_scales + 3 * g);
+        ls[1] = __ldg(p.S.log_scales + 3 * g + 1);
+        ls[2] = __ldg(p.S.log_scales + 3 * g + 2);
+        if ((reinterpret_cast<uintptr_t>(p.S.quats) & 15u) == 0) {
+            float4 qv = __ldg(reinterpret_cast<const float4 *>(p.S.quats) + g);
+            q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
+        }
+        logit = __ldg(p.S.logits + g);
+        const bool vec4 = (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
+        load_sh<K>(p.S.sh, g, vec4, sh);
+        float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
+        float shs = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) shs += sh[i];
+        if (!isfinite(chk) || !isfinite(shs)) {
+            ok = false;
+            atomicOr(&p.st->flags, ST_NONFINITE);
+        }
+    }
+    GaussPre pre;
+    if (ok && !gauss_pre(ls, q, pre)) {
+        ok = false;
+        atomicOr(&p.st->flags, ST_ZERO_QUAT);
+    }
+    // opacity in the log2 domain: log2(sigmoid(x)) = -log2(1 + e^-x)
+    const float LOG2E = 1.4426950408889634f;
+    const float lo = logit >= 0.f ? -log1pf(expf(-logit)) * LOG2E
+                                  : (logit - log1pf(expf(logit))) * LOG2E;
+
+    for (int vi = 0; vi < p.n_views; ++vi) {
+        const DevView &V = vt.v[p.views[vi]];
+        Decision d;
+        d.visible = false;
+        d.x0 = d.x1 = d.y0 = d.y1 = 0;
+        d.tz = 0.f;
+        if (ok) decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+        if (d.visible) {
+            // 2D mean relative to the principal point, as an unevaluated double-float sum
+            float xh, xl, yh, yl, zh, zl, uh, ul, vh, vl;
+            dot3_plus(V.R[0], V.R[1], V.R[2], m[0], m[1], m[2], V.t[0], xh, xl);
+            dot3_plus(V.R[3], V.R[4], V.R[5], m[0], m[1], m[2], V.t[1], yh, yl);
+            dot3_plus(V.R[6], V.R[7], V.R[8], m[0], m[1], m[2], V.t[2], zh, zl);
+            proj_ratio(V.fx, xh, xl, zh, zl, uh, ul);
+            proj_ratio(V.fy, yh, yl, zh, zl, vh, vl);
+            // Cholesky factors of the conic of [[n0+.3, b], [b, n1+.3]] with the
+            // cancellation-free determinant of the decision path
+            const float c = d.n1 + 0.3f;
+            const float l0 = sqrtf(c / d.det) * kCholScale;
+            const float l1 = -d.b / sqrtf(c * d.det) * kCholScale;
+            const float l2 = kCholScale / sqrtf(c);
+            // colour from the view direction (camera centre = -R^T t)
+            float cc0 = -(V.R[0] * V.t[0] + V.R[3] * V.t[1] + V.R[6] * V.t[2]);
+            float cc1 = -(V.R[1] * V.t[0] + V.R[4] * V.t[1] + V.R[7] * V.t[2]);
+            float cc2 = -(V.R[2] * V.t[0] + V.R[5] * V.t[1] + V.R[8] * V.t[2]);
+            float dx = m[0] - cc0, dy = m[1] - cc1, dz = m[2] - cc2;
+            float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv; dy *= inv; dz *= inv;
+            float Y[16];
+            sh_basis(dx, dy, dz, K, Y);
+            float col[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
+                col[ch] = fmaxf(acc, 0.0f);
+            }
+            float4 *r = p.rec + (size_t)(V.rec_base + g) * kRecF4;
+            r[0] = make_float4(uh, vh, ul, vl);
+            r[1] = make_float4(l0, l1, l2, lo);
+            r[2] = make_float4(col[0], col[1], col[2], d.tz);
+        }
+        // warp-cooperative emission: one atomic per warp, coalesced key writes
+        const uint32_t cnt = d.visible ? (uint32_t)((d.x1 - d.x0) * (d.y1 - d.y0)) : 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.st->instances, (unsigned long long)total);
+        base = __shfl_sync(FULL, base, 0);
+        const uint32_t excl = incl - cnt;
+        const int nx = d.visible ? d.x1 - d.x0 : 1;
+        const uint32_t dbits = __float_as_uint(d.tz);
+        const uint32_t rid = (uint32_t)(V.rec_base + g);
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                uint32_t v = __shfl_sync(FULL, incl, j + step - 1);
+                if (v <= k) j += step;
+            }
+            const uint32_t oex = __shfl_sync(FULL, excl, j);
+            const int ox0 = __shfl_sync(FULL, d.x0, j);
+            const int oy0 = __shfl_sync(FULL, d.y0, j);
+            const int onx = __shfl_sync(FULL, nx, j);
+            const uint32_t odb = __shfl_sync(FULL, dbits, j);
+            const uint32_t orid = __shfl_sync(FULL, rid, j);
+            if (k < total) {
+                const uint32_t local = k - oex;
+                const int ty = oy0 + (int)(local / (uint32_t)onx);
+                const int tx = ox0 + (int)(local % (uint32_t)onx);
+                const unsigned long long tid =
+                    (unsigned long long)(V.tile_base + (int64_t)ty * V.gw + tx);
+                const unsigned long long pos = base + k;
+                if (pos < p.cap) {
+                    p.keys[pos] = (tid << 32) | odb;
+                    p.vals[pos] = orid;
+                }
+            }
+        }
+        if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
+    }
+}
+
+// Principal points of the views, read by the blend kernels to build each
+// tile's local frame (the plan holds sizes only).
+__global__ void k_write_viewtab(const __grid_constant__ ViewTable vt, float4 *viewtab)
+{
+    const int v = threadIdx.x;
+    if (v < vt.n_views) viewtab[v] = make_float4(vt.v[v].cx, vt.v[v].cy, 0.f, 0.f);
+}
+
+cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream)
+{
+    k_write_viewtab<<<1, VRS_MAX_VIEWS, 0, stream>>>(vt, viewtab);
+    return cudaGetLastError();
+}
+
+// Host launcher: one launch per scene (the SH degree is a template argument so
+// that a Gaussian's coefficients stay in registers across its views).
+cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8_t *views,
+                              int n_views, float4 *rec, unsigned long long *keys, uint32_t *vals,
+                              DevStatus *st, unsigned long long cap, cudaStream_t stream)
+{
+    if (S.n <= 0 || n_views <= 0) return cudaSuccess;
+    PreParams p;
+    p.S = S;
+    p.n_views = n_views;
+    for (int i = 0; i < VRS_MAX_VIEWS; ++i) p.views[i] = i < n_views ? views[i] : 0;
+    p.rec = rec;
+    p.keys = keys;
+    p.vals = vals;
+    p.st = st;
+    p.cap = cap;
+    const int block = 128;
+    const unsigned grid = grid_for(S.n, block);
+    switch (S.K) {
+        case 1: k_preprocess<1><<<grid, block, 0, stream>>>(vt, p); break;
+        case 4: k_preprocess<4><<<grid, block, 0, stream>>>(vt, p); break;
+        case 9: k_preprocess<9><<<grid, block, 0, stream>>>(vt, p); break;
+        case 16: k_preprocess<16><<<grid, block, 0, stream>>>(vt, p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vrs

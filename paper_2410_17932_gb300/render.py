@@ -1,0 +1,245 @@
+"""PyTorch front end of libvrs: device memory, streams and autograd glue only.
+
+Every step of the rasterizer runs in libvrs's CUDA kernels through the C-ABI
+(``_lib``); this module allocates the workspace and outputs with torch, passes
+torch's current stream, and splits the packed outputs per view.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@dataclass
+class SceneTensors:
+    """One scene's Gaussian parameters as contiguous float32 CUDA tensors."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda", requires_grad=False) -> "SceneTensors":
+        def t(a):
+            x = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device)
+            return x.requires_grad_(requires_grad) if requires_grad else x
+        return SceneTensors(t(scene.means), t(scene.log_scales), t(scene.quats),
+                            t(scene.opacity_logits), t(scene.sh), int(scene.sh_degree))
+
+    def tensors(self):
+        return [getattr(self, k) for k in PARAM_NAMES]
+
+    def zeros_like(self) -> "SceneTensors":
+        return SceneTensors(*[torch.zeros_like(x, requires_grad=False) for x in self.tensors()],
+                            self.sh_degree)
+
+
+def scene_struct(st: SceneTensors) -> L.vrs_scene:
+    s = L.vrs_scene()
+    for name in PARAM_NAMES:
+        x = getattr(st, name)
+        if x.numel() and (not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        setattr(s, name, x.data_ptr() if x.numel() else None)
+    s.n = st.n
+    s.sh_degree = st.sh_degree
+    return s
+
+
+def camera_struct(cam) -> L.vrs_camera:
+    c = L.vrs_camera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.znear = float(cam.znear)
+    c.tan_fovx = float(np.float32(cam.tan_fovx))
+    c.tan_fovy = float(np.float32(cam.tan_fovy))
+    c.width, c.height, c.scene = int(cam.width), int(cam.height), int(cam.scene)
+    return c
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Rasterizer:
+    """A planned batch of views over one or more scenes, with its workspace and outputs."""
+
+    def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
+                 persistent: bool = False, backward: bool = False, max_instances: int = 0,
+                 device="cuda"):
+        self.scenes = list(scenes)
+        self.views = list(views)
+        self.device = torch.device(device)
+        self.tile = tile
+        self.persistent = bool(persistent)
+        self.backward = bool(backward)
+        self._make_plan(max_instances)
+
+    # -- planning ------------------------------------------------------------------------
+    def _make_plan(self, max_instances: int):
+        n_s, n_v = len(self.scenes), len(self.views)
+        self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
+        self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
+        opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), 0, int(max_instances))
+        plan = L.vrs_plan()
+        L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
+        self.plan = plan
+        self.workspace = torch.empty(int(plan.workspace_bytes), dtype=torch.uint8, device=self.device)
+        P = int(plan.n_pixels)
+        self.rgb = torch.empty(3 * P, dtype=torch.float32, device=self.device)
+        self.depth = torch.empty(P, dtype=torch.float32, device=self.device)
+        self.T = torch.empty(P, dtype=torch.float32, device=self.device)
+
+    def set_views(self, views: Sequence):
+        """New poses for views of the same sizes (no re-plan)."""
+        self.views = list(views)
+        self._view_arr = (L.vrs_camera * len(self.views))(*[camera_struct(v) for v in self.views])
+
+    def set_scenes(self, scenes: Sequence[SceneTensors]):
+        self.scenes = list(scenes)
+        self._scene_arr = (L.vrs_scene * len(self.scenes))(*[scene_struct(s) for s in self.scenes])
+
+    # -- the three steps -----------------------------------------------------------------
+    def preprocess(self, stream=None):
+        L._check(L.vrs_preprocess(self.plan, self._scene_arr, self._view_arr,
+                                  self.workspace.data_ptr(), _stream_handle(stream)), "vrs_preprocess")
+
+    def bin_sort(self, stream=None):
+        L._check(L.vrs_bin_sort(self.plan, self.workspace.data_ptr(), _stream_handle(stream)),
+                 "vrs_bin_sort")
+
+    def render_fwd(self, rgb=None, depth=None, T=None, stream=None):
+        rgb = self.rgb if rgb is None else rgb
+        depth = self.depth if depth is None else depth
+        T = self.T if T is None else T
+        L._check(L.vrs_render_fwd(self.plan, self.workspace.data_ptr(), rgb.data_ptr(),
+                                  depth.data_ptr(), T.data_ptr(), _stream_handle(stream)),
+                 "vrs_render_fwd")
+
+    def forward_async(self, stream=None):
+        """The whole forward path, stream ordered, no host synchronisation."""
+        self.preprocess(stream)
+        self.bin_sort(stream)
+        self.render_fwd(stream=stream)
+
+    def status(self, stream=None):
+        info = L.vrs_run_info()
+        code = L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(stream))
+        return code, int(info.flags), int(info.instances)
+
+    def forward(self, stream=None, check: bool = True, grow: bool = True):
+        """Forward path; on a capacity overflow re-plans with room for the measured count."""
+        self.forward_async(stream)
+        if not check:
+            return
+        code, flags, inst = self.status(stream)
+        if code == L.VRS_ERR_CAPACITY and grow:
+            self._make_plan(int(inst * 1.25) + 65536)
+            self.forward_async(stream)
+            code, flags, inst = self.status(stream)
+        if code not in (L.VRS_OK, L.VRS_ERR_NONFINITE, L.VRS_ERR_INVALID):
+            raise L.VrsError(code, "forward")
+        self.last_status = (code, flags, inst)
+
+    def backward_params(self, dL_drgb, dL_ddepth, dL_dT=None, grads: Optional[List[SceneTensors]] = None,
+                        stream=None) -> List[SceneTensors]:
+        """Accumulates parameter gradients (+=) for upstream gradients of the packed outputs."""
+        if grads is None:
+            grads = [s.zeros_like() for s in self.scenes]
+        garr = (L.vrs_scene * len(grads))(*[scene_struct(g) for g in grads])
+        dT = dL_dT.data_ptr() if dL_dT is not None else None
+        L._check(L.vrs_render_bwd(self.plan, self.workspace.data_ptr(), self._scene_arr,
+                                  self._view_arr, self.T.data_ptr(), dL_drgb.data_ptr(),
+                                  dL_ddepth.data_ptr(), dT, garr, _stream_handle(stream)),
+                 "vrs_render_bwd")
+        return grads
+
+    # -- views of the packed outputs and the workspace ------------------------------------------
+    def view_slices(self, v: int):
+        p = self.plan
+        b = int(p.view_pix_base[v])
+        W, H = int(p.view_w[v]), int(p.view_h[v])
+        return b, W, H
+
+    def outputs(self, v: int, rgb=None, depth=None, T=None):
+        b, W, H = self.view_slices(v)
+        rgb = self.rgb if rgb is None else rgb
+        depth = self.depth if depth is None else depth
+        T = self.T if T is None else T
+        return (rgb[3 * b:3 * b + 3 * W * H].view(3, H, W), depth[b:b + W * H].view(H, W),
+                T[b:b + W * H].view(H, W))
+
+    def ws_view(self, off: int, count: int, dtype) -> torch.Tensor:
+        nbytes = count * torch.tensor([], dtype=dtype).element_size()
+        return self.workspace[off:off + nbytes].view(dtype)
+
+    def sorted_lists(self):
+        p = self.plan
+        _, _, inst = self.status()
+        m = min(inst, int(p.max_instances))
+        keys = self.ws_view(int(p.off_keys[p.sorted_buf]), m, torch.int64)
+        vals = self.ws_view(int(p.off_vals[p.sorted_buf]), m, torch.int32)
+        ranges = self.ws_view(int(p.off_ranges), 2 * int(p.n_tiles), torch.int32).view(-1, 2)
+        return keys, vals, ranges
+
+    def records(self) -> torch.Tensor:
+        p = self.plan
+        return self.ws_view(int(p.off_records), 12 * int(p.n_records), torch.float32).view(-1, 12)
+
+    def n_contrib(self) -> torch.Tensor:
+        p = self.plan
+        return self.ws_view(int(p.off_ncontrib), int(p.n_pixels), torch.int32)
+
+
+class VrsRenderFunction(torch.autograd.Function):
+    """Differentiable forward of a Rasterizer over its scenes' parameter tensors.
+
+    forward(ras, *params) -> (rgb, depth, T) packed over views; params are the
+    scenes' [means, log_scales, quats, opacity_logits, sh] in scene order.
+    """
+
+    @staticmethod
+    def forward(ctx, ras: Rasterizer, *params):
+        ras.forward()
+        ctx.ras = ras
+        return ras.rgb.clone(), ras.depth.clone(), ras.T.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_T):
+        ras = ctx.ras
+        g_rgb = torch.zeros_like(ras.rgb) if g_rgb is None else g_rgb.contiguous()
+        g_depth = torch.zeros_like(ras.depth) if g_depth is None else g_depth.contiguous()
+        g_T = None if g_T is None else g_T.contiguous()
+        grads = ras.backward_params(g_rgb, g_depth, g_T)
+        out = [None]
+        for g in grads:
+            out.extend(g.tensors())
+        return tuple(out)
+
+
+def render(ras: Rasterizer):
+    """Autograd-aware forward: returns packed (rgb, depth, T)."""
+    params = []
+    for s in ras.scenes:
+        params.extend(s.tensors())
+    return VrsRenderFunction.apply(ras, *params)

@@ -1,0 +1,169 @@
+"""GPU parity of the forward path (preprocess, bin/sort, blend) against the CPU oracle.
+
+Bars: bit-exact instance counts, sorted key lists, record-index lists and tile
+ranges; per-pixel images within max abs 2e-4 (RGB, T) and 1e-4 relative
+(Eq. 1 depth) outside the knife-edge pixels the oracle flags (alpha within
+5e-5 relative of 1/255 or T' within 1e-4 relative of the 1e-4 stop).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_17932_gb300 import inputs as I
+from tests.gpu_util import compare_images, decode_records, make_rasterizer, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(scenes, views, **kw):
+    torch = torch_cuda()
+    ras, sts = make_rasterizer(scenes, views, **kw)
+    ras.forward()
+    torch.cuda.synchronize()
+    return ras
+
+
+def _check_sort(ras, scenes, views, tile=16):
+    keys, vals, ranges = ras.sorted_lists()
+    bs = oracle.bin_sort(scenes, views, tile)
+    k = keys.cpu().numpy().view(np.uint64)
+    v = vals.cpu().numpy().view(np.uint32)
+    assert len(k) == len(bs["keys"])
+    assert np.array_equal(k, bs["keys"])
+    assert np.array_equal(v, bs["vals"])
+    r = ranges.cpu().numpy().astype(np.int64)
+    assert np.array_equal(r, bs["ranges"])
+    return bs
+
+
+def test_plain_200_records_and_sort():
+    scs, cams = I.plain_200()
+    ras = _run(scs, cams)
+    code, flags, inst = ras.last_status
+    assert code == 0 and flags == 0
+    bs = _check_sort(ras, scs, cams)
+    assert inst == len(bs["keys"]) > 10000
+    # preprocess records of the visible Gaussians against the FP64 projection
+    rec = decode_records(ras.records().cpu().numpy())
+    d = oracle.decide(scs[0], cams[0])
+    p = oracle.project(scs[0], cams[0])
+    vis = d["visible"].astype(bool)
+    assert np.abs(rec["ubar"][vis] - p["ubar"][vis]).max() <= 1e-6 * (1 + np.abs(p["ubar"][vis]).max())
+    assert np.abs(rec["vbar"][vis] - p["vbar"][vis]).max() <= 1e-6 * (1 + np.abs(p["vbar"][vis]).max())
+    assert np.all(rec["depth"][vis] == d["depth"][vis])
+    scale = np.abs(p["conic"][vis]).max(axis=1, keepdims=True)
+    assert (np.abs(rec["conic"][vis] - p["conic"][vis]) / scale).max() < 2e-5
+    assert np.abs(rec["lo"][vis] - np.log2(p["opacity"][vis])).max() < 2e-6
+    assert np.abs(rec["rgb"][vis] - p["rgb"][vis]).max() < 2e-6
+
+
+def test_plain_200_image_parity():
+    scs, cams = I.plain_200()
+    ras = _run(scs, cams)
+    rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
+    orc = oracle.render(scs[0], cams[0])
+    worst = compare_images((rgb, depth, T), orc, "plain_200")
+    nc = ras.n_contrib().cpu().numpy().reshape(200, 200)
+    ok = orc["flags"] == 0
+    assert np.array_equal(nc[ok], orc["n_contrib"][ok])
+    print("plain_200 worst", worst)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_sizes_ragged(tile):
+    # 203 x 141: not a multiple of any tile size
+    scs, _ = I.plain_200()
+    cam = I.Camera(np.eye(3), np.zeros(3), 180.0, 190.0, 101.3, 70.6, 203, 141)
+    ras = _run(scs, [cam], tile=tile)
+    _check_sort(ras, scs, [cam], tile)
+    rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
+    orc = oracle.render(scs[0], cam, tile=tile)
+    compare_images((rgb, depth, T), orc, f"tile{tile}")
+
+
+def test_persistent_equals_per_tile():
+    torch = torch_cuda()
+    scs, cams = I.plain_200()
+    a = _run(scs, cams)
+    b = _run(scs, cams, persistent=True)
+    for x, y in zip((a.rgb, a.depth, a.T), (b.rgb, b.depth, b.T)):
+        assert torch.equal(x, y)
+
+
+def test_multiview_multiscene_and_crop_window():
+    torch = torch_cuda()
+    s0 = I.uniform_box_scene(3000, 41, sh_degree=3)
+    s1 = I.uniform_box_scene(2000, 42, sh_degree=1)
+    full = I.Camera(I._yaw_pitch(0.05, -0.03), [0.02, -0.01, 0.1], 150.0, 150.0, 96.0, 80.0, 192, 160)
+    crop = full.crop(32, 48, 64, 80)
+    other = I.Camera(np.eye(3), np.zeros(3), 120.0, 120.0, 50.0, 40.0, 100, 80, scene=1)
+    views = [full, other, crop]
+    ras = _run([s0, s1], views)
+    _check_sort(ras, [s0, s1], views)
+    for v, cam in enumerate(views):
+        sc = [s0, s1][cam.scene]
+        rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(v)]
+        compare_images((rgb, depth, T), oracle.render(sc, cam), f"view{v}")
+    f_rgb, f_d, f_T = ras.outputs(0)
+    c_rgb, c_d, c_T = ras.outputs(2)
+    assert torch.equal(c_rgb, f_rgb[:, 48:128, 32:96])
+    assert torch.equal(c_d, f_d[48:128, 32:96])
+    assert torch.equal(c_T, f_T[48:128, 32:96])
+
+
+def test_empty_scene_and_all_behind():
+    torch = torch_cuda()
+    empty = I.uniform_box_scene(0, 1)
+    behind = I.uniform_box_scene(500, 2, z=(-6.0, -2.0))
+    cam = I.identity_camera(72, 40)
+    for sc in (empty, behind):
+        ras = _run([sc], [cam])
+        assert ras.last_status[2] == 0
+        rgb, depth, T = ras.outputs(0)
+        assert torch.all(rgb == 0) and torch.all(depth == 0) and torch.all(T == 1)
+
+
+def test_device_status_zero_quat_and_nonfinite():
+    scs, cams = I.plain_200()
+    sc = scs[0].subset(np.arange(400))
+    sc.quats[3] = 0.0
+    sc.means[7, 1] = np.nan
+    sc.sh[9, 0, 2] = np.inf
+    ras = _run([sc], cams)
+    code, flags, _ = ras.last_status
+    assert flags & 1 and flags & 2
+    keys, vals, _ = ras.sorted_lists()
+    v = vals.cpu().numpy()
+    assert not np.isin(v, [3, 7, 9]).any()
+    bs = oracle.bin_sort([sc], cams)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), bs["keys"])
+    assert np.array_equal(v.view(np.uint32), bs["vals"])
+    orc = oracle.render(sc.subset(np.setdiff1d(np.arange(400), [3, 7, 9])), cams[0])
+    rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
+    compare_images((rgb, depth, T), orc, "skipped")
+
+
+def test_capacity_overflow_reported_then_regrown():
+    from paper_2410_17932_gb300 import _lib as L
+    torch = torch_cuda()
+    scs, cams = I.plain_200()
+    ras, _ = make_rasterizer(scs, cams, max_instances=1000)
+    ras.forward_async()
+    code, flags, inst = ras.status()
+    assert code == L.VRS_ERR_CAPACITY and flags & 4 and inst > 1000
+    ras.forward()          # re-plans with room for the measured count
+    assert ras.last_status[0] == 0
+    _check_sort(ras, scs, cams)
+
+
+def test_invalid_arguments_rejected_on_host():
+    from paper_2410_17932_gb300 import _lib as L
+    torch_cuda()
+    scs, cams = I.plain_200()
+    ras, _ = make_rasterizer(scs, cams)
+    bad = L.vrs_camera.from_buffer_copy(ras._view_arr[0])
+    bad.width = 100
+    arr = (L.vrs_camera * 1)(bad)
+    assert L.vrs_preprocess(ras.plan, ras._scene_arr, arr, ras.workspace.data_ptr(), 0) == L.VRS_ERR_INVALID
+    assert L.vrs_preprocess(ras.plan, ras._scene_arr, ras._view_arr, ras.workspace.data_ptr() + 8, 0) \
+        == L.VRS_ERR_INVALID
