@@ -133,7 +133,7 @@ typedef struct {
     int64_t off_keys[2];       /* [max_instances] uint64 ping-pong key buffers */
     int64_t off_vals[2];       /* [max_instances] uint32 ping-pong record-index buffers */
     int64_t off_hist;          /* radix scratch */
-    int64_t off_ranges;        /* [n_tiles] uint2 {start, end} into the sorted list */
+    int64_t off_ranges;        /* [n_tiles] uint2 {start, end} into the sorted list; {0, 0} if empty */
     int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1 */
     int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
     int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */

@@ -296,5 +296,6 @@ def bin_sort(scenes: Sequence, views: Sequence, tile: int = 16, decs: Optional[L
         ids = np.arange(n_tiles)
         ranges[:, 0] = np.searchsorted(tiles_of, ids, side="left")
         ranges[:, 1] = np.searchsorted(tiles_of, ids, side="right")
+        ranges[ranges[:, 0] == ranges[:, 1]] = 0      # an empty tile's range is {0, 0}
     return dict(keys=keys, vals=vals, ranges=ranges, counts=counts, rec_base=rec_base,
                 tile_base=tile_base)

@@ -21,7 +21,7 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
                               const float *dL_ddepth, const float *dL_dT, float *grad2d,
-                              int64_t n_tiles, cudaStream_t s);
+                              int64_t n_tiles, int64_t n_records, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d,
                                    const DevStatus *st, cudaStream_t s);
@@ -299,7 +299,7 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
                           at<uint32_t>(workspace, plan->off_vals[plan->sorted_buf]),
                           at<uint2>(workspace, plan->off_ranges), st,
                           at<uint32_t>(workspace, plan->off_ncontrib), T_final, dL_drgb, dL_ddepth,
-                          dL_dT, g2, plan->n_tiles, s);
+                          dL_dT, g2, plan->n_tiles, plan->n_records, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];

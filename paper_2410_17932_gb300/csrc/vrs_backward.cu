@@ -1,20 +1,464 @@
-// Adjoint of the rasterizer (placeholder until the reverse kernels land).
+// Adjoint of the rasterizer.  The method is trained end to end by gradient
+// descent with torch as the automatic-gradient framework over hand-written
+// renderers (Sec. 3.5, Sec. 4 "Training"); this file is that renderer's
+// reverse pass.
+//
+// k_render_bwd: per tile, the reverse of the forward blend.  Each pixel starts
+// from its final transmittance and walks its tile list backwards from the last
+// blended splat, recovering T_i = T_{i+1} / (1 - alpha_i), with running suffix
+// sums S_C = sum_{j>i} rgb_j w_j and S_D = sum_{j>i} d_j w_j (w_j = alpha_j T_j):
+//   dL/dalpha_i = T_i (g_C . rgb_i + g_D d_i) - (g_C . S_C + g_D S_D + g_T T_final) / (1 - alpha_i).
+// The staging, culling and alpha of every pair are the forward's, bit for bit
+// (shared device functions), so the same pairs are blended.  Per splat, the 10
+// gradients of the warp's 64 pixels are summed with shuffles and added to the
+// splat's record gradient with one atomic per value.
+//
+// k_backward_params: per Gaussian, the chain rule from the record gradients of
+// each view to means, log-scales, quaternion, opacity logit and SH coefficients,
+// accumulated into the caller's arrays.
 #include "vrs_internal.cuh"
 
 namespace vrs {
 
-cudaError_t launch_render_bwd(const ViewTable &, const float4 *, const float4 *, const uint32_t *,
-                              const uint2 *, const DevStatus *, const uint32_t *, const float *,
-                              const float *, const float *, const float *, float *, int64_t,
-                              cudaStream_t)
+struct BwdArgs {
+    const float4 *viewtab;
+    const float4 *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    const DevStatus *st;
+    const uint32_t *ncontrib;
+    const float *Tf;
+    const float *g_rgb;
+    const float *g_depth;
+    const float *g_T;        // nullable
+    float *grad2d;
+    int64_t n_records;
+};
+
+constexpr float kInvChol2 = 1.0f / (kCholScale * kCholScale);   // 2 / log2(e)
+
+struct PixState {
+    float T, SC0, SC1, SC2, SD, gC0, gC1, gC2, gD, gT, Tfin;
+    uint32_t last;
+};
+
+// One pixel's contribution to the 10 record gradients of a blended splat.
+__device__ __forceinline__ void pixel_adjoint(PixState &p, float q, float dx, float dy, const float4 A,
+                                              const float4 B, const float4 C, float *g)
 {
-    return cudaErrorNotSupported;
+    const float e = ex2_approx(__fsub_rn(B.y, q));
+    const float al = fminf(e, 0.99f);
+    const float om = 1.0f - al;
+    const float Tb = p.T / om;
+    const float w = al * Tb;
+    g[6] += p.gC0 * w;
+    g[7] += p.gC1 * w;
+    g[8] += p.gC2 * w;
+    g[9] += p.gD * w;
+    const float dLda = Tb * (p.gC0 * C.x + p.gC1 * C.y + p.gC2 * C.z + p.gD * B.w) -
+                       (p.gC0 * p.SC0 + p.gC1 * p.SC1 + p.gC2 * p.SC2 + p.gD * p.SD + p.gT * p.Tfin) / om;
+    p.SC0 = fmaf(C.x, w, p.SC0);
+    p.SC1 = fmaf(C.y, w, p.SC1);
+    p.SC2 = fmaf(C.z, w, p.SC2);
+    p.SD = fmaf(B.w, w, p.SD);
+    p.T = Tb;
+    if (e < 0.99f) {
+        const float dLdp = dLda * al;              // d alpha / d power = alpha (natural units)
+        g[5] += dLda * ex2_approx(-q);             // d alpha / d opacity = 2^-q'
+        const float l0 = A.z, l1 = A.w, l2 = B.x;
+        const float t = l0 * dx + l1 * dy;
+        g[0] -= dLdp * (l0 * t) * kInvChol2;                    // -(a dx + b dy)
+        g[1] -= dLdp * (l1 * t + l2 * l2 * dy) * kInvChol2;     // -(c dy + b dx)
+        g[2] -= dLdp * 0.5f * dx * dx;
+        g[3] -= dLdp * dx * dy;
+        g[4] -= dLdp * 0.5f * dy * dy;
+    }
 }
 
-cudaError_t launch_backward_params(const ViewTable &, const DevScene &, const DevScene &,
-                                   const int8_t *, int, const float *, const DevStatus *, cudaStream_t)
+template <int TS>
+__global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
+    k_render_bwd(const __grid_constant__ ViewTable vt, const BwdArgs a)
 {
-    return cudaErrorNotSupported;
+    using Cfg = BlendCfg<TS>;
+    __shared__ float4 sA[Cfg::BATCH], sB[Cfg::BATCH], sC[Cfg::BATCH];
+    __shared__ uint32_t smask[Cfg::BATCH], srid[Cfg::BATCH];
+    __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
+    __shared__ uint32_t s_max;
+
+    if (a.st->flags & ST_CAPACITY) return;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int px_l = (w % Cfg::WGX) * 8 + 2 * (lane & 3);
+    const int py_l = (w / Cfg::WGX) * 8 + (lane >> 2);
+    const float pxc = (float)px_l + 0.5f, pyc = (float)py_l + 0.5f;
+    const uint32_t lmask = lanemask_lt();
+
+    const int64_t t = blockIdx.x;
+    const int vi = view_of_tile(vt, t);
+    const DevView &V = vt.v[vi];
+    const float4 pp = a.viewtab[vi];
+    const int64_t lt_ = t - V.tile_base;
+    const int tx = (int)(lt_ % V.gw), ty = (int)(lt_ / V.gw);
+    const int px = tx * TS + px_l, py = ty * TS + py_l;
+    const bool in0 = px < V.w && py < V.h, in1 = px + 1 < V.w && py < V.h;
+    float oxh, oxl, oyh, oyl;
+    tile_origin((float)(tx * TS), pp.x, oxh, oxl);
+    tile_origin((float)(ty * TS), pp.y, oyh, oyl);
+    const uint2 range = a.ranges[t];
+
+    const int64_t HW = (int64_t)V.w * V.h;
+    const int64_t lp = (int64_t)py * V.w + px;
+    const int64_t pix = V.pix_base + lp;
+    const float *grgb = a.g_rgb + 3 * V.pix_base;
+    PixState P0, P1;
+    P0.SC0 = P0.SC1 = P0.SC2 = P0.SD = 0.f;
+    P1.SC0 = P1.SC1 = P1.SC2 = P1.SD = 0.f;
+    P0.last = P1.last = 0;
+    P0.T = P1.T = P0.Tfin = P1.Tfin = 1.f;
+    P0.gC0 = P0.gC1 = P0.gC2 = P0.gD = P0.gT = 0.f;
+    P1.gC0 = P1.gC1 = P1.gC2 = P1.gD = P1.gT = 0.f;
+    if (in0) {
+        P0.last = a.ncontrib[pix];
+        P0.T = P0.Tfin = a.Tf[pix];
+        P0.gC0 = grgb[lp];
+        P0.gC1 = grgb[HW + lp];
+        P0.gC2 = grgb[2 * HW + lp];
+        P0.gD = a.g_depth[pix];
+        P0.gT = a.g_T ? a.g_T[pix] : 0.f;
+    }
+    if (in1) {
+        P1.last = a.ncontrib[pix + 1];
+        P1.T = P1.Tfin = a.Tf[pix + 1];
+        P1.gC0 = grgb[lp + 1];
+        P1.gC1 = grgb[HW + lp + 1];
+        P1.gC2 = grgb[2 * HW + lp + 1];
+        P1.gD = a.g_depth[pix + 1];
+        P1.gT = a.g_T ? a.g_T[pix + 1] : 0.f;
+    }
+    if (tid == 0) s_max = 0u;
+    __syncthreads();
+    const uint32_t wm = __reduce_max_sync(FULL, max(P0.last, P1.last));
+    if (lane == 0) atomicMax(&s_max, wm);
+    __syncthreads();
+    const uint32_t maxlast = s_max;
+    const int nb = (int)((maxlast + Cfg::BATCH - 1) / Cfg::BATCH);
+
+    for (int bi = nb - 1; bi >= 0; --bi) {
+        const uint32_t bs = range.x + (uint32_t)bi * Cfg::BATCH;
+        const uint32_t j = bs + tid;
+        const uint32_t rid = (j < range.x + maxlast) ? __ldg(a.vals + j) : 0xffffffffu;
+        if ((int64_t)rid < a.n_records) {
+            float4 A, B, C;
+            smask[tid] = stage_instance<TS>(a.rec, rid, oxh, oxl, oyh, oyl, A, B, C);
+            sA[tid] = A;
+            sB[tid] = B;
+            sC[tid] = C;
+        } else {
+            smask[tid] = 0u;
+        }
+        srid[tid] = rid;
+        __syncthreads();
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < Cfg::BATCH / 32; ++c) {
+            const uint32_t bit = (smask[c * 32 + lane] >> w) & 1u;
+            const uint32_t bal = __ballot_sync(FULL, bit);
+            if (bit) slist[w][cnt + __popc(bal & lmask)] = (uint16_t)(c * 32 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int k = cnt - 1; k >= 0; --k) {
+            const int jj = slist[w][k];
+            const uint32_t pos = (uint32_t)bi * Cfg::BATCH + jj + 1;
+            const float4 A = sA[jj];
+            const float4 B = sB[jj];
+            float q0, q1;
+            pair_q2(A.x, A.y, A.z, A.w, B.x, pxc, pyc, q0, q1);
+            const bool c0 = pos <= P0.last && q0 <= B.z;
+            const bool c1 = pos <= P1.last && q1 <= B.z;
+            if (!__any_sync(FULL, c0 || c1)) continue;
+            const float4 C = sC[jj];
+            float g[kGrad2D];
+#pragma unroll
+            for (int i = 0; i < kGrad2D; ++i) g[i] = 0.f;
+            const float dx = A.x - pxc, dy = A.y - pyc;
+            if (c0) pixel_adjoint(P0, q0, dx, dy, A, B, C, g);
+            if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, A, B, C, g);
+#pragma unroll
+            for (int i = 0; i < kGrad2D; ++i) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) g[i] += __shfl_xor_sync(FULL, g[i], o);
+            }
+            if (lane < kGrad2D) {
+                float v = g[0];
+#pragma unroll
+                for (int i = 1; i < kGrad2D; ++i) v = lane == i ? g[i] : v;
+                atomicAdd(a.grad2d + (size_t)srid[jj] * kGrad2D + lane, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int TS>
+static cudaError_t launch_bwd_ts(const ViewTable &vt, const BwdArgs &a, int64_t n_tiles, cudaStream_t s)
+{
+    k_render_bwd<TS><<<(unsigned)n_tiles, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
+                              const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
+                              const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
+                              const float *dL_ddepth, const float *dL_dT, float *grad2d,
+                              int64_t n_tiles, int64_t n_records, cudaStream_t s)
+{
+    BwdArgs a{viewtab, rec, vals, ranges, st, ncontrib, Tf, dL_drgb, dL_ddepth, dL_dT, grad2d, n_records};
+    if (n_tiles <= 0) return cudaSuccess;
+    switch (vt.tile) {
+        case 8: return launch_bwd_ts<8>(vt, a, n_tiles, s);
+        case 16: return launch_bwd_ts<16>(vt, a, n_tiles, s);
+        case 32: return launch_bwd_ts<32>(vt, a, n_tiles, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-Gaussian chain rule.
+
+// Partial derivatives of the 16 SH basis polynomials w.r.t. x, y, z.
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int K, float *gx, float *gy,
+                                              float *gz)
+{
+    const float C1 = 0.48860251190291992f;
+    const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.54627421529603959f;
+    const float C3a = 0.59004358992664352f, C3b = 2.8906114426405538f, C3c = 0.45704579946446572f;
+    const float C3d = 0.3731763325901154f, C3e = 1.4453057213202769f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gx[k] = gy[k] = gz[k] = 0.f;
+    if (K > 1) {
+        gy[1] = -C1;
+        gz[2] = C1;
+        gx[3] = -C1;
+    }
+    if (K > 4) {
+        gx[4] = C2a * y;            gy[4] = C2a * x;
+        gy[5] = -C2a * z;           gz[5] = -C2a * y;
+        gx[6] = -2.f * C2b * x;     gy[6] = -2.f * C2b * y;     gz[6] = 4.f * C2b * z;
+        gx[7] = -C2a * z;           gz[7] = -C2a * x;
+        gx[8] = 2.f * C2c * x;      gy[8] = -2.f * C2c * y;
+    }
+    if (K > 9) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        gx[9] = -C3a * 6.f * x * y;                   gy[9] = -C3a * (3.f * xx - 3.f * yy);
+        gx[10] = C3b * y * z;  gy[10] = C3b * x * z;  gz[10] = C3b * x * y;
+        gx[11] = C3c * 2.f * x * y;
+        gy[11] = -C3c * (4.f * zz - xx - 3.f * yy);
+        gz[11] = -C3c * 8.f * y * z;
+        gx[12] = -C3d * 6.f * x * z;                  gy[12] = -C3d * 6.f * y * z;
+        gz[12] = C3d * (6.f * zz - 3.f * xx - 3.f * yy);
+        gx[13] = -C3c * (4.f * zz - 3.f * xx - yy);
+        gy[13] = C3c * 2.f * x * y;
+        gz[13] = -C3c * 8.f * x * z;
+        gx[14] = C3e * 2.f * x * z;  gy[14] = -C3e * 2.f * y * z;  gz[14] = C3e * (xx - yy);
+        gx[15] = -C3a * (3.f * xx - 3.f * yy);        gy[15] = C3a * 6.f * x * y;
+    }
+}
+
+struct ParamArgs {
+    DevScene S;            // parameters
+    DevScene G;            // gradient arrays (written through a cast)
+    int32_t n_views;
+    int8_t views[VRS_MAX_VIEWS];
+    const float *grad2d;
+    const DevStatus *st;
+};
+
+template <int K>
+__global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__ ViewTable vt,
+                                                         const __grid_constant__ ParamArgs p)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.S.n) return;
+    if (p.st->flags & ST_CAPACITY) return;
+    const float m[3] = {p.S.means[3 * g], p.S.means[3 * g + 1], p.S.means[3 * g + 2]};
+    const float ls[3] = {p.S.log_scales[3 * g], p.S.log_scales[3 * g + 1], p.S.log_scales[3 * g + 2]};
+    const float q[4] = {p.S.quats[4 * g], p.S.quats[4 * g + 1], p.S.quats[4 * g + 2], p.S.quats[4 * g + 3]};
+    const float logit = p.S.logits[g];
+    const float *shg = p.S.sh + (size_t)g * 3 * K;
+    GaussPre pre;
+    if (!gauss_pre(ls, q, pre)) return;
+    float sh[3 * K];
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) sh[i] = shg[i];
+    float gsh[3 * K];
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) gsh[i] = 0.f;
+    float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gqh[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
+    const float o = 1.0f / (1.0f + expf(-logit));
+    bool any = false;
+
+    for (int vi = 0; vi < p.n_views; ++vi) {
+        const DevView &V = vt.v[p.views[vi]];
+        const float *G2 = p.grad2d + (size_t)(V.rec_base + g) * kGrad2D;
+        float G[kGrad2D];
+        bool nz = false;
+#pragma unroll
+        for (int i = 0; i < kGrad2D; ++i) {
+            G[i] = G2[i];
+            nz |= G[i] != 0.f;
+        }
+        if (!nz) continue;
+        Decision d;
+        decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+        if (!d.visible) continue;
+        any = true;
+        // opacity
+        glogit += G[5] * o * (1.0f - o);
+        // colour through the SH basis and the view direction
+        const float cc0 = -(V.R[0] * V.t[0] + V.R[3] * V.t[1] + V.R[6] * V.t[2]);
+        const float cc1 = -(V.R[1] * V.t[0] + V.R[4] * V.t[1] + V.R[7] * V.t[2]);
+        const float cc2 = -(V.R[2] * V.t[0] + V.R[5] * V.t[1] + V.R[8] * V.t[2]);
+        const float v0_ = m[0] - cc0, v1_ = m[1] - cc1, v2_ = m[2] - cc2;
+        const float vn = sqrtf(v0_ * v0_ + v1_ * v1_ + v2_ * v2_);
+        const float dx = v0_ / vn, dy = v1_ / vn, dz = v2_ / vn;
+        float Y[16], Yx[16], Yy[16], Yz[16];
+        sh_basis(dx, dy, dz, K, Y);
+        sh_basis_grad(dx, dy, dz, K, Yx, Yy, Yz);
+        float gd0 = 0.f, gd1 = 0.f, gd2 = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
+            if (acc < 0.f) continue;                 // max(0, .) clamped this channel
+            const float gc = G[6 + ch];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gsh[3 * k + ch] += gc * Y[k];
+                gd0 += gc * sh[3 * k + ch] * Yx[k];
+                gd1 += gc * sh[3 * k + ch] * Yy[k];
+                gd2 += gc * sh[3 * k + ch] * Yz[k];
+            }
+        }
+        const float dd = dx * gd0 + dy * gd1 + dz * gd2;
+        gm[0] += (gd0 - dx * dd) / vn;
+        gm[1] += (gd1 - dy * dd) / vn;
+        gm[2] += (gd2 - dz * dd) / vn;
+        // projection of the mean and the depth
+        const float tx = d.tx, ty = d.ty, tz = d.tz;
+        const float iz = 1.0f / tz, iz2 = iz * iz;
+        float dtx = G[0] * V.fx * iz;
+        float dty = G[1] * V.fy * iz;
+        float dtz = G[9] - (G[0] * V.fx * tx + G[1] * V.fy * ty) * iz2;
+        // conic = adj(Sigma') / det with Sigma' = [[A, B], [B, C]] = V V^T + 0.3 I
+        const float A = d.n0 + 0.3f, Bc = d.b, C = d.n1 + 0.3f, det = d.det;
+        const float idet2 = 1.0f / (det * det);
+        const float gA = (-C * C * G[2] + Bc * C * G[3] - Bc * Bc * G[4]) * idet2;
+        const float gB = (2.f * Bc * C * G[2] - (A * C + Bc * Bc) * G[3] + 2.f * A * Bc * G[4]) * idet2;
+        const float gC = (-Bc * Bc * G[2] + A * Bc * G[3] - A * A * G[4]) * idet2;
+        // A = v0.v0 + .3, B = v0.v1, C = v1.v1 + .3 with V = T M
+        float gV0[3], gV1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gV0[j] = 2.f * gA * d.v0[j] + gB * d.v1[j];
+            gV1[j] = gB * d.v0[j] + 2.f * gC * d.v1[j];
+        }
+        float gT0[3], gT1[3], gM[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gT0[k] = gV0[0] * pre.M[3 * k] + gV0[1] * pre.M[3 * k + 1] + gV0[2] * pre.M[3 * k + 2];
+            gT1[k] = gV1[0] * pre.M[3 * k] + gV1[1] * pre.M[3 * k + 1] + gV1[2] * pre.M[3 * k + 2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gM[3 * k + j] = d.T0[k] * gV0[j] + d.T1[k] * gV1[j];
+        }
+        // T0 = J00 W0 + J02 W2, T1 = J11 W1 + J12 W2
+        const float *W = V.R;
+        const float gJ00 = gT0[0] * W[0] + gT0[1] * W[1] + gT0[2] * W[2];
+        const float gJ02 = gT0[0] * W[6] + gT0[1] * W[7] + gT0[2] * W[8];
+        const float gJ11 = gT1[0] * W[3] + gT1[1] * W[4] + gT1[2] * W[5];
+        const float gJ12 = gT1[0] * W[6] + gT1[1] * W[7] + gT1[2] * W[8];
+        dtz -= (gJ00 * V.fx + gJ11 * V.fy) * iz2;
+        if (!d.clampx) {
+            dtx -= gJ02 * V.fx * iz2;
+            dtz += gJ02 * 2.f * V.fx * tx * iz2 * iz;
+        } else {
+            const float L = fminf(1.3f * V.tanx, fmaxf(-1.3f * V.tanx, d.txtz));
+            dtz += gJ02 * V.fx * L * iz2;
+        }
+        if (!d.clampy) {
+            dty -= gJ12 * V.fy * iz2;
+            dtz += gJ12 * 2.f * V.fy * ty * iz2 * iz;
+        } else {
+            const float L = fminf(1.3f * V.tany, fmaxf(-1.3f * V.tany, d.tytz));
+            dtz += gJ12 * V.fy * L * iz2;
+        }
+        gm[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+        gm[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+        gm[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+        // M = Rq S
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float gs = gM[j] * pre.Rq[j] + gM[3 + j] * pre.Rq[3 + j] + gM[6 + j] * pre.Rq[6 + j];
+            gls[j] += gs * pre.s[j];
+        }
+        float gR[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gR[3 * k + j] = gM[3 * k + j] * pre.s[j];
+        // Rq(w, x, y, z) of the normalised quaternion
+        const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float w_ = q[0] / qn, x_ = q[1] / qn, y_ = q[2] / qn, z_ = q[3] / qn;
+        gqh[0] += 2.f * (-z_ * gR[1] + y_ * gR[2] + z_ * gR[3] - x_ * gR[5] - y_ * gR[6] + x_ * gR[7]);
+        gqh[1] += 2.f * (y_ * gR[1] + z_ * gR[2] + y_ * gR[3] - 2.f * x_ * gR[4] - w_ * gR[5] +
+                         z_ * gR[6] + w_ * gR[7] - 2.f * x_ * gR[8]);
+        gqh[2] += 2.f * (-2.f * y_ * gR[0] + x_ * gR[1] + w_ * gR[2] + x_ * gR[3] + z_ * gR[5] -
+                         w_ * gR[6] + z_ * gR[7] - 2.f * y_ * gR[8]);
+        gqh[3] += 2.f * (-2.f * z_ * gR[0] - w_ * gR[1] + x_ * gR[2] + w_ * gR[3] - 2.f * z_ * gR[4] +
+                         y_ * gR[5] + x_ * gR[6] + y_ * gR[7]);
+    }
+    if (!any) return;
+    float *Gm = const_cast<float *>(p.G.means), *Gl = const_cast<float *>(p.G.log_scales);
+    float *Gq = const_cast<float *>(p.G.quats), *Go = const_cast<float *>(p.G.logits);
+    float *Gs = const_cast<float *>(p.G.sh);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Gm[3 * g + i] += gm[i];
+        Gl[3 * g + i] += gls[i];
+    }
+    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float qh[4] = {q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn};
+    const float dot = gqh[0] * qh[0] + gqh[1] * qh[1] + gqh[2] * qh[2] + gqh[3] * qh[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Gq[4 * g + i] += (gqh[i] - qh[i] * dot) / qn;
+    Go[g] += glogit;
+    float *gs_out = Gs + (size_t)g * 3 * K;
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) gs_out[i] += gsh[i];
+}
+
+cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
+                                   const int8_t *views, int n_views, const float *grad2d,
+                                   const DevStatus *st, cudaStream_t s)
+{
+    if (S.n <= 0 || n_views <= 0) return cudaSuccess;
+    ParamArgs p;
+    p.S = S;
+    p.G = G;
+    p.n_views = n_views;
+    for (int i = 0; i < VRS_MAX_VIEWS; ++i) p.views[i] = i < n_views ? views[i] : 0;
+    p.grad2d = grad2d;
+    p.st = st;
+    const unsigned grid = grid_for(S.n, 128);
+    switch (S.K) {
+        case 1: k_backward_params<1><<<grid, 128, 0, s>>>(vt, p); break;
+        case 4: k_backward_params<4><<<grid, 128, 0, s>>>(vt, p); break;
+        case 9: k_backward_params<9><<<grid, 128, 0, s>>>(vt, p); break;
+        case 16: k_backward_params<16><<<grid, 128, 0, s>>>(vt, p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace vrs

@@ -158,7 +158,8 @@ struct Decision {
     float tx, ty, tz;          // camera-space mean (FP32 decision values)
     float txtz, tytz;
     float T0[3], T1[3];        // rows of J W
-    float n0, n1, b;           // |v0|^2, |v1|^2, v0.v1 of V = (J W) M
+    float v0[3], v1[3];        // rows of V = (J W) M
+    float n0, n1, b;           // |v0|^2, |v1|^2, v0.v1
     float det;                 // det of the dilated 2D covariance
     float ub, vb, rad;
     int x0, x1, y0, y1;
@@ -200,7 +201,7 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
         d.T0[k] = FADD(FMUL(j00, W[k]), FMUL(j02, W[6 + k]));
         d.T1[k] = FADD(FMUL(j11, W[3 + k]), FMUL(j12, W[6 + k]));
     }
-    float v0[3], v1[3];
+    float *v0 = d.v0, *v1 = d.v1;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         float a = FMUL(d.T0[0], g.M[j]);
@@ -385,6 +386,61 @@ __device__ __forceinline__ void pair_q2(float su, float sv, float l0, float l1, 
 __device__ __forceinline__ float pair_alpha(float lo, float q)
 {
     return fminf(ex2_approx(__fsub_rn(lo, q)), 0.99f);
+}
+
+// ---------------------------------------------------------------------------
+// Blend-kernel geometry and the staging of one instance into a tile's local
+// frame, shared by the forward and backward blend kernels.
+
+template <int TS>
+struct BlendCfg {
+    static constexpr int THREADS = TS * TS / 2;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int WGX = TS / 8;       // warps per tile row
+    static constexpr int BATCH = THREADS;
+};
+
+
+// Tile-local frame of a tile: origin (tx*TS - cx, ty*TS - cy) as an exact
+// double-float pair (hi, lo).
+__device__ __forceinline__ void tile_origin(float tile_px, float c, float &hi, float &lo)
+{
+    hi = __fsub_rn(tile_px, c);
+    const float bb = __fsub_rn(hi, tile_px);
+    lo = __fadd_rn(__fsub_rn(tile_px, __fsub_rn(hi, bb)), __fsub_rn(-c, bb));
+}
+
+// Stage one instance: tile-local mean, conic factors, threshold and per-warp mask.
+template <int TS>
+__device__ __forceinline__ uint32_t stage_instance(const float4 *rec, uint32_t rid, float oxh,
+                                                   float oxl, float oyh, float oyl, float4 &A,
+                                                   float4 &B, float4 &C)
+{
+    using Cfg = BlendCfg<TS>;
+    const float4 *rp = rec + (size_t)rid * kRecF4;
+    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+    const float su = __fadd_rn(__fsub_rn(r0.x, oxh), __fsub_rn(r0.z, oxl));
+    const float sv = __fadd_rn(__fsub_rn(r0.y, oyh), __fsub_rn(r0.w, oyl));
+    const float l0 = r1.x, l1 = r1.y, l2 = r1.z, lo = r1.w;
+    const float lt = lo + kLog2_255;
+    A = make_float4(su, sv, l0, l1);
+    B = make_float4(l2, lo, lt, r2.w);
+    C = make_float4(r2.x, r2.y, r2.z, 0.f);
+    uint32_t mask = 0;
+    if (lt > 0.f) {
+        // half extents of the ellipse q' <= lt: sqrt(lt * Sigma''_xx), sqrt(lt * Sigma''_yy)
+        const float ey = sqrtf(lt) / l2;
+        const float ex = sqrtf(lt * (l1 * l1 + l2 * l2)) / (fabsf(l0) * l2);
+        const float hx = ex * 1.001f + 3.5f + 1e-3f;
+        const float hy = ey * 1.001f + 3.5f + 1e-3f;
+#pragma unroll
+        for (int w = 0; w < Cfg::WARPS; ++w) {
+            const float cx = (float)((w % Cfg::WGX) * 8) + 4.0f;
+            const float cy = (float)((w / Cfg::WGX) * 8) + 4.0f;
+            if (fabsf(su - cx) <= hx && fabsf(sv - cy) <= hy) mask |= 1u << w;
+        }
+    }
+    return mask;
 }
 
 // Launch helpers (host).

@@ -338,8 +338,11 @@ def test_bin_sort_against_enumeration(orc):
     assert [int(k) for k in bs["keys"]] == [e[0] for e in exp]
     assert [int(v) for v in bs["vals"]] == [e[1] for e in exp]
     r = bs["ranges"]
-    assert r[0, 0] == 0 and r[-1, 1] == len(exp)
-    assert np.all(r[1:, 0] == r[:-1, 1])
+    ne = r[r[:, 1] > r[:, 0]]                      # empty tiles are {0, 0}
+    assert ne[0, 0] == 0 and ne[-1, 1] == len(exp)
+    assert np.all(ne[1:, 0] == ne[:-1, 1])
+    tiles = (bs["keys"] >> np.uint64(32)).astype(np.int64)
+    assert np.array_equal(np.bincount(tiles, minlength=len(r)), r[:, 1] - r[:, 0])
 
 
 # --------------------------------------------------------------------------- reverse pass
