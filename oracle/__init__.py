@@ -31,8 +31,8 @@ _LIB = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-ALPHA_WIN = 5e-5     # relative window around 1/255 that marks a knife-edge pixel
-T_WIN = 1e-4         # relative window around the 1e-4 transmittance stop
+ALPHA_WIN = 2e-5     # relative window around 1/255 that marks a knife-edge pixel
+T_WIN = 3e-5         # relative window around the 1e-4 transmittance stop
 
 
 def build(force: bool = False) -> str:

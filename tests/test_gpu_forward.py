@@ -3,7 +3,7 @@
 Bars: bit-exact instance counts, sorted key lists, record-index lists and tile
 ranges; per-pixel images within max abs 2e-4 (RGB, T) and 1e-4 relative
 (Eq. 1 depth) outside the knife-edge pixels the oracle flags (alpha within
-5e-5 relative of 1/255 or T' within 1e-4 relative of the 1e-4 stop).
+2e-5 relative of 1/255 or T' within 3e-5 relative of the 1e-4 stop).
 """
 import numpy as np
 import pytest
