@@ -227,6 +227,39 @@ vrs_status vrs_query_status(const vrs_plan *plan, const void *workspace, vrs_run
 /* Clears the device status block (stream ordered). */
 vrs_status vrs_reset_status(const vrs_plan *plan, void *workspace, void *stream);
 
+/* Largest n that vrs_sort_pairs_noalloc accepts: its static scratch holds this many pairs. */
+#define VRS_NOALLOC_MAX_PAIRS (1 << 20)
+
+/* Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of
+ * each key (8 bits per pass), the same sort vrs_bin_sort runs on the tile
+ * instances, for callers that must not allocate device memory: code running
+ * inside a CUDA stream capture (where cudaMalloc is not allowed), real-time
+ * frame loops that must not risk the device-wide synchronisation an
+ * allocation can cause, and plug-ins that live inside another application's
+ * fixed memory budget.  The paper has no counterpart; this is a service of
+ * the library.
+ *
+ * It allocates nothing.  Its scratch is a static device array of about
+ * 13.6 MB (VRS_NOALLOC_MAX_PAIRS pairs of ping-pong storage plus digit counts)
+ * that every GPU loading the library holds until the process exits.  The
+ * first call on a device, with that device current, looks the array's device
+ * address up and caches it; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * resets what must start at zero), so calls that overlap on the GPU - on
+ * different streams with no ordering between them - race and must not be
+ * issued.
+ *
+ * keys_in, vals_in: device, n entries, read only.  keys_out, vals_out: device,
+ * n entries, must not overlap the inputs.  Pairs with equal sort bits keep
+ * their input order.  Returns VRS_ERR_CAPACITY for n > VRS_NOALLOC_MAX_PAIRS
+ * (nothing is launched), VRS_ERR_INVALID for n < 0, key_bits outside 1..64,
+ * a NULL pointer or an output equal to its input, VRS_ERR_CUDA on a launch or
+ * set-up failure; n == 0 returns VRS_OK at once.  Stream ordered on `stream`
+ * (a cudaStream_t as void*). */
+vrs_status vrs_sort_pairs_noalloc(const uint64_t *keys_in, const uint32_t *vals_in,
+                                  uint64_t *keys_out, uint32_t *vals_out, int64_t n,
+                                  int32_t key_bits, void *stream);
+
 /* A static, human-readable name of a status. */
 const char *vrs_status_string(vrs_status status);
 

@@ -74,8 +74,11 @@ SIGNATURES = [
                               ctypes.POINTER(vrs_scene), _vp]),
     ("vrs_query_status", _i32, [ctypes.POINTER(vrs_plan), _vp, ctypes.POINTER(vrs_run_info), _vp]),
     ("vrs_reset_status", _i32, [ctypes.POINTER(vrs_plan), _vp, _vp]),
+    ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     ("vrs_status_string", ctypes.c_char_p, [_i32]),
 ]
+
+VRS_NOALLOC_MAX_PAIRS = 1 << 20
 
 _lock = threading.Lock()
 _lib = None
@@ -147,3 +150,8 @@ def vrs_reset_status(plan, workspace: int, stream: int) -> int:
 
 def vrs_status_string(code: int) -> str:
     return status_string(code)
+
+
+def vrs_sort_pairs_noalloc(keys_in: int, vals_in: int, keys_out: int, vals_out: int, n: int,
+                           key_bits: int, stream: int) -> int:
+    return load().vrs_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream)

@@ -10,28 +10,9 @@
 // instances is not deterministic; after this pass the list is).
 // The instance count is read on the device, so the launch sequence is fixed
 // by the plan and can be captured in a CUDA graph.
-#include "vrs_internal.cuh"
+#include "vrs_sort.cuh"
 
 namespace vrs {
-
-constexpr int kRadix = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys
-constexpr int kSortWarps = kSortThreads / 32;
-
-struct SortArgs {
-    const unsigned long long *keys_in;
-    const uint32_t *vals_in;
-    unsigned long long *keys_out;
-    uint32_t *vals_out;
-    uint32_t *counts;     // [kRadix][G]
-    uint32_t *totals;     // [kRadix]
-    const DevStatus *st;
-    unsigned long long cap;
-    int shift;
-    int G;
-};
 
 __device__ __forceinline__ uint32_t live_count(const DevStatus *st, unsigned long long cap)
 {
@@ -126,15 +107,6 @@ __global__ void __launch_bounds__(1024) k_scan_digits(const SortArgs a)
     if (t == (int)blockDim.x - 1) a.totals[d] = incl;
 }
 
-struct DownSmem {
-    unsigned long long keys[kSortTile];
-    uint32_t vals[kSortTile];
-    uint32_t whist[kSortWarps][kRadix + 1];
-    uint32_t dstart[kRadix];
-    uint32_t gbase[kRadix];
-    uint32_t tcnt[kRadix];
-    uint32_t wtot[kSortWarps];
-};
 
 __global__ void __launch_bounds__(kSortThreads) k_downsweep(const SortArgs a)
 {
