@@ -154,6 +154,19 @@ static int f_isfinite(float v) { return isfinite(v) ? 1 : 0; }
 /* keeps a tile index inside the int range before conversion */
 static double clamp_big(double v) { return v < -1.0e9 ? -1.0e9 : (v > 1.0e9 ? 1.0e9 : v); }
 
+/* floor((a + b) / tile) of the exact real sum of two floats: the rounded sum
+ * s and its exact error e (Knuth's two-sum, in double), then one step down
+ * when s is a multiple of the tile and e < 0. */
+static int floor_sum_div(float a, float b, int tile)
+{
+    double s = (double)a + (double)b;
+    double bb = s - (double)a;
+    double e = ((double)a - (s - bb)) + ((double)b - bb);
+    double k = floor(s / tile);
+    if (s == k * tile && e < 0.0) k -= 1.0;
+    return (int)clamp_big(k);
+}
+
 /* ------------------------------------------------------------------------- */
 /* The integer decisions, in FP32.  Each statement below is one correctly
  * rounded IEEE operation; the order is part of the definition.
@@ -190,8 +203,8 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         qq = qq + q[2] * q[2];
         qq = qq + q[3] * q[3];
         if (!(qq > 0.0f)) { status |= 1; continue; }
-        float qn = sqrtf(qq);
-        float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        float iq = 1.0f / sqrtf(qq);
+        float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
         float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
         float wx = w * x, wy = w * y, wz = w * z;
         float Rq[9];
@@ -213,12 +226,13 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         const float tx = tc[0], ty = tc[1], tz = tc[2];
         if (!(tz > cam->znear)) continue;
         /* clamped projection Jacobian, rows of T = J W */
-        float txtz = tx / tz, tytz = ty / tz;
-        float cxz = fminf(limx, fmaxf(-limx, txtz)) * tz;
-        float cyz = fminf(limy, fmaxf(-limy, tytz)) * tz;
-        float j00 = cam->fx / tz, j11 = cam->fy / tz, tz2 = tz * tz;
-        float j02 = -((cam->fx * cxz) / tz2);
-        float j12 = -((cam->fy * cyz) / tz2);
+        float iz = 1.0f / tz;
+        float txtz = tx * iz, tytz = ty * iz;
+        float cxz = fminf(limx, fmaxf(-limx, txtz));      /* clamped x/z */
+        float cyz = fminf(limy, fmaxf(-limy, tytz));
+        float j00 = cam->fx * iz, j11 = cam->fy * iz;
+        float j02 = -(j00 * cxz);                          /* -fx (x/z) / z */
+        float j12 = -(j11 * cyz);
         float T0[3], T1[3];
         for (int k = 0; k < 3; ++k) {
             T0[k] = j00 * W[k] + j02 * W[6 + k];
@@ -258,10 +272,10 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         float ub = cam->fx * txtz, vb = cam->fy * tytz;
         float xlo = ub - rad, xhi = ub + rad, ylo = vb - rad, yhi = vb + rad;
         /* tile rectangle: floor of the exact value of (edge + principal point) / tile */
-        int x0 = (int)clamp_big(floor(((double)xlo + (double)cam->cx) / tile));
-        int x1 = (int)clamp_big(floor(((double)xhi + (double)cam->cx) / tile)) + 1;
-        int y0 = (int)clamp_big(floor(((double)ylo + (double)cam->cy) / tile));
-        int y1 = (int)clamp_big(floor(((double)yhi + (double)cam->cy) / tile)) + 1;
+        int x0 = floor_sum_div(xlo, cam->cx, tile);
+        int x1 = floor_sum_div(xhi, cam->cx, tile) + 1;
+        int y0 = floor_sum_div(ylo, cam->cy, tile);
+        int y1 = floor_sum_div(yhi, cam->cy, tile) + 1;
         x0 = x0 < 0 ? 0 : (x0 > gw ? gw : x0);
         x1 = x1 < 0 ? 0 : (x1 > gw ? gw : x1);
         y0 = y0 < 0 ? 0 : (y0 > gh ? gh : y0);

@@ -80,18 +80,15 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_bwd(const __grid_constant__ ViewTable vt, const BwdArgs a)
 {
     using Cfg = BlendCfg<TS>;
-    __shared__ float4 sA[Cfg::BATCH], sB[Cfg::BATCH], sC[Cfg::BATCH];
-    __shared__ uint32_t smask[Cfg::BATCH], srid[Cfg::BATCH];
-    __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
-    __shared__ uint32_t s_max;
+    __shared__ float4 wA[Cfg::WARPS][32], wB[Cfg::WARPS][32], wC[Cfg::WARPS][32];
+    __shared__ uint32_t wR[Cfg::WARPS][32];
 
     if (a.st->flags & ST_CAPACITY) return;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int px_l = (w % Cfg::WGX) * 8 + 2 * (lane & 3);
-    const int py_l = (w / Cfg::WGX) * 8 + (lane >> 2);
-    const float pxc = (float)px_l + 0.5f, pyc = (float)py_l + 0.5f;
     const uint32_t lmask = lanemask_lt();
+    const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
+    const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
 
     const int64_t t = blockIdx.x;
     const int vi = view_of_tile(vt, t);
@@ -99,7 +96,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const float4 pp = a.viewtab[vi];
     const int64_t lt_ = t - V.tile_base;
     const int tx = (int)(lt_ % V.gw), ty = (int)(lt_ / V.gw);
-    const int px = tx * TS + px_l, py = ty * TS + py_l;
+    const int px = tx * TS + bx + 2 * (lane & 3), py = ty * TS + by + (lane >> 2);
     const bool in0 = px < V.w && py < V.h, in1 = px + 1 < V.w && py < V.h;
     float oxh, oxl, oyh, oyl;
     tile_origin((float)(tx * TS), pp.x, oxh, oxl);
@@ -135,55 +132,49 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
         P1.gD = a.g_depth[pix + 1];
         P1.gT = a.g_T ? a.g_T[pix + 1] : 0.f;
     }
-    if (tid == 0) s_max = 0u;
-    __syncthreads();
-    const uint32_t wm = __reduce_max_sync(FULL, max(P0.last, P1.last));
-    if (lane == 0) atomicMax(&s_max, wm);
-    __syncthreads();
-    const uint32_t maxlast = s_max;
-    const int nb = (int)((maxlast + Cfg::BATCH - 1) / Cfg::BATCH);
+    // this warp's blended positions end at its largest last contributor
+    const uint32_t maxlast = __reduce_max_sync(FULL, max(P0.last, P1.last));
+    if (maxlast == 0) return;
+    const int nb = (int)((maxlast + 31) / 32);
 
     for (int bi = nb - 1; bi >= 0; --bi) {
-        const uint32_t bs = range.x + (uint32_t)bi * Cfg::BATCH;
-        const uint32_t j = bs + tid;
+        const uint32_t bs = range.x + (uint32_t)bi * 32;
+        const uint32_t j = bs + lane;
         const uint32_t rid = (j < range.x + maxlast) ? __ldg(a.vals + j) : 0xffffffffu;
+        bool hit = false;
+        float4 A, B, C;
         if ((int64_t)rid < a.n_records) {
-            float4 A, B, C;
-            smask[tid] = stage_instance<TS>(a.rec, rid, oxh, oxl, oyh, oyl, A, B, C);
-            sA[tid] = A;
-            sB[tid] = B;
-            sC[tid] = C;
-        } else {
-            smask[tid] = 0u;
+            float4 r0, r1, r2;
+            load_record(a.rec, rid, r0, r1, r2);
+            stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
+            hit = cull_block(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z), (float)bx + 0.5f, (float)by + 0.5f);
         }
-        srid[tid] = rid;
-        __syncthreads();
-        int cnt = 0;
-#pragma unroll
-        for (int c = 0; c < Cfg::BATCH / 32; ++c) {
-            const uint32_t bit = (smask[c * 32 + lane] >> w) & 1u;
-            const uint32_t bal = __ballot_sync(FULL, bit);
-            if (bit) slist[w][cnt + __popc(bal & lmask)] = (uint16_t)(c * 32 + lane);
-            cnt += __popc(bal);
+        const uint32_t bal = __ballot_sync(FULL, hit);
+        if (hit) {
+            const int slot = __popc(bal & lmask);
+            C.w = __int_as_float(lane);
+            wA[w][slot] = A;
+            wB[w][slot] = B;
+            wC[w][slot] = C;
+            wR[w][slot] = rid;
         }
         __syncwarp();
-        for (int k = cnt - 1; k >= 0; --k) {
-            const int jj = slist[w][k];
-            const uint32_t pos = (uint32_t)bi * Cfg::BATCH + jj + 1;
-            const float4 A = sA[jj];
-            const float4 B = sB[jj];
+        for (int k = __popc(bal) - 1; k >= 0; --k) {
+            const float4 Ak = wA[w][k];
+            const float4 Bk = wB[w][k];
+            const float4 Ck = wC[w][k];
+            const uint32_t pos = (uint32_t)bi * 32 + (uint32_t)__float_as_int(Ck.w) + 1;
             float q0, q1;
-            pair_q2(A.x, A.y, A.z, A.w, B.x, pxc, pyc, q0, q1);
-            const bool c0 = pos <= P0.last && q0 <= B.z;
-            const bool c1 = pos <= P1.last && q1 <= B.z;
+            pair_q2(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, pxc, pyc, q0, q1);
+            const bool c0 = pos <= P0.last && q0 <= Bk.z;
+            const bool c1 = pos <= P1.last && q1 <= Bk.z;
             if (!__any_sync(FULL, c0 || c1)) continue;
-            const float4 C = sC[jj];
             float g[kGrad2D];
 #pragma unroll
             for (int i = 0; i < kGrad2D; ++i) g[i] = 0.f;
-            const float dx = A.x - pxc, dy = A.y - pyc;
-            if (c0) pixel_adjoint(P0, q0, dx, dy, A, B, C, g);
-            if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, A, B, C, g);
+            const float dx = Ak.x - pxc, dy = Ak.y - pyc;
+            if (c0) pixel_adjoint(P0, q0, dx, dy, Ak, Bk, Ck, g);
+            if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, Ak, Bk, Ck, g);
 #pragma unroll
             for (int i = 0; i < kGrad2D; ++i) {
 #pragma unroll
@@ -193,10 +184,10 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 float v = g[0];
 #pragma unroll
                 for (int i = 1; i < kGrad2D; ++i) v = lane == i ? g[i] : v;
-                atomicAdd(a.grad2d + (size_t)srid[jj] * kGrad2D + lane, v);
+                atomicAdd(a.grad2d + (size_t)wR[w][k] * kGrad2D + lane, v);
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 

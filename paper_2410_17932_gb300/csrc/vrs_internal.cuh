@@ -133,8 +133,8 @@ __device__ __forceinline__ bool gauss_pre(const float ls[3], const float q[4], G
     qq = FADD(qq, FMUL(q[2], q[2]));
     qq = FADD(qq, FMUL(q[3], q[3]));
     if (!(qq > 0.0f)) return false;
-    float qn = __fsqrt_rn(qq);
-    float w = FDIV(q[0], qn), x = FDIV(q[1], qn), y = FDIV(q[2], qn), z = FDIV(q[3], qn);
+    float iq = FDIV(1.0f, __fsqrt_rn(qq));
+    float w = FMUL(q[0], iq), x = FMUL(q[1], iq), y = FMUL(q[2], iq), z = FMUL(q[3], iq);
     float xx = FMUL(x, x), yy = FMUL(y, y), zz = FMUL(z, z);
     float xy = FMUL(x, y), xz = FMUL(x, z), yz = FMUL(y, z);
     float wx = FMUL(w, x), wy = FMUL(w, y), wz = FMUL(w, z);
@@ -152,6 +152,22 @@ __device__ __forceinline__ bool gauss_pre(const float ls[3], const float q[4], G
 #pragma unroll
         for (int j = 0; j < 3; ++j) g.M[3 * k + j] = FMUL(g.Rq[3 * k + j], g.s[j]);
     return true;
+}
+
+// floor((a + b) * inv_tile) of the exact real sum of two floats, inv_tile a
+// power of two: the rounded sum s and its exact error e (Knuth's two-sum), then
+// one step down when s is a multiple of the tile and e < 0.  Exact for
+// |a + b| < 2^24; larger values lie far outside any tile grid and are clamped.
+__device__ __forceinline__ int floor_sum_div(float a, float b, float inv_tile)
+{
+    const float s = FADD(a, b);
+    const float bb = FSUB(s, a);
+    const float e = FADD(FSUB(a, FSUB(s, bb)), FSUB(b, bb));
+    const float q = FMUL(s, inv_tile);
+    float k = floorf(q);
+    if (q == k && e < 0.0f) k = FSUB(k, 1.0f);
+    k = fminf(fmaxf(k, -1.0e9f), 1.0e9f);
+    return (int)k;
 }
 
 struct Decision {
@@ -187,15 +203,16 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     const float tz = tc[2];
     if (!(tz > V.znear)) return;
     const float limx = FMUL(1.3f, V.tanx), limy = FMUL(1.3f, V.tany);
-    d.txtz = FDIV(tc[0], tz);
-    d.tytz = FDIV(tc[1], tz);
+    const float iz = FDIV(1.0f, tz);
+    d.txtz = FMUL(tc[0], iz);
+    d.tytz = FMUL(tc[1], iz);
     d.clampx = (d.txtz > limx) || (d.txtz < -limx);
     d.clampy = (d.tytz > limy) || (d.tytz < -limy);
-    float cxz = FMUL(fminf(limx, fmaxf(-limx, d.txtz)), tz);
-    float cyz = FMUL(fminf(limy, fmaxf(-limy, d.tytz)), tz);
-    float j00 = FDIV(V.fx, tz), j11 = FDIV(V.fy, tz), tz2 = FMUL(tz, tz);
-    float j02 = -FDIV(FMUL(V.fx, cxz), tz2);
-    float j12 = -FDIV(FMUL(V.fy, cyz), tz2);
+    const float cxz = fminf(limx, fmaxf(-limx, d.txtz));     // clamped x/z
+    const float cyz = fminf(limy, fmaxf(-limy, d.tytz));
+    const float j00 = FMUL(V.fx, iz), j11 = FMUL(V.fy, iz);
+    const float j02 = -FMUL(j00, cxz);                        // -fx (x/z) / z
+    const float j12 = -FMUL(j11, cyz);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         d.T0[k] = FADD(FMUL(j00, W[k]), FMUL(j02, W[6 + k]));
@@ -253,17 +270,10 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     d.vb = FMUL(V.fy, d.tytz);
     float xlo = FSUB(d.ub, rad), xhi = FADD(d.ub, rad);
     float ylo = FSUB(d.vb, rad), yhi = FADD(d.vb, rad);
-    // floor of the exact value of (edge + principal point) / tile, in double
-    const double inv = 1.0 / (double)tile;   // a power of two: exact
-    double fx0 = floor(__dmul_rn(__dadd_rn((double)xlo, (double)V.cx), inv));
-    double fx1 = floor(__dmul_rn(__dadd_rn((double)xhi, (double)V.cx), inv));
-    double fy0 = floor(__dmul_rn(__dadd_rn((double)ylo, (double)V.cy), inv));
-    double fy1 = floor(__dmul_rn(__dadd_rn((double)yhi, (double)V.cy), inv));
-    fx0 = fmin(fmax(fx0, -1.0e9), 1.0e9);
-    fx1 = fmin(fmax(fx1, -1.0e9), 1.0e9);
-    fy0 = fmin(fmax(fy0, -1.0e9), 1.0e9);
-    fy1 = fmin(fmax(fy1, -1.0e9), 1.0e9);
-    int x0 = (int)fx0, x1 = (int)fx1 + 1, y0 = (int)fy0, y1 = (int)fy1 + 1;
+    // floor of the exact value of (edge + principal point) / tile
+    const float inv = 1.0f / (float)tile;    // a power of two: exact
+    int x0 = floor_sum_div(xlo, V.cx, inv), x1 = floor_sum_div(xhi, V.cx, inv) + 1;
+    int y0 = floor_sum_div(ylo, V.cy, inv), y1 = floor_sum_div(yhi, V.cy, inv) + 1;
     x0 = min(max(x0, 0), V.gw);
     x1 = min(max(x1, 0), V.gw);
     y0 = min(max(y0, 0), V.gh);
@@ -410,37 +420,128 @@ __device__ __forceinline__ void tile_origin(float tile_px, float c, float &hi, f
     lo = __fadd_rn(__fsub_rn(tile_px, __fsub_rn(hi, bb)), __fsub_rn(-c, bb));
 }
 
-// Stage one instance: tile-local mean, conic factors, threshold and per-warp mask.
-template <int TS>
-__device__ __forceinline__ uint32_t stage_instance(const float4 *rec, uint32_t rid, float oxh,
-                                                   float oxl, float oyh, float oyl, float4 &A,
-                                                   float4 &B, float4 &C)
+// Culling of one staged splat against the 8x8 pixel blocks of a tile.
+// q'(p) = (l0 (su - px) + l1 (sv - py))^2 + (l2 (sv - py))^2 is convex, so
+// unless its minimiser (su, sv) lies in a block's rectangle of pixel centres,
+// its minimum over the rectangle lies on an edge, where it is a 1D quadratic
+// minimised at a clamped vertex.  A block is kept when that minimum is within
+// lt plus a margin far above the rounding of either evaluation, so only pairs
+// with alpha < 1/255 for certain are dropped.  A bounding-box test of the
+// ellipse q' <= lt screens the blocks first.
+struct CullSplat {
+    float su, sv, l0, l1, l2, thr, il0, ic, hx, hy;
+};
+
+__device__ __forceinline__ CullSplat cull_setup(float su, float sv, float l0, float l1, float l2, float lt)
 {
-    using Cfg = BlendCfg<TS>;
+    CullSplat c;
+    c.su = su;
+    c.sv = sv;
+    c.l0 = l0;
+    c.l1 = l1;
+    c.l2 = l2;
+    c.thr = lt + 1e-3f * (1.0f + fabsf(lt));
+    c.il0 = 1.0f / l0;
+    const float s2 = l1 * l1 + l2 * l2;
+    c.ic = 1.0f / s2;
+    const float lp = fmaxf(c.thr, 0.f);
+    // half extents of q' <= thr: sqrt(thr * Sigma''_xx), sqrt(thr * Sigma''_yy), plus the half block
+    c.hx = sqrtf(lp * s2) * c.il0 / l2 * 1.001f + 3.5f + 1e-3f;
+    c.hy = sqrtf(lp) / l2 * 1.001f + 3.5f + 1e-3f;
+    return c;
+}
+
+// Block of pixel centres [x0, x0 + 7] x [y0, y0 + 7] (tile-local).
+__device__ __forceinline__ bool cull_block(const CullSplat &c, float x0, float y0)
+{
+    if (c.thr <= 0.f) return false;
+    if (fabsf(c.su - (x0 + 3.5f)) > c.hx || fabsf(c.sv - (y0 + 3.5f)) > c.hy) return false;
+    const float u0 = c.su - (x0 + 7.0f), u1 = c.su - x0, v0 = c.sv - (y0 + 7.0f), v1 = c.sv - y0;
+    if (u0 <= 0.f && u1 >= 0.f && v0 <= 0.f && v1 >= 0.f) return true;
+    float best = 3.0e38f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float v = e ? v1 : v0;                       // horizontal edges
+        const float u = fminf(fmaxf(-c.l1 * v * c.il0, u0), u1);
+        const float t = fmaf(c.l0, u, c.l1 * v), sy = c.l2 * v;
+        best = fminf(best, fmaf(t, t, sy * sy));
+        const float uu = e ? u1 : u0;                      // vertical edges
+        const float vv = fminf(fmaxf(-c.l0 * c.l1 * uu * c.ic, v0), v1);
+        const float t2 = fmaf(c.l0, uu, c.l1 * vv), sy2 = c.l2 * vv;
+        best = fminf(best, fmaf(t2, t2, sy2 * sy2));
+    }
+    return best <= c.thr;
+}
+
+// Gathers one instance's record and moves it into the tile-local frame:
+// A = (su, sv, l0, l1), B = (l2, lo, lt, depth), C = (r, g, b, -).
+__device__ __forceinline__ void load_record(const float4 *rec, uint32_t rid, float4 &r0, float4 &r1,
+                                            float4 &r2)
+{
     const float4 *rp = rec + (size_t)rid * kRecF4;
-    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+    r0 = __ldg(rp);
+    r1 = __ldg(rp + 1);
+    r2 = __ldg(rp + 2);
+}
+
+__device__ __forceinline__ void stage_record(const float4 r0, const float4 r1, const float4 r2,
+                                             float oxh, float oxl, float oyh, float oyl, float4 &A,
+                                             float4 &B, float4 &C)
+{
     const float su = __fadd_rn(__fsub_rn(r0.x, oxh), __fsub_rn(r0.z, oxl));
     const float sv = __fadd_rn(__fsub_rn(r0.y, oyh), __fsub_rn(r0.w, oyl));
-    const float l0 = r1.x, l1 = r1.y, l2 = r1.z, lo = r1.w;
-    const float lt = lo + kLog2_255;
-    A = make_float4(su, sv, l0, l1);
-    B = make_float4(l2, lo, lt, r2.w);
+    A = make_float4(su, sv, r1.x, r1.y);
+    B = make_float4(r1.z, r1.w, r1.w + kLog2_255, r2.w);
     C = make_float4(r2.x, r2.y, r2.z, 0.f);
-    uint32_t mask = 0;
-    if (lt > 0.f) {
-        // half extents of the ellipse q' <= lt: sqrt(lt * Sigma''_xx), sqrt(lt * Sigma''_yy)
-        const float ey = sqrtf(lt) / l2;
-        const float ex = sqrtf(lt * (l1 * l1 + l2 * l2)) / (fabsf(l0) * l2);
-        const float hx = ex * 1.001f + 3.5f + 1e-3f;
-        const float hy = ey * 1.001f + 3.5f + 1e-3f;
-#pragma unroll
-        for (int w = 0; w < Cfg::WARPS; ++w) {
-            const float cx = (float)((w % Cfg::WGX) * 8) + 4.0f;
-            const float cy = (float)((w / Cfg::WGX) * 8) + 4.0f;
-            if (fabsf(su - cx) <= hx && fabsf(sv - cy) <= hy) mask |= 1u << w;
-        }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk-copy (TMA, non-tensor) helpers.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1D bulk copy global -> shared, completing `bytes` on the mbarrier.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_iters)
+{
+    for (uint32_t i = 0; i < max_iters; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    return mask;
+    return false;
 }
 
 // Launch helpers (host).

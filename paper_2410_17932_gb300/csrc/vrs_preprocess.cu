@@ -19,42 +19,47 @@ struct PreParams {
     unsigned long long cap;
 };
 
+// Rows of SH coefficients that are a whole number of 16-byte chunks (degree 1
+// and 3) are bulk-copied (TMA, cp.async.bulk) into padded shared-memory rows
+// at kernel start and read only for the colour, so the copies overlap the
+// FP32 decision path; other degrees are loaded into registers.
 template <int K>
-__device__ __forceinline__ void load_sh(const float *sh, int g, bool vec4, float *c)
-{
-    const float *src = sh + (size_t)g * 3 * K;
-    if constexpr ((3 * K) % 4 == 0) {
-        if (vec4) {
-            const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-            for (int i = 0; i < 3 * K / 4; ++i) {
-                float4 v = __ldg(s4 + i);
-                c[4 * i] = v.x;
-                c[4 * i + 1] = v.y;
-                c[4 * i + 2] = v.z;
-                c[4 * i + 3] = v.w;
-            }
-            return;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 3 * K; ++i) c[i] = __ldg(src + i);
-}
+struct ShStage {
+    static constexpr bool kBulk = (12 * K) % 16 == 0;
+    static constexpr int kRow = kBulk ? 3 * K + 4 : 4;          // padded row (floats): 52 for SH-3
+    static constexpr int kFloats = kBulk ? 128 * kRow : 4;
+};
+
+constexpr uint32_t kBulkWaitIters = 1u << 22;
 
 template <int K>
 __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ ViewTable vt,
                                                     const __grid_constant__ PreParams p)
 {
+    using SS = ShStage<K>;
+    __shared__ __align__(16) float sh_s[SS::kFloats];
+    __shared__ __align__(8) uint64_t bar;
     const unsigned FULL = 0xffffffffu;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool in = g < p.S.n;
+    const bool use_bulk = SS::kBulk && (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
+
+    if (use_bulk) {
+        if (threadIdx.x == 0) {
+            const int n_here = min((int)blockDim.x, p.S.n - (int)(blockIdx.x * blockDim.x));
+            mbar_init(&bar, 1);
+            mbar_arrive_expect_tx(&bar, (uint32_t)n_here * 12u * K);
+        }
+        __syncthreads();
+        if (in) bulk_g2s(&sh_s[threadIdx.x * SS::kRow], p.S.sh + (size_t)g * 3 * K, 12u * K, &bar);
+    }
 
     float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
     float logit = 0.f;
-    float sh[3 * K];
+    float shr[SS::kBulk ? 1 : 3 * K];
 #pragma unroll
-    for (int i = 0; i < 3 * K; ++i) sh[i] = 0.f;
+    for (int i = 0; i < (SS::kBulk ? 1 : 3 * K); ++i) shr[i] = 0.f;
     bool ok = in;
     if (in) {
         m[0] = __ldg(p.S.means + 3 * g);
@@ -71,26 +76,26 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
             for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
         }
         logit = __ldg(p.S.logits + g);
-        const bool vec4 = (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
-        load_sh<K>(p.S.sh, g, vec4, sh);
-        float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
-        float shs = 0.f;
+        if (!use_bulk) {
+            const float *src = p.S.sh + (size_t)g * 3 * K;
 #pragma unroll
-        for (int i = 0; i < 3 * K; ++i) shs += sh[i];
-        if (!isfinite(chk) || !isfinite(shs)) {
-            ok = false;
-            atomicOr(&p.st->flags, ST_NONFINITE);
+            for (int i = 0; i < (SS::kBulk ? 1 : 3 * K); ++i) shr[i] = __ldg(src + i);
         }
+        const float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
+        if (!isfinite(chk)) ok = false;
     }
     GaussPre pre;
+    bool zero_quat = false;
     if (ok && !gauss_pre(ls, q, pre)) {
         ok = false;
-        atomicOr(&p.st->flags, ST_ZERO_QUAT);
+        zero_quat = true;
     }
-    // opacity in the log2 domain: log2(sigmoid(x)) = -log2(1 + e^-x)
     const float LOG2E = 1.4426950408889634f;
     const float lo = logit >= 0.f ? -log1pf(expf(-logit)) * LOG2E
                                   : (logit - log1pf(expf(logit))) * LOG2E;
+    const float *shp = use_bulk ? &sh_s[threadIdx.x * SS::kRow] : shr;
+    bool sh_checked = false;       // the coefficients have arrived and are finite
+    bool nonfinite = in && !ok && !zero_quat;
 
     for (int vi = 0; vi < p.n_views; ++vi) {
         const DevView &V = vt.v[p.views[vi]];
@@ -99,6 +104,22 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
         d.x0 = d.x1 = d.y0 = d.y1 = 0;
         d.tz = 0.f;
         if (ok) decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+        if (d.visible && !sh_checked) {
+            if (use_bulk && !mbar_wait(&bar, 0, kBulkWaitIters)) {
+                atomicOr(&p.st->flags, ST_TIMEOUT);
+                ok = false;
+            } else {
+                float shs = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3 * K; ++i) shs += use_bulk ? shp[i] : shr[SS::kBulk ? 0 : i];
+                if (!isfinite(shs)) {
+                    ok = false;
+                    nonfinite = true;
+                }
+            }
+            sh_checked = true;
+            if (!ok) d.visible = false;
+        }
         if (d.visible) {
             // 2D mean relative to the principal point, as an unevaluated double-float sum
             float xh, xl, yh, yl, zh, zl, uh, ul, vh, vl;
@@ -122,18 +143,26 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
             dx *= inv; dy *= inv; dz *= inv;
             float Y[16];
             sh_basis(dx, dy, dz, K, Y);
-            float col[3];
+            float col[3] = {0.5f, 0.5f, 0.5f};
+            if (use_bulk) {
+                const float4 *s4 = reinterpret_cast<const float4 *>(shp);
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.5f;
+                for (int i = 0; i < 3 * K / 4; ++i) {
+                    const float4 v4 = s4[i];
+                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
-                col[ch] = fmaxf(acc, 0.0f);
+                    for (int e = 0; e < 4; ++e) col[(4 * i + e) % 3] += Y[(4 * i + e) / 3] * vv[e];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) col[ch] += Y[k] * shr[SS::kBulk ? 0 : 3 * k + ch];
             }
             float4 *r = p.rec + (size_t)(V.rec_base + g) * kRecF4;
             r[0] = make_float4(uh, vh, ul, vl);
             r[1] = make_float4(l0, l1, l2, lo);
-            r[2] = make_float4(col[0], col[1], col[2], d.tz);
+            r[2] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), d.tz);
         }
         // warp-cooperative emission: one atomic per warp, coalesced key writes
         const uint32_t cnt = d.visible ? (uint32_t)((d.x1 - d.x0) * (d.y1 - d.y0)) : 0u;
@@ -181,6 +210,11 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
         }
         if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
     }
+    if (nonfinite) atomicOr(&p.st->flags, ST_NONFINITE);
+    if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
+    // the CTA's shared memory must outlive its bulk copies
+    if (use_bulk && in && !sh_checked && !mbar_wait(&bar, 0, kBulkWaitIters))
+        atomicOr(&p.st->flags, ST_TIMEOUT);
 }
 
 // Principal points of the views, read by the blend kernels to build each

@@ -1,17 +1,18 @@
 // Step 3: per-tile front-to-back alpha compositing of colour, the approximate
 // depth of Eq. 1 (Sec. 3.2) and the final transmittance.
 //
-// One CTA owns one tile (TS x TS pixels); every thread owns two horizontally
-// adjacent pixels and every warp an 8x8 block.  The tile's sorted instances are
-// staged in batches of one per thread: the staging thread gathers the 48-byte
-// record, moves the 2D mean into the tile-local frame (double-float, so that a
-// 2016-pixel-wide view keeps sub-1e-5 px positions), and tests the splat's
-// alpha >= 1/255 ellipse against each warp's 8x8 block.  Each warp then
-// compacts the batch to the splats that can reach its block (ballot + popc,
-// order preserved) and evaluates only those.  A warp that has finished all its
-// pixels skips the evaluation; the CTA leaves when every pixel has stopped.
-// The culling is conservative (only pairs with alpha < 1/255 for certain are
-// skipped), so the image is the same as without it.
+// One CTA owns one tile (TS x TS pixels); every warp owns an 8x8 block and
+// every lane two horizontally adjacent pixels.  The tile's sorted instances
+// are staged in shared memory in batches of one per thread: the staging lane
+// gathers the 48-byte record, moves its 2D mean into the tile-local frame in
+// double-float (2016-pixel-wide views keep sub-1e-5 px positions), and tests
+// the splat against every warp's block (a bounding-box screen, then the exact
+// minimum of the quadratic form over the block).  Each warp compacts the
+// batch to the splats that can reach its block (ballot + popc, list order
+// kept) and evaluates only those, two at a time, without branches: a pixel's
+// update is a select on its skip / stop / blend decision.  The culling only
+// drops pairs with alpha < 1/255 for certain, so the image is the same as
+// without it.  The CTA leaves a tile when all of its pixels have stopped.
 #include "vrs_internal.cuh"
 
 namespace vrs {
@@ -32,6 +33,35 @@ struct FwdArgs {
     int persistent;
 };
 
+struct PixAcc {
+    float T, r, g, b, D;
+    uint32_t last, stop;
+    bool done;
+};
+
+// One splat at one pixel, front to back: skip below 1/255, stop before T would
+// drop under 1e-4, otherwise blend.  Written as selects (no branches).
+__device__ __forceinline__ void pix_update(PixAcc &P, float q, const float4 &B, const float4 &C,
+                                           uint32_t &n_blend)
+{
+    const bool h = !P.done && q <= B.z;
+    const float al = pair_alpha(B.y, q);
+    const float Tn = P.T * (1.f - al);
+    const bool stop = h && Tn < 1e-4f;
+    const bool blend = h && !stop;
+    const float wt = blend ? al * P.T : 0.f;
+    P.r = fmaf(C.x, wt, P.r);
+    P.g = fmaf(C.y, wt, P.g);
+    P.b = fmaf(C.z, wt, P.b);
+    P.D = fmaf(B.w, wt, P.D);
+    const uint32_t pos = (uint32_t)__float_as_int(C.w);
+    P.T = blend ? Tn : P.T;
+    P.last = blend ? pos : P.last;
+    P.stop = stop ? pos : P.stop;
+    P.done = P.done || stop;
+    n_blend += blend ? 1u : 0u;
+}
+
 template <int TS>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
@@ -43,17 +73,17 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     __shared__ int64_t s_tile;
     __shared__ unsigned long long s_cnt[2];
 
-    if (a.st->flags & ST_CAPACITY) return;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int px_l = (w % Cfg::WGX) * 8 + 2 * (lane & 3);
-    const int py_l = (w / Cfg::WGX) * 8 + (lane >> 2);
-    const float pxc = (float)px_l + 0.5f, pyc = (float)py_l + 0.5f;
+    const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
+    const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
     const uint32_t lmask = lanemask_lt();
     if (tid == 0) s_cnt[0] = s_cnt[1] = 0ull;
+    __syncthreads();
+    const bool skip_all = (a.st->flags & ST_CAPACITY) != 0;
     uint32_t n_eval = 0, n_blend = 0;
 
-    for (int64_t iter = 0;; ++iter) {
+    for (int64_t iter = 0; !skip_all; ++iter) {
         int64_t t;
         if (a.persistent) {
             if (tid == 0) {
@@ -73,34 +103,36 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
         const float4 pp = a.viewtab[vi];
         const int64_t lt_ = t - V.tile_base;
         const int tx = (int)(lt_ % V.gw), ty = (int)(lt_ / V.gw);
-        const int px = tx * TS + px_l, py = ty * TS + py_l;
+        const int px = tx * TS + bx + 2 * (lane & 3), py = ty * TS + by + (lane >> 2);
         const bool in0 = px < V.w && py < V.h, in1 = px + 1 < V.w && py < V.h;
         float oxh, oxl, oyh, oyl;
         tile_origin((float)(tx * TS), pp.x, oxh, oxl);
         tile_origin((float)(ty * TS), pp.y, oyh, oyl);
         const uint2 range = a.ranges[t];
 
-        float T0 = 1.f, T1 = 1.f, D0 = 0.f, D1 = 0.f;
-        float c0r = 0.f, c0g = 0.f, c0b = 0.f, c1r = 0.f, c1g = 0.f, c1b = 0.f;
-        uint32_t last0 = 0, last1 = 0;
-        uint32_t stop0 = range.y - range.x, stop1 = range.y - range.x;
-        bool done0 = !in0, done1 = !in1;
-        if (!in0) stop0 = 0;
-        if (!in1) stop1 = 0;
+        PixAcc P0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in0 ? range.y - range.x : 0u, !in0};
+        PixAcc P1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in1 ? range.y - range.x : 0u, !in1};
 
         for (uint32_t bs = range.x; bs < range.y; bs += Cfg::BATCH) {
-            if (__syncthreads_and(done0 && done1)) break;
+            if (__syncthreads_and(P0.done && P1.done)) break;
             const uint32_t j = bs + tid;
             const uint32_t rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
+            uint32_t mask = 0u;
             if ((int64_t)rid < a.n_records) {
-                float4 A, B, C;
-                smask[tid] = stage_instance<TS>(a.rec, rid, oxh, oxl, oyh, oyl, A, B, C);
+                float4 r0, r1, r2, A, B, C;
+                load_record(a.rec, rid, r0, r1, r2);
+                stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
+                C.w = __int_as_float((int)(j - range.x + 1));
+                const CullSplat cs = cull_setup(A.x, A.y, A.z, A.w, B.x, B.z);
+#pragma unroll
+                for (int ww = 0; ww < Cfg::WARPS; ++ww)
+                    if (cull_block(cs, (float)((ww % Cfg::WGX) * 8) + 0.5f, (float)((ww / Cfg::WGX) * 8) + 0.5f))
+                        mask |= 1u << ww;
                 sA[tid] = A;
                 sB[tid] = B;
                 sC[tid] = C;
-            } else {
-                smask[tid] = 0u;
             }
+            smask[tid] = mask;
             __syncthreads();
             int cnt = 0;
 #pragma unroll
@@ -111,88 +143,61 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 cnt += __popc(bal);
             }
             __syncwarp();
-            if (!__all_sync(FULL, done0 && done1)) {
-                for (int k = 0; k < cnt; ++k) {
-                    const int jj = slist[w][k];
-                    const float4 A = sA[jj];
-                    const float4 B = sB[jj];
-                    float q0, q1;
-                    pair_q2(A.x, A.y, A.z, A.w, B.x, pxc, pyc, q0, q1);
-                    const bool h0 = !done0 && q0 <= B.z;
-                    const bool h1 = !done1 && q1 <= B.z;
-                    if (h0 || h1) {
-                        const float4 C = sC[jj];
-                        const uint32_t pos = bs + jj + 1 - range.x;
-                        if (h0) {
-                            const float al = pair_alpha(B.y, q0);
-                            const float Tn = T0 * (1.f - al);
-                            if (Tn < 1e-4f) {
-                                done0 = true;
-                                stop0 = pos;
-                            } else {
-                                ++n_blend;
-                                const float wt = al * T0;
-                                c0r = fmaf(C.x, wt, c0r);
-                                c0g = fmaf(C.y, wt, c0g);
-                                c0b = fmaf(C.z, wt, c0b);
-                                D0 = fmaf(B.w, wt, D0);
-                                T0 = Tn;
-                                last0 = pos;
-                            }
-                        }
-                        if (h1) {
-                            const float al = pair_alpha(B.y, q1);
-                            const float Tn = T1 * (1.f - al);
-                            if (Tn < 1e-4f) {
-                                done1 = true;
-                                stop1 = pos;
-                            } else {
-                                ++n_blend;
-                                const float wt = al * T1;
-                                c1r = fmaf(C.x, wt, c1r);
-                                c1g = fmaf(C.y, wt, c1g);
-                                c1b = fmaf(C.z, wt, c1b);
-                                D1 = fmaf(B.w, wt, D1);
-                                T1 = Tn;
-                                last1 = pos;
-                            }
-                        }
-                    }
+            if (!__all_sync(FULL, P0.done && P1.done)) {
+                int k = 0;
+                for (; k + 1 < cnt; k += 2) {
+                    const int j0 = slist[w][k], j1 = slist[w][k + 1];
+                    const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
+                    const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1];
+                    float q00, q01, q10, q11;
+                    pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
+                    pair_q2(A1.x, A1.y, A1.z, A1.w, B1.x, pxc, pyc, q10, q11);
+                    pix_update(P0, q00, B0, C0, n_blend);
+                    pix_update(P1, q01, B0, C0, n_blend);
+                    pix_update(P0, q10, B1, C1, n_blend);
+                    pix_update(P1, q11, B1, C1, n_blend);
+                }
+                if (k < cnt) {
+                    const int j0 = slist[w][k];
+                    const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
+                    float q00, q01;
+                    pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
+                    pix_update(P0, q00, B0, C0, n_blend);
+                    pix_update(P1, q01, B0, C0, n_blend);
                 }
             }
             __syncthreads();
         }
-        n_eval += stop0 + stop1;
+        n_eval += (in0 ? P0.stop : 0u) + (in1 ? P1.stop : 0u);
         const int64_t HW = (int64_t)V.w * V.h;
-        const int64_t pix = V.pix_base + (int64_t)py * V.w + px;
-        float *rgb = a.rgb + 3 * V.pix_base;
         const int64_t lp = (int64_t)py * V.w + px;
+        const int64_t pix = V.pix_base + lp;
+        float *rgb = a.rgb + 3 * V.pix_base;
         if (in0) {
-            rgb[lp] = c0r;
-            rgb[HW + lp] = c0g;
-            rgb[2 * HW + lp] = c0b;
-            a.depth[pix] = D0;
-            a.Tf[pix] = T0;
-            a.ncontrib[pix] = last0;
+            rgb[lp] = P0.r;
+            rgb[HW + lp] = P0.g;
+            rgb[2 * HW + lp] = P0.b;
+            a.depth[pix] = P0.D;
+            a.Tf[pix] = P0.T;
+            a.ncontrib[pix] = P0.last;
         }
         if (in1) {
-            rgb[lp + 1] = c1r;
-            rgb[HW + lp + 1] = c1g;
-            rgb[2 * HW + lp + 1] = c1b;
-            a.depth[pix + 1] = D1;
-            a.Tf[pix + 1] = T1;
-            a.ncontrib[pix + 1] = last1;
+            rgb[lp + 1] = P1.r;
+            rgb[HW + lp + 1] = P1.g;
+            rgb[2 * HW + lp + 1] = P1.b;
+            a.depth[pix + 1] = P1.D;
+            a.Tf[pix + 1] = P1.T;
+            a.ncontrib[pix + 1] = P1.last;
         }
     }
-    // algorithmic work counters: one reduction and one RED per CTA
+    // algorithmic work counters: warp sums, one shared add per warp, one RED per CTA
     const uint32_t ev = __reduce_add_sync(FULL, n_eval), bl = __reduce_add_sync(FULL, n_blend);
-    __syncthreads();
-    if (lane == 0) {
+    if (lane == 0 && (ev | bl)) {
         atomicAdd(&s_cnt[0], (unsigned long long)ev);
         atomicAdd(&s_cnt[1], (unsigned long long)bl);
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && (s_cnt[0] | s_cnt[1])) {
         atomicAdd(&a.st->pair_evals, s_cnt[0]);
         atomicAdd(&a.st->pair_blends, s_cnt[1]);
     }
@@ -250,7 +255,6 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               int persistent, int n_sms, cudaStream_t s)
 {
     FwdArgs a;
-    a.n_records = n_records;
     a.viewtab = viewtab;
     a.rec = rec;
     a.vals = vals;
@@ -262,6 +266,7 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
     a.ncontrib = ncontrib;
     a.order = order;
     a.n_tiles = n_tiles;
+    a.n_records = n_records;
     a.persistent = persistent;
     int grid = (int)n_tiles;
     cudaError_t e;
@@ -274,8 +279,10 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
         const int g = n_sms * 4;
         k_order_hist<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, st);
         k_order_scatter<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, order_tmp + kBuckets, order, st);
-        const int per_sm = vt.tile == 8 ? 16 : (vt.tile == 16 ? 8 : 2);
-        grid = (int)((int64_t)n_sms * per_sm < n_tiles ? (int64_t)n_sms * per_sm : n_tiles);
+        // one resident wave of CTAs pulling tiles
+        const int per_sm = vt.tile == 8 ? 24 : (vt.tile == 16 ? 8 : 2);
+        const int64_t ctas = (int64_t)n_sms * per_sm;
+        grid = (int)(ctas < n_tiles ? ctas : n_tiles);
     }
     if (grid <= 0) return cudaSuccess;
     switch (vt.tile) {
