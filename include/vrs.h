@@ -110,7 +110,8 @@ typedef struct {
     int32_t persistent;    /* 1 = blend every tile of every view in one persistent
                               launch, heaviest tiles first; 0 = one CTA per tile */
     int32_t backward;      /* 1 = reserve the workspace that vrs_render_bwd needs */
-    int32_t reserved;
+    int32_t sort;          /* 0 = bucket by tile, then sort each tile's bucket (default);
+                              1 = one global LSD radix sort of all keys.  Same result. */
     int64_t max_instances; /* capacity of the (tile, Gaussian) instance list; 0 = 4 x records + 65536 */
 } vrs_plan_opts;
 
@@ -137,8 +138,12 @@ typedef struct {
     int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1 */
     int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
     int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */
+    int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] big-tile
+                                  list, [ceil(n_tiles / 1024)] block sums (bucketed sort) */
     int32_t sorted_buf;        /* which ping-pong buffer holds the sorted list */
     int32_t n_sms;
+    int32_t sort_mode;         /* vrs_plan_opts.sort */
+    int32_t reserved;
     /* per scene */
     int32_t scene_n[VRS_MAX_SCENES];
     int32_t scene_deg[VRS_MAX_SCENES];
@@ -187,8 +192,12 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
                           void *workspace, void *stream);
 
 /* Step 2 (Sec. 1: tiling and sorting of all primitives).  Sorts the instances
- * by key with an 8-bit LSD radix sort over plan.key_bits bits, orders runs of
- * equal keys by record index, and writes each tile's [start, end) range.
+ * into (tile, depth, record index) order and writes each tile's [start, end)
+ * range.  plan.sort_mode 0 scans the per-tile counts taken at emission,
+ * scatters the instances into tile buckets and sorts every bucket on its own
+ * (a warp per tile of <= 256 instances, a CTA otherwise); mode 1 runs an 8-bit
+ * LSD radix sort over plan.key_bits bits and orders runs of equal keys by
+ * record index.  Both give the same list.
  * After it, the sorted keys and record indices are at
  * workspace + plan.off_keys[plan.sorted_buf] / off_vals[plan.sorted_buf]. */
 vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);

@@ -1,0 +1,116 @@
+"""Autotuner and CUDA-graph runner for batched multi-view rendering.
+
+The batched path renders every view of every scene in one launch sequence:
+one preprocess launch per scene, one sort and one blend launch for the whole
+batch.  The persistent blend pulls tiles in longest-first order, so views of
+uneven size share the GPU without tail effects.  The sequence is allocation
+and synchronisation free, so it can be captured once in a CUDA graph and
+replayed every frame.
+
+The tuner times candidate plans on the caller's own batch and caches the
+fastest under a key of (GPU name, view sizes, scene sizes):
+  - blend schedule: one CTA per tile, or the persistent longest-first grid;
+  - sort: tile buckets, or the global LSD radix sort (the key width is the
+    plan's minimal tile-id bits + 32 either way);
+  - tile edge 8 / 16 / 32 only when ``allow_tile_change`` is set, because the
+    tile size changes which splats a pixel sees (pixels also see a splat
+    beyond its 3-sigma ellipse inside the tiles it touches).
+All other choices give bit-identical images.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from .render import Rasterizer, SceneTensors
+
+CACHE_PATH = os.environ.get("VRS_AUTOTUNE_CACHE",
+                            os.path.join(os.path.expanduser("~"), ".cache", "vrs_autotune.json"))
+
+
+def _key(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: bool) -> str:
+    dev = torch.cuda.get_device_name()
+    sig = json.dumps([dev, [(v.width, v.height, v.scene) for v in views],
+                      [(s.n, s.sh_degree) for s in scenes], allow_tile_change])
+    return hashlib.sha1(sig.encode()).hexdigest()
+
+
+class GraphRunner:
+    """Captures Rasterizer.forward_async in a CUDA graph and replays it."""
+
+    def __init__(self, ras: Rasterizer, warmup: int = 2):
+        self.ras = ras
+        ras.forward()                       # sizes the instance list outside the capture
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                ras.forward_async()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            ras.forward_async()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+
+
+def time_ms(fn, iters: int = 20, warmup: int = 3) -> float:
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def candidates(allow_tile_change: bool, tile: int = 16) -> List[Dict]:
+    tiles = (8, 16, 32) if allow_tile_change else (tile,)
+    return [dict(tile=t, persistent=p, sort=s) for t, p, s in itertools.product(tiles, (0, 1), (0, 1))]
+
+
+def tune(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: bool = False,
+         tile: int = 16, iters: int = 10, use_cache: bool = True, verbose: bool = False) -> Dict:
+    """Returns the fastest {tile, persistent, sort} for this batch (cached)."""
+    key = _key(scenes, views, allow_tile_change)
+    cache = {}
+    if use_cache and os.path.exists(CACHE_PATH):
+        try:
+            with open(CACHE_PATH) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        return cache[key]["best"]
+    results = []
+    for c in candidates(allow_tile_change, tile):
+        ras = Rasterizer(scenes, views, **c)
+        runner = GraphRunner(ras)
+        ms = time_ms(runner.replay, iters=iters)
+        results.append((ms, c))
+        if verbose:
+            print(f"autotune {c}: {ms:.4f} ms")
+        del runner, ras
+    results.sort(key=lambda x: x[0])
+    best = results[0][1]
+    if use_cache:
+        cache[key] = {"best": best, "timings": [(ms, c) for ms, c in results]}
+        try:
+            os.makedirs(os.path.dirname(CACHE_PATH), exist_ok=True)
+            with open(CACHE_PATH, "w") as f:
+                json.dump(cache, f)
+        except OSError:
+            pass
+    return best

@@ -5,13 +5,18 @@
 
 namespace vrs {
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8_t *views, int n_views,
-                              float4 *rec, unsigned long long *keys, uint32_t *vals, DevStatus *st,
-                              unsigned long long cap, cudaStream_t stream);
+                              float4 *rec, unsigned long long *keys, uint32_t *vals, uint32_t *tile_cnt,
+                              DevStatus *st, unsigned long long cap, cudaStream_t stream);
 cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream);
 cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
                         uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
                         int64_t n_tiles, const DevStatus *st, unsigned long long cap, int passes, int G,
                         int n_sms, cudaStream_t stream);
+cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *vals_in,
+                             unsigned long long *bucket, unsigned long long *keys_out, uint32_t *vals_out,
+                             const uint32_t *cnt, uint32_t *cursor, uint32_t *blocksum, uint32_t *big_list,
+                             uint2 *ranges, DevStatus *st, unsigned long long cap, int64_t n_tiles,
+                             int n_sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
@@ -136,6 +141,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     const int tile = o.tile == 0 ? 16 : o.tile;
     if (tile != 8 && tile != 16 && tile != 32) return VRS_ERR_INVALID;
     if (o.max_instances < 0) return VRS_ERR_INVALID;
+    if (o.sort != 0 && o.sort != 1) return VRS_ERR_INVALID;
     vrs_plan P;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
@@ -143,6 +149,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.tile = tile;
     P.persistent = o.persistent ? 1 : 0;
     P.backward = o.backward ? 1 : 0;
+    P.sort_mode = o.sort;
     for (int s = 0; s < n_scenes; ++s) {
         if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
         P.scene_n[s] = scenes[s].n;
@@ -171,7 +178,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.n_pixels = pix;
     P.key_bits = 32 + bits_for(tiles);
     P.sort_passes = (P.key_bits + 7) / 8;
-    P.sorted_buf = P.sort_passes % 2;
+    P.sorted_buf = P.sort_mode == 0 ? 0 : P.sort_passes % 2;
     int64_t cap = o.max_instances > 0 ? o.max_instances : 4 * rec + 65536;
     if (cap > ((int64_t)1 << 31)) cap = (int64_t)1 << 31;
     P.max_instances = cap;
@@ -201,6 +208,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.off_ncontrib = take(pix * 4);
     P.off_order = take((tiles + kOrderTmp) * 4);
     P.off_grad2d = P.backward ? take(rec * kGrad2D * 4) : 0;
+    P.off_tilesort = take((3 * tiles + (tiles + 1023) / 1024) * 4);
     P.workspace_bytes = off;
     *plan = P;
     return VRS_OK;
@@ -224,13 +232,19 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
     if (e != cudaSuccess) return VRS_ERR_CUDA;
     e = launch_write_viewtab(vt, viewtab, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
+    uint32_t *tile_cnt = nullptr;
+    if (plan->sort_mode == 0) {
+        tile_cnt = at<uint32_t>(workspace, plan->off_tilesort);
+        e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)plan->n_tiles, s);
+        if (e != cudaSuccess) return VRS_ERR_CUDA;
+    }
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];
         const int nv = views_of_scene(plan, sc, vlist);
         e = launch_preprocess(vt, dev_scene(scenes[sc]), vlist, nv,
                               at<float4>(workspace, plan->off_records),
                               at<unsigned long long>(workspace, plan->off_keys[0]),
-                              at<uint32_t>(workspace, plan->off_vals[0]), st,
+                              at<uint32_t>(workspace, plan->off_vals[0]), tile_cnt, st,
                               (unsigned long long)plan->max_instances, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
     }
@@ -240,6 +254,17 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
 vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream)
 {
     if (!plan || !workspace) return VRS_ERR_INVALID;
+    if (plan->sort_mode == 0) {
+        uint32_t *ts = at<uint32_t>(workspace, plan->off_tilesort);
+        const int64_t nt = plan->n_tiles;
+        cudaError_t e = launch_tile_sort(
+            at<unsigned long long>(workspace, plan->off_keys[0]), at<uint32_t>(workspace, plan->off_vals[0]),
+            at<unsigned long long>(workspace, plan->off_keys[1]), at<unsigned long long>(workspace, plan->off_keys[0]),
+            at<uint32_t>(workspace, plan->off_vals[0]), ts, ts + nt, ts + 3 * nt, ts + 2 * nt,
+            at<uint2>(workspace, plan->off_ranges), at<DevStatus>(workspace, plan->off_status),
+            (unsigned long long)plan->max_instances, nt, plan->n_sms, static_cast<cudaStream_t>(stream));
+        return cuda_status(e);
+    }
     uint32_t *hist = at<uint32_t>(workspace, plan->off_hist);
     cudaError_t e = launch_sort(at<unsigned long long>(workspace, plan->off_keys[0]),
                                 at<uint32_t>(workspace, plan->off_vals[0]),

@@ -15,6 +15,7 @@ struct PreParams {
     float4 *rec;
     unsigned long long *keys;
     uint32_t *vals;
+    uint32_t *tile_cnt;              // nullable: instances per tile (bucketed sort)
     DevStatus *st;
     unsigned long long cap;
 };
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
                 if (pos < p.cap) {
                     p.keys[pos] = (tid << 32) | odb;
                     p.vals[pos] = orid;
+                    if (p.tile_cnt) atomicAdd(p.tile_cnt + tid, 1u);
                 }
             }
         }
@@ -235,7 +237,8 @@ cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStrea
 // that a Gaussian's coefficients stay in registers across its views).
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8_t *views,
                               int n_views, float4 *rec, unsigned long long *keys, uint32_t *vals,
-                              DevStatus *st, unsigned long long cap, cudaStream_t stream)
+                              uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
+                              cudaStream_t stream)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     PreParams p;
@@ -245,6 +248,7 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8
     p.rec = rec;
     p.keys = keys;
     p.vals = vals;
+    p.tile_cnt = tile_cnt;
     p.st = st;
     p.cap = cap;
     const int block = 128;

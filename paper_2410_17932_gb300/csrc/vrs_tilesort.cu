@@ -1,0 +1,305 @@
+// Step 2, bucketed form (the default): the (tile, depth) instances are grouped
+// by tile and each tile's bucket is sorted on its own (Sec. 1: tiling and
+// sorting all primitives).  vrs_preprocess already counted every tile's
+// instances while emitting them; here
+//   k_tile_blocksum, k_tile_scan   exclusive scan of the counts -> tile ranges
+//   k_tile_scatter                 each instance into its tile's bucket as the
+//                                  composite (depth bits << 32 | record index)
+//   k_tile_sort_small              one warp per tile of <= 256 instances: a
+//                                  bitonic network in registers and shuffles
+//   k_tile_sort_big                larger tiles, one CTA each: a bitonic network
+//                                  in shared memory up to 4096, beyond that
+//                                  sorted 4096-runs merged in global memory
+// Sorting the composite orders equal depths by record index, so the result is
+// the unique (tile, depth, record) order and matches the radix path bit for bit.
+#include "vrs_internal.cuh"
+
+namespace vrs {
+
+constexpr int kScanBlock = 1024;
+constexpr int kSmallMax = 256;
+constexpr int kBigChunk = 4096;
+constexpr int kBigThreads = 256;
+
+struct TileSortArgs {
+    const unsigned long long *keys_in;   // emitted keys (tile << 32 | depth bits)
+    const uint32_t *vals_in;             // emitted record indices
+    unsigned long long *bucket;          // [cap] composites
+    unsigned long long *keys_out;        // sorted keys (may alias keys_in)
+    uint32_t *vals_out;                  // sorted record indices (may alias vals_in)
+    const uint32_t *cnt;                 // [n_tiles] instances per tile
+    uint32_t *cursor;                    // [n_tiles]
+    uint32_t *blocksum;                  // [ceil(n_tiles / kScanBlock)]
+    uint32_t *big_list;                  // [n_tiles]
+    uint2 *ranges;                       // [n_tiles]
+    DevStatus *st;
+    unsigned long long cap;
+    int64_t n_tiles;
+};
+
+__device__ __forceinline__ uint32_t live_instances(const DevStatus *st, unsigned long long cap)
+{
+    if (st->flags & ST_CAPACITY) return 0u;
+    const unsigned long long n = st->instances;
+    return (uint32_t)(n < cap ? n : cap);
+}
+
+__device__ __forceinline__ uint32_t block_sum1024(uint32_t v, uint32_t *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    uint32_t s = 0;
+    if (w == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+        s = __reduce_add_sync(0xffffffffu, s);
+    }
+    __syncthreads();
+    return s;   // valid in warp 0
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_tile_blocksum(const TileSortArgs a)
+{
+    __shared__ uint32_t sh[32];
+    if (live_instances(a.st, a.cap) == 0) return;
+    const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const uint32_t v = t < a.n_tiles ? a.cnt[t] : 0u;
+    const uint32_t s = block_sum1024(v, sh);
+    if (threadIdx.x == 0) a.blocksum[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a)
+{
+    __shared__ uint32_t sh[32];
+    __shared__ uint32_t base_s;
+    if (live_instances(a.st, a.cap) == 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // prefix of the block sums of the blocks before this one
+    uint32_t p = 0;
+    for (uint32_t b = threadIdx.x; b < blockIdx.x; b += kScanBlock) p += a.blocksum[b];
+    p = block_sum1024(p, sh);
+    if (threadIdx.x == 0) base_s = p;
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const uint32_t v = t < a.n_tiles ? a.cnt[t] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    uint32_t wo = 0;
+    for (int i = 0; i < w; ++i) wo += sh[i];
+    const uint32_t off = base_s + wo + x - v;
+    if (t < a.n_tiles) {
+        a.ranges[t] = v ? make_uint2(off, off + v) : make_uint2(0u, 0u);
+        a.cursor[t] = off;
+        if (v > (uint32_t)kSmallMax) a.big_list[atomicAdd(&a.st->work[1], 1u)] = (uint32_t)t;
+    }
+}
+
+__global__ void k_tile_scatter(const TileSortArgs a)
+{
+    const uint32_t M = live_instances(a.st, a.cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        const unsigned long long key = a.keys_in[i];
+        const uint32_t t = (uint32_t)(key >> 32);
+        if ((int64_t)t >= a.n_tiles) continue;   // cannot happen for keys from vrs_preprocess
+        const uint32_t pos = atomicAdd(&a.cursor[t], 1u);
+        a.bucket[pos] = (key << 32) | (unsigned long long)a.vals_in[i];
+    }
+}
+
+__device__ __forceinline__ void cmp_swap(unsigned long long &x, unsigned long long &y, bool asc)
+{
+    const unsigned long long lo = x < y ? x : y, hi = x < y ? y : x;
+    x = asc ? lo : hi;
+    y = asc ? hi : lo;
+}
+
+// Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i].
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lane)
+{
+    constexpr int P = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int ji = j >> 5;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    if ((i & ji) == 0) {
+                        const int e = i * 32 + lane;
+                        cmp_swap(v[i], v[i | ji], (e & k) == 0);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int e = i * 32 + lane;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], j);
+                    const bool asc = (e & k) == 0, lower = (lane & j) == 0;
+                    const bool take_min = lower == asc;
+                    v[i] = take_min ? (v[i] < o ? v[i] : o) : (v[i] < o ? o : v[i]);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_tile(const TileSortArgs &a, uint32_t t, uint32_t start, uint32_t n,
+                                               int lane)
+{
+    unsigned long long v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const uint32_t e = i * 32 + lane;
+        v[i] = e < n ? a.bucket[start + e] : ~0ull;
+    }
+    warp_bitonic<E>(v, lane);
+    const unsigned long long th = (unsigned long long)t << 32;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const uint32_t e = i * 32 + lane;
+        if (e < n) {
+            a.keys_out[start + e] = th | (v[i] >> 32);
+            a.vals_out[start + e] = (uint32_t)v[i];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_tile_sort_small(const TileSortArgs a)
+{
+    if (live_instances(a.st, a.cap) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (t >= a.n_tiles) return;
+    const uint32_t n = a.cnt[t];
+    if (n == 0 || n > (uint32_t)kSmallMax) return;   // empty, or sorted by k_tile_sort_big
+    const uint32_t start = a.ranges[t].x;
+    if (n <= 32) warp_sort_tile<1>(a, (uint32_t)t, start, n, lane);
+    else if (n <= 64) warp_sort_tile<2>(a, (uint32_t)t, start, n, lane);
+    else if (n <= 128) warp_sort_tile<4>(a, (uint32_t)t, start, n, lane);
+    else warp_sort_tile<8>(a, (uint32_t)t, start, n, lane);
+}
+
+// Bitonic sort of P (a power of two <= kBigChunk) composites in shared memory.
+__device__ void block_bitonic(unsigned long long *s, uint32_t P)
+{
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t e = threadIdx.x; e < P; e += blockDim.x) {
+                const uint32_t o = e ^ j;
+                if (o > e) {
+                    unsigned long long x = s[e], y = s[o];
+                    cmp_swap(x, y, (e & k) == 0);
+                    s[e] = x;
+                    s[o] = y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Merges sorted src[0, la) and src[la, la + lb) into dst (merge path; one CTA).
+__device__ void block_merge(const unsigned long long *src, uint32_t la, uint32_t lb, unsigned long long *dst)
+{
+    const unsigned long long *A = src, *B = src + la;
+    const uint32_t total = la + lb;
+    const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
+    const uint32_t d0 = min(total, threadIdx.x * per), d1 = min(total, d0 + per);
+    if (d0 >= d1) return;
+    // split point of diagonal d0: number of elements taken from A
+    uint32_t lo = d0 > lb ? d0 - lb : 0u, hi = min(d0, la);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    uint32_t i = lo, j = d0 - lo;
+    for (uint32_t d = d0; d < d1; ++d) {
+        const bool takeA = j >= lb || (i < la && A[i] <= B[j]);
+        dst[d] = takeA ? A[i++] : B[j++];
+    }
+}
+
+__global__ void __launch_bounds__(kBigThreads) k_tile_sort_big(const TileSortArgs a)
+{
+    __shared__ unsigned long long s[kBigChunk];
+    __shared__ uint32_t s_idx;
+    if (live_instances(a.st, a.cap) == 0) return;
+    const uint32_t n_big = a.st->work[1];
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[2], 1u);
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        __syncthreads();
+        if (idx >= n_big) break;
+        const uint32_t t = a.big_list[idx];
+        const uint32_t start = a.ranges[t].x, n = a.cnt[t];
+        unsigned long long *bk = a.bucket + start;
+        unsigned long long *tmp = a.keys_out + start;   // scratch until the final write
+        // sorted runs of kBigChunk in the bucket
+        for (uint32_t c0 = 0; c0 < n; c0 += kBigChunk) {
+            const uint32_t m = min((uint32_t)kBigChunk, n - c0);
+            uint32_t P = 32;
+            while (P < m) P <<= 1;
+            for (uint32_t e = threadIdx.x; e < P; e += blockDim.x) s[e] = e < m ? bk[c0 + e] : ~0ull;
+            __syncthreads();
+            block_bitonic(s, P);
+            for (uint32_t e = threadIdx.x; e < m; e += blockDim.x) bk[c0 + e] = s[e];
+            __syncthreads();
+        }
+        // pairwise merges, bucket <-> scratch
+        unsigned long long *src = bk, *dst = tmp;
+        for (uint32_t width = kBigChunk; width < n; width <<= 1) {
+            for (uint32_t r0 = 0; r0 < n; r0 += 2 * width) {
+                const uint32_t la = min(width, n - r0);
+                const uint32_t lb = min(width, n - r0 - la);
+                block_merge(src + r0, la, lb, dst + r0);
+            }
+            __syncthreads();
+            unsigned long long *x = src;
+            src = dst;
+            dst = x;
+        }
+        // split the composites into the sorted key and record-index lists (in place
+        // when the result is already in the key list: every thread reads, then writes,
+        // the same element)
+        const unsigned long long th = (unsigned long long)t << 32;
+        for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const unsigned long long c = src[e];
+            a.keys_out[start + e] = th | (c >> 32);
+            a.vals_out[start + e] = (uint32_t)c;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *vals_in,
+                             unsigned long long *bucket, unsigned long long *keys_out, uint32_t *vals_out,
+                             const uint32_t *cnt, uint32_t *cursor, uint32_t *blocksum, uint32_t *big_list,
+                             uint2 *ranges, DevStatus *st, unsigned long long cap, int64_t n_tiles,
+                             int n_sms, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    TileSortArgs a{keys_in, vals_in, bucket, keys_out, vals_out, cnt, cursor, blocksum, big_list,
+                   ranges, st, cap, n_tiles};
+    cudaError_t e = cudaMemsetAsync(&st->work[1], 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((n_tiles + kScanBlock - 1) / kScanBlock);
+    k_tile_blocksum<<<nb, kScanBlock, 0, s>>>(a);
+    k_tile_scan<<<nb, kScanBlock, 0, s>>>(a);
+    k_tile_scatter<<<n_sms * 8, 256, 0, s>>>(a);
+    k_tile_sort_small<<<(unsigned)((n_tiles + 3) / 4), 128, 0, s>>>(a);
+    k_tile_sort_big<<<n_sms * 2, kBigThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace vrs

@@ -86,13 +86,14 @@ class Rasterizer:
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
                  persistent: bool = False, backward: bool = False, max_instances: int = 0,
-                 device="cuda"):
+                 sort: int = 0, device="cuda"):
         self.scenes = list(scenes)
         self.views = list(views)
         self.device = torch.device(device)
         self.tile = tile
         self.persistent = bool(persistent)
         self.backward = bool(backward)
+        self.sort = int(sort)
         self._make_plan(max_instances)
 
     # -- planning ------------------------------------------------------------------------
@@ -100,7 +101,8 @@ class Rasterizer:
         n_s, n_v = len(self.scenes), len(self.views)
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
-        opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), 0, int(max_instances))
+        opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), self.sort,
+                               int(max_instances))
         plan = L.vrs_plan()
         L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
         self.plan = plan

@@ -167,3 +167,32 @@ def test_invalid_arguments_rejected_on_host():
     assert L.vrs_preprocess(ras.plan, ras._scene_arr, arr, ras.workspace.data_ptr(), 0) == L.VRS_ERR_INVALID
     assert L.vrs_preprocess(ras.plan, ras._scene_arr, ras._view_arr, ras.workspace.data_ptr() + 8, 0) \
         == L.VRS_ERR_INVALID
+
+
+@pytest.mark.parametrize("n", [300, 3000, 20000])
+def test_bucketed_sort_crowded_tiles(n):
+    """n splats stacked on four tiles: the warp, shared-memory and merge paths of the bucketed sort."""
+    torch = torch_cuda()
+    sc = I.uniform_box_scene(n, 90 + n, xy=(-0.01, 0.01), z=(2.0, 6.0), log_scale=(-6.0, 0.2))
+    cam = I.identity_camera(64, 64, 200.0)
+    a = _run([sc], [cam], sort=0)
+    bs = _check_sort(a, [sc], [cam])
+    assert (bs["ranges"][:, 1] - bs["ranges"][:, 0]).max() >= n
+    b = _run([sc], [cam], sort=1)
+    _check_sort(b, [sc], [cam])
+    assert torch.equal(a.rgb, b.rgb) and torch.equal(a.depth, b.depth) and torch.equal(a.T, b.T)
+    rgb, depth, T = [x.cpu().numpy() for x in a.outputs(0)]
+    compare_images((rgb, depth, T), oracle.render(sc, cam), f"crowded{n}")
+
+
+def test_radix_and_bucketed_sorts_agree_multiview():
+    torch = torch_cuda()
+    s0 = I.uniform_box_scene(4000, 51, sh_degree=2)
+    views = [I.identity_camera(120, 96, 110.0), I.Camera(I._yaw_pitch(0.1, 0.0), [0.0, 0.0, 0.2], 90.0, 90.0,
+                                                         40.0, 50.0, 88, 104)]
+    a = _run([s0], views, sort=0)
+    b = _run([s0], views, sort=1)
+    ka, va, ra = a.sorted_lists()
+    kb, vb, rb = b.sorted_lists()
+    assert torch.equal(ka, kb) and torch.equal(va, vb) and torch.equal(ra, rb)
+    _check_sort(a, [s0], views)
