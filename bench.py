@@ -36,8 +36,14 @@ WORKLOADS = {
     "periphery_stereo_05m": "stereo frame 2016x2240/eye, 0.5M SH-3 Gaussians, clustered room",
     "dense_stereo_3m": "stereo frame 2016x2240/eye + 2 x 512x512 foveal crops, 3M SH-3 Gaussians",
 }
-ALU_OPS_SKIP = 15      # FP32 ops per evaluated Gaussian-pixel pair (definition: power, exp, clamp, test)
-ALU_OPS_BLEND = 10     # extra FP32 ops per blended pair (T update, stop test, 3 colour + 1 depth FMA)
+# FP32 lane-ops a blended Gaussian-pixel pair needs by the definition: offset and
+# quadratic form (11), exp, opacity and clamp (3), skip test (1), then the T
+# update, stop test and weight (4), three colour and one depth FMA (4), plus the
+# running-T and last-position bookkeeping (2).  Pairs that do not change a pixel
+# are not counted, so the fraction is the share of the FP32 issue peak spent on
+# pixel-changing work (culling and early exit raise it; evaluating pairs that
+# cannot contribute lowers it).
+ALU_OPS_PER_BLEND = 25
 
 
 def load_workload(name):
@@ -195,6 +201,88 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------------------------
+# The other workloads, reported beside the headline
+
+def _time_loop(fn, flush, iters):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record()
+        fn()
+        e1.record()
+    torch.cuda.synchronize()
+    return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+
+
+def run_extras(args):
+    import torch
+    from paper_2410_17932_gb300 import autotune
+    from paper_2410_17932_gb300 import inputs as I
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    # dense stereo frame, 3 M Gaussians, two eyes + two 512x512 foveal crops (forward)
+    scenes, views = I.dense_stereo_3m()
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    ras = Rasterizer(sts, views)
+    ras.forward()
+    for _ in range(3):
+        ras.forward_async()
+    out["dense_stereo_3m_ms_per_frame"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+    out["dense_stereo_3m_instances"] = ras.last_status[2]
+    del ras, sts
+    # training step: forward + backward of one 1264x832 view over 1 M Gaussians
+    scenes, views = I.training_view_1m()
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    ras = Rasterizer(sts, views, backward=True)
+    ras.forward()
+    g = I.upstream_grads(views, 7)[0]
+    gC = torch.as_tensor(g[0].reshape(-1), device="cuda")
+    gD = torch.as_tensor(g[1].reshape(-1), device="cuda")
+    grads = [s.zeros_like() for s in sts]
+
+    def step():
+        ras.forward_async()
+        ras.backward_params(gC, gD, None, grads)
+
+    for _ in range(3):
+        step()
+    out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(step, flush, args.extra_steps), 4)
+    out["training_view_1m_fwd_ms"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+    del ras, sts, grads
+    # 32 views of uneven size over 4 scenes: batched persistent under a CUDA graph vs per-view launches
+    scenes, views = I.batched_multiview()
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    best = autotune.tune(sts, views, iters=5, use_cache=False)
+    batched = Rasterizer(sts, views, **best)
+    runner = autotune.GraphRunner(batched)
+    ms_batched = _time_loop(runner.replay, flush, args.extra_steps)
+    singles = []
+    for cam in views:
+        c1 = I.Camera(cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.znear, 0,
+                      cam.tan_fovx, cam.tan_fovy)
+        r = Rasterizer([sts[cam.scene]], [c1], tile=best["tile"])
+        r.forward()
+        singles.append(r)
+
+    def per_view():
+        for r in singles:
+            r.forward_async()
+
+    for _ in range(2):
+        per_view()
+    ms_per_view = _time_loop(per_view, flush, max(3, args.extra_steps // 4))
+    same = all(torch.equal(x, y) for v, r in enumerate(singles)
+               for x, y in zip(batched.outputs(v), r.outputs(0)))
+    out["batched_32_views"] = {"batched_graph_ms": round(ms_batched, 4), "per_view_launches_ms": round(ms_per_view, 4),
+                               "speedup": round(ms_per_view / ms_batched, 3), "autotuned": best,
+                               "identical_images": bool(same),
+                               "pixels": int(batched.plan.n_pixels), "instances": int(batched.last_status[2])}
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 
 def main():
     ap = argparse.ArgumentParser()
@@ -210,6 +298,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-extras", action="store_true", help="skip the 3M, training and 32-view runs")
+    ap.add_argument("--extra-steps", type=int, default=20)
+    ap.add_argument("--blend-traffic", type=float, default=None,
+                    help="DRAM bytes per blend launch from an ncu capture of the current kernel")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -230,10 +322,7 @@ def main():
     ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent)
     ras.forward()                       # sizes the instance list
     code, flags, inst = ras.last_status
-    from paper_2410_17932_gb300 import _lib as L
-    info = L.vrs_run_info()
-    L.vrs_query_status(ras.plan, ras.workspace.data_ptr(), info, torch.cuda.current_stream().cuda_stream)
-    pair_evals, pair_blends = int(info.pair_evals), int(info.pair_blends)
+    pair_evals, pair_blends = ras.count_pairs()   # algorithmic units, one untimed counting pass
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -283,14 +372,16 @@ def main():
     dominant = max(stage, key=stage.get)
     p = ras.plan
     if dominant == "render_fwd":
-        ops = ALU_OPS_SKIP * pair_evals + ALU_OPS_BLEND * pair_blends
+        ops = ALU_OPS_PER_BLEND * pair_blends
         peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12   # T lane-ops/s
         achieved = ops / (stage["render_fwd"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_render_fwd<16>", "achieved": round(achieved, 3),
+        roof = {"bound": "alu", "kernel": f"k_render_fwd<{int(p.tile)}>", "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4),
-                "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} clock)",
-                "units": f"{pair_evals} Gaussian-pixel evaluations, {pair_blends} blended"}
+                "traffic": args.blend_traffic,
+                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
+                "units": f"{pair_blends} blended Gaussian-pixel pairs x {ALU_OPS_PER_BLEND} ops",
+                "context": {"definitional_evaluations": pair_evals,
+                            "evaluations_per_s": round(pair_evals / (stage['render_fwd'] * 1e-3), 1)}}
     else:
         n = sum(s.n for s in scenes)
         if dominant == "preprocess":
@@ -340,7 +431,14 @@ def main():
                "sample": f"decide+project+tile lists over all Gaussians; FP64 compositing on {sampled} "
                          f"of {nt} tiles, extrapolated by tile count"}
 
-    launches_per_step = (1 + len(scenes)) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
+    extra = None
+    if rank == 0 and not args.no_extras:
+        extra = run_extras(args)
+
+    if p.sort_mode == 0:
+        launches_per_step = (1 + len(scenes)) + 5 + (3 if p.persistent else 1)
+    else:
+        launches_per_step = (1 + len(scenes)) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
     if rank == 0:
         line = {
             "metric": "ms per stereo frame @2016x2240/eye (0.5M SH-3 Gaussians)",
@@ -357,6 +455,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * K,
+            "extra": extra,
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }

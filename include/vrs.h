@@ -113,6 +113,9 @@ typedef struct {
     int32_t sort;          /* 0 = bucket by tile, then sort each tile's bucket (default);
                               1 = one global LSD radix sort of all keys.  Same result. */
     int64_t max_instances; /* capacity of the (tile, Gaussian) instance list; 0 = 4 x records + 65536 */
+    int32_t count_pairs;   /* 1 = vrs_render_fwd also counts the Gaussian-pixel pairs it evaluated
+                              and blended into the status block (a slower, measuring variant) */
+    int32_t reserved;
 } vrs_plan_opts;
 
 /* Sizes and workspace layout, filled by vrs_plan_batch.  Treat as read-only. */
@@ -143,7 +146,7 @@ typedef struct {
     int32_t sorted_buf;        /* which ping-pong buffer holds the sorted list */
     int32_t n_sms;
     int32_t sort_mode;         /* vrs_plan_opts.sort */
-    int32_t reserved;
+    int32_t count_pairs;       /* vrs_plan_opts.count_pairs; may be toggled between calls */
     /* per scene */
     int32_t scene_n[VRS_MAX_SCENES];
     int32_t scene_deg[VRS_MAX_SCENES];
@@ -163,9 +166,10 @@ typedef struct {
     uint32_t reserved;
     uint64_t instances;        /* tile instances requested by the last vrs_preprocess
                                   (may exceed max_instances on overflow) */
-    uint64_t pair_evals;       /* Gaussian-pixel pairs the last vrs_render_fwd evaluated by
-                                  definition: per pixel, its tile-list position where it
-                                  stopped, else the list length */
+    uint64_t pair_evals;       /* with plan.count_pairs: Gaussian-pixel pairs vrs_render_fwd
+                                  evaluated by definition since the last vrs_preprocess (per
+                                  pixel, its tile-list position where it stopped, else the list
+                                  length) */
     uint64_t pair_blends;      /* of those, pairs that were blended */
 } vrs_run_info;
 

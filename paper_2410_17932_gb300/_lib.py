@@ -37,7 +37,7 @@ class vrs_camera(ctypes.Structure):
 
 class vrs_plan_opts(ctypes.Structure):
     _fields_ = [("tile", _i32), ("persistent", _i32), ("backward", _i32), ("sort", _i32),
-                ("max_instances", _i64)]
+                ("max_instances", _i64), ("count_pairs", _i32), ("reserved", _i32)]
 
 
 class vrs_plan(ctypes.Structure):
@@ -49,7 +49,7 @@ class vrs_plan(ctypes.Structure):
                 ("off_vals", _i64 * 2), ("off_hist", _i64), ("off_ranges", _i64),
                 ("off_ncontrib", _i64), ("off_order", _i64), ("off_grad2d", _i64),
                 ("off_tilesort", _i64), ("sorted_buf", _i32), ("n_sms", _i32), ("sort_mode", _i32),
-                ("reserved", _i32),
+                ("count_pairs", _i32),
                 ("scene_n", _i32 * VRS_MAX_SCENES), ("scene_deg", _i32 * VRS_MAX_SCENES),
                 ("view_scene", _i32 * VRS_MAX_VIEWS), ("view_w", _i32 * VRS_MAX_VIEWS),
                 ("view_h", _i32 * VRS_MAX_VIEWS), ("view_gw", _i32 * VRS_MAX_VIEWS),

@@ -21,12 +21,13 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              int persistent, int n_sms, cudaStream_t s);
+                              unsigned long long cap, int persistent, int count, int n_sms,
+                              cudaStream_t s);
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
                               const float *dL_ddepth, const float *dL_dT, float *grad2d,
-                              int64_t n_tiles, int64_t n_records, cudaStream_t s);
+                              int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d,
                                    const DevStatus *st, cudaStream_t s);
@@ -150,6 +151,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.persistent = o.persistent ? 1 : 0;
     P.backward = o.backward ? 1 : 0;
     P.sort_mode = o.sort;
+    P.count_pairs = o.count_pairs ? 1 : 0;
     for (int s = 0; s < n_scenes; ++s) {
         if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
         P.scene_n[s] = scenes[s].n;
@@ -291,7 +293,8 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         at<uint32_t>(workspace, plan->off_vals[sb]), at<uint2>(workspace, plan->off_ranges),
         at<DevStatus>(workspace, plan->off_status), rgb, depth, T_final,
         at<uint32_t>(workspace, plan->off_ncontrib), order, order + plan->n_tiles, plan->n_tiles,
-        plan->n_records, plan->persistent, plan->n_sms, static_cast<cudaStream_t>(stream));
+        plan->n_records, (unsigned long long)plan->max_instances, plan->persistent, plan->count_pairs,
+        plan->n_sms, static_cast<cudaStream_t>(stream));
     return cuda_status(e);
 }
 
@@ -324,7 +327,7 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
                           at<uint32_t>(workspace, plan->off_vals[plan->sorted_buf]),
                           at<uint2>(workspace, plan->off_ranges), st,
                           at<uint32_t>(workspace, plan->off_ncontrib), T_final, dL_drgb, dL_ddepth,
-                          dL_dT, g2, plan->n_tiles, plan->n_records, s);
+                          dL_dT, g2, plan->n_tiles, plan->n_records, (unsigned long long)plan->max_instances, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];

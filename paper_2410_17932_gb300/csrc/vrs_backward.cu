@@ -33,6 +33,7 @@ struct BwdArgs {
     const float *g_T;        // nullable
     float *grad2d;
     int64_t n_records;
+    unsigned long long cap;
 };
 
 constexpr float kInvChol2 = 1.0f / (kCholScale * kCholScale);   // 2 / log2(e)
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     float oxh, oxl, oyh, oyl;
     tile_origin((float)(tx * TS), pp.x, oxh, oxl);
     tile_origin((float)(ty * TS), pp.y, oyh, oyl);
-    const uint2 range = a.ranges[t];
+    const uint2 range = live_range(a.ranges, t, a.st, a.cap);
 
     const int64_t HW = (int64_t)V.w * V.h;
     const int64_t lp = (int64_t)py * V.w + px;
@@ -202,9 +203,9 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
                               const float *dL_ddepth, const float *dL_dT, float *grad2d,
-                              int64_t n_tiles, int64_t n_records, cudaStream_t s)
+                              int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s)
 {
-    BwdArgs a{viewtab, rec, vals, ranges, st, ncontrib, Tf, dL_drgb, dL_ddepth, dL_dT, grad2d, n_records};
+    BwdArgs a{viewtab, rec, vals, ranges, st, ncontrib, Tf, dL_drgb, dL_ddepth, dL_dT, grad2d, n_records, cap};
     if (n_tiles <= 0) return cudaSuccess;
     switch (vt.tile) {
         case 8: return launch_bwd_ts<8>(vt, a, n_tiles, s);

@@ -544,6 +544,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// A tile's [start, end) clamped to the live instance list, so that no range
+// value can send a gather outside the list.
+__device__ __forceinline__ uint2 live_range(const uint2 *ranges, int64_t t, const DevStatus *st,
+                                            unsigned long long cap)
+{
+    const unsigned long long n = st->instances;
+    const uint32_t m = (uint32_t)(n < cap ? n : cap);
+    uint2 r = ranges[t];
+    r.y = min(r.y, m);
+    r.x = min(r.x, r.y);
+    return r;
+}
+
 // Launch helpers (host).
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 

@@ -20,47 +20,67 @@ struct PreParams {
     unsigned long long cap;
 };
 
-// Rows of SH coefficients that are a whole number of 16-byte chunks (degree 1
-// and 3) are bulk-copied (TMA, cp.async.bulk) into padded shared-memory rows
-// at kernel start and read only for the colour, so the copies overlap the
-// FP32 decision path; other degrees are loaded into registers.
+// Per CTA of 128 Gaussians: (1) the coefficient rows are staged in shared
+// memory, by one bulk copy (TMA, cp.async.bulk) per row when a row is a whole
+// number of 16-byte chunks (SH degree 1 and 3) and by plain loads otherwise,
+// so the copies overlap the FP32 decision path; (2) per view, every lane takes
+// its Gaussian's integer decisions and the warp emits the tile keys; the
+// visible (Gaussian, view) pairs are queued in shared memory; (3) the queue is
+// drained densely, one pair per thread, to write the projected records.
+// Only about a quarter of the pairs of a VR view are visible, so draining a
+// compacted queue instead of running the record math in every warp with a
+// visible lane cuts the issued instructions several-fold.
 template <int K>
 struct ShStage {
     static constexpr bool kBulk = (12 * K) % 16 == 0;
-    static constexpr int kRow = kBulk ? 3 * K + 4 : 4;          // padded row (floats): 52 for SH-3
-    static constexpr int kFloats = kBulk ? 128 * kRow : 4;
+    static constexpr int kRow = kBulk ? 3 * K + 4 : 3 * K + 1;   // padded row (floats): 52 for SH-3
 };
 
 constexpr uint32_t kBulkWaitIters = 1u << 22;
+constexpr int kPreThreads = 128;
+constexpr int kViewChunk = 4;                       // views per queue round
+constexpr int kQueue = kPreThreads * kViewChunk;
+
+struct PreItem {
+    float n1, b, det, tz;
+};
 
 template <int K>
-__global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ ViewTable vt,
-                                                    const __grid_constant__ PreParams p)
+__global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constant__ ViewTable vt,
+                                                            const __grid_constant__ PreParams p)
 {
     using SS = ShStage<K>;
-    __shared__ __align__(16) float sh_s[SS::kFloats];
+    __shared__ __align__(16) float sh_s[kPreThreads * SS::kRow];
+    __shared__ float m_s[kPreThreads][3];
+    __shared__ float lo_s[kPreThreads];
+    __shared__ PreItem items[kQueue];
+    __shared__ uint16_t item_g[kQueue];
+    __shared__ uint8_t item_v[kQueue];
+    __shared__ uint32_t qn;
     __shared__ __align__(8) uint64_t bar;
     const unsigned FULL = 0xffffffffu;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int g = blockIdx.x * kPreThreads + tid;
+    const int lane = tid & 31;
     const bool in = g < p.S.n;
     const bool use_bulk = SS::kBulk && (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
+    float *row = &sh_s[tid * SS::kRow];
 
     if (use_bulk) {
-        if (threadIdx.x == 0) {
-            const int n_here = min((int)blockDim.x, p.S.n - (int)(blockIdx.x * blockDim.x));
+        if (tid == 0) {
+            const int n_here = min(kPreThreads, p.S.n - (int)(blockIdx.x * kPreThreads));
             mbar_init(&bar, 1);
             mbar_arrive_expect_tx(&bar, (uint32_t)n_here * 12u * K);
         }
         __syncthreads();
-        if (in) bulk_g2s(&sh_s[threadIdx.x * SS::kRow], p.S.sh + (size_t)g * 3 * K, 12u * K, &bar);
+        if (in) bulk_g2s(row, p.S.sh + (size_t)g * 3 * K, 12u * K, &bar);
+    } else if (in) {
+        const float *src = p.S.sh + (size_t)g * 3 * K;
+        for (int i = 0; i < 3 * K; ++i) row[i] = __ldg(src + i);
     }
 
     float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
     float logit = 0.f;
-    float shr[SS::kBulk ? 1 : 3 * K];
-#pragma unroll
-    for (int i = 0; i < (SS::kBulk ? 1 : 3 * K); ++i) shr[i] = 0.f;
     bool ok = in;
     if (in) {
         m[0] = __ldg(p.S.means + 3 * g);
@@ -77,11 +97,6 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
             for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
         }
         logit = __ldg(p.S.logits + g);
-        if (!use_bulk) {
-            const float *src = p.S.sh + (size_t)g * 3 * K;
-#pragma unroll
-            for (int i = 0; i < (SS::kBulk ? 1 : 3 * K); ++i) shr[i] = __ldg(src + i);
-        }
         const float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
         if (!isfinite(chk)) ok = false;
     }
@@ -91,62 +106,136 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
         ok = false;
         zero_quat = true;
     }
-    const float LOG2E = 1.4426950408889634f;
-    const float lo = logit >= 0.f ? -log1pf(expf(-logit)) * LOG2E
-                                  : (logit - log1pf(expf(logit))) * LOG2E;
-    const float *shp = use_bulk ? &sh_s[threadIdx.x * SS::kRow] : shr;
-    bool sh_checked = false;       // the coefficients have arrived and are finite
-    bool nonfinite = in && !ok && !zero_quat;
+    const bool nonfinite_params = in && !ok && !zero_quat;
+    m_s[tid][0] = m[0];
+    m_s[tid][1] = m[1];
+    m_s[tid][2] = m[2];
+    // log2(sigmoid(x)) = -log2(1 + e^-x)
+    lo_s[tid] = logit >= 0.f ? -__log2f(1.0f + __expf(-logit)) : logit * 1.4426950408889634f - __log2f(1.0f + __expf(logit));
+    bool sh_checked = false, nonfinite_sh = false, timed_out = false;
 
-    for (int vi = 0; vi < p.n_views; ++vi) {
-        const DevView &V = vt.v[p.views[vi]];
-        Decision d;
-        d.visible = false;
-        d.x0 = d.x1 = d.y0 = d.y1 = 0;
-        d.tz = 0.f;
-        if (ok) decide(V, pre, m[0], m[1], m[2], vt.tile, d);
-        if (d.visible && !sh_checked) {
-            if (use_bulk && !mbar_wait(&bar, 0, kBulkWaitIters)) {
-                atomicOr(&p.st->flags, ST_TIMEOUT);
-                ok = false;
-            } else {
-                float shs = 0.f;
-#pragma unroll
-                for (int i = 0; i < 3 * K; ++i) shs += use_bulk ? shp[i] : shr[SS::kBulk ? 0 : i];
-                if (!isfinite(shs)) {
+    for (int vc = 0; vc < p.n_views; vc += kViewChunk) {
+        if (tid == 0) qn = 0u;
+        __syncthreads();
+        const int vend = min(p.n_views, vc + kViewChunk);
+        for (int vi = vc; vi < vend; ++vi) {
+            const DevView &V = vt.v[p.views[vi]];
+            Decision d;
+            d.visible = false;
+            d.x0 = d.x1 = d.y0 = d.y1 = 0;
+            d.tz = 0.f;
+            if (ok) decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+            if (d.visible && !sh_checked) {
+                // the coefficients are needed from here on: wait for them, check them
+                if (use_bulk && !mbar_wait(&bar, 0, kBulkWaitIters)) {
+                    timed_out = true;
                     ok = false;
-                    nonfinite = true;
+                } else {
+                    float shs = 0.f;
+                    for (int i = 0; i < 3 * K; ++i) shs += row[i];
+                    if (!isfinite(shs)) {
+                        ok = false;
+                        nonfinite_sh = true;
+                    }
+                }
+                sh_checked = true;
+                if (!ok) d.visible = false;
+            }
+            // queue the visible pair (one shared atomic per warp)
+            const uint32_t vb = __ballot_sync(FULL, d.visible);
+            uint32_t qbase = 0;
+            if (lane == 0 && vb) qbase = atomicAdd(&qn, (uint32_t)__popc(vb));
+            qbase = __shfl_sync(FULL, qbase, 0);
+            if (d.visible) {
+                const uint32_t slot = qbase + __popc(vb & lanemask_lt());
+                items[slot] = PreItem{d.n1, d.b, d.det, d.tz};
+                item_g[slot] = (uint16_t)tid;
+                item_v[slot] = (uint8_t)(vi - vc);
+            }
+            // warp-cooperative emission: one atomic per warp, coalesced key writes
+            const uint32_t cnt = d.visible ? (uint32_t)((d.x1 - d.x0) * (d.y1 - d.y0)) : 0u;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            if (total == 0) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&p.st->instances, (unsigned long long)total);
+            base = __shfl_sync(FULL, base, 0);
+            const uint32_t excl = incl - cnt;
+            const int nx = d.visible ? d.x1 - d.x0 : 1;
+            const uint32_t dbits = __float_as_uint(d.tz);
+            const uint32_t rid = (uint32_t)(V.rec_base + g);
+            for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    uint32_t v = __shfl_sync(FULL, incl, j + step - 1);
+                    if (v <= k) j += step;
+                }
+                const uint32_t oex = __shfl_sync(FULL, excl, j);
+                const int ox0 = __shfl_sync(FULL, d.x0, j);
+                const int oy0 = __shfl_sync(FULL, d.y0, j);
+                const int onx = __shfl_sync(FULL, nx, j);
+                const uint32_t odb = __shfl_sync(FULL, dbits, j);
+                const uint32_t orid = __shfl_sync(FULL, rid, j);
+                if (k < total) {
+                    const uint32_t local = k - oex;
+                    const int ty = oy0 + (int)(local / (uint32_t)onx);
+                    const int tx = ox0 + (int)(local % (uint32_t)onx);
+                    const unsigned long long tid64 =
+                        (unsigned long long)(V.tile_base + (int64_t)ty * V.gw + tx);
+                    const unsigned long long pos = base + k;
+                    if (pos < p.cap) {
+                        p.keys[pos] = (tid64 << 32) | odb;
+                        p.vals[pos] = orid;
+                        if (p.tile_cnt) atomicAdd(p.tile_cnt + tid64, 1u);
+                    }
                 }
             }
-            sh_checked = true;
-            if (!ok) d.visible = false;
+            if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
         }
-        if (d.visible) {
+        __syncthreads();
+        const uint32_t nq = qn;
+        if (nq && use_bulk && !sh_checked && !mbar_wait(&bar, 0, kBulkWaitIters)) timed_out = true;
+        sh_checked = sh_checked || nq != 0;
+        // drain the queue: one visible (Gaussian, view) pair per thread
+        for (uint32_t it = tid; it < nq && !timed_out; it += kPreThreads) {
+            const PreItem I_ = items[it];
+            const int gl = item_g[it];
+            const DevView &V = vt.v[p.views[vc + item_v[it]]];
+            const float mx = m_s[gl][0], my = m_s[gl][1], mz = m_s[gl][2];
             // 2D mean relative to the principal point, as an unevaluated double-float sum
             float xh, xl, yh, yl, zh, zl, uh, ul, vh, vl;
-            dot3_plus(V.R[0], V.R[1], V.R[2], m[0], m[1], m[2], V.t[0], xh, xl);
-            dot3_plus(V.R[3], V.R[4], V.R[5], m[0], m[1], m[2], V.t[1], yh, yl);
-            dot3_plus(V.R[6], V.R[7], V.R[8], m[0], m[1], m[2], V.t[2], zh, zl);
+            dot3_plus(V.R[0], V.R[1], V.R[2], mx, my, mz, V.t[0], xh, xl);
+            dot3_plus(V.R[3], V.R[4], V.R[5], mx, my, mz, V.t[1], yh, yl);
+            dot3_plus(V.R[6], V.R[7], V.R[8], mx, my, mz, V.t[2], zh, zl);
             proj_ratio(V.fx, xh, xl, zh, zl, uh, ul);
             proj_ratio(V.fy, yh, yl, zh, zl, vh, vl);
             // Cholesky factors of the conic of [[n0+.3, b], [b, n1+.3]] with the
             // cancellation-free determinant of the decision path
-            const float c = d.n1 + 0.3f;
-            const float l0 = sqrtf(c / d.det) * kCholScale;
-            const float l1 = -d.b / sqrtf(c * d.det) * kCholScale;
-            const float l2 = kCholScale / sqrtf(c);
+            const float c = I_.n1 + 0.3f;
+            const float rc = rsqrtf(c), rd = rsqrtf(I_.det);
+            const float l0 = c * rc * rd * kCholScale;       // sqrt(c / det)
+            const float l1 = -I_.b * rc * rd * kCholScale;   // -b / sqrt(c det)
+            const float l2 = rc * kCholScale;                // 1 / sqrt(c)
             // colour from the view direction (camera centre = -R^T t)
-            float cc0 = -(V.R[0] * V.t[0] + V.R[3] * V.t[1] + V.R[6] * V.t[2]);
-            float cc1 = -(V.R[1] * V.t[0] + V.R[4] * V.t[1] + V.R[7] * V.t[2]);
-            float cc2 = -(V.R[2] * V.t[0] + V.R[5] * V.t[1] + V.R[8] * V.t[2]);
-            float dx = m[0] - cc0, dy = m[1] - cc1, dz = m[2] - cc2;
-            float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+            const float cc0 = -(V.R[0] * V.t[0] + V.R[3] * V.t[1] + V.R[6] * V.t[2]);
+            const float cc1 = -(V.R[1] * V.t[0] + V.R[4] * V.t[1] + V.R[7] * V.t[2]);
+            const float cc2 = -(V.R[2] * V.t[0] + V.R[5] * V.t[1] + V.R[8] * V.t[2]);
+            float dx = mx - cc0, dy = my - cc1, dz = mz - cc2;
+            const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= inv; dy *= inv; dz *= inv;
             float Y[16];
             sh_basis(dx, dy, dz, K, Y);
             float col[3] = {0.5f, 0.5f, 0.5f};
-            if (use_bulk) {
-                const float4 *s4 = reinterpret_cast<const float4 *>(shp);
+            const float *sr = &sh_s[gl * SS::kRow];
+            if constexpr (SS::kBulk) {
+                const float4 *s4 = reinterpret_cast<const float4 *>(sr);
 #pragma unroll
                 for (int i = 0; i < 3 * K / 4; ++i) {
                     const float4 v4 = s4[i];
@@ -158,65 +247,20 @@ __global__ void __launch_bounds__(128) k_preprocess(const __grid_constant__ View
 #pragma unroll
                 for (int k = 0; k < K; ++k)
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) col[ch] += Y[k] * shr[SS::kBulk ? 0 : 3 * k + ch];
+                    for (int ch = 0; ch < 3; ++ch) col[ch] += Y[k] * sr[3 * k + ch];
             }
-            float4 *r = p.rec + (size_t)(V.rec_base + g) * kRecF4;
+            float4 *r = p.rec + (size_t)(V.rec_base + blockIdx.x * kPreThreads + gl) * kRecF4;
             r[0] = make_float4(uh, vh, ul, vl);
-            r[1] = make_float4(l0, l1, l2, lo);
-            r[2] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), d.tz);
+            r[1] = make_float4(l0, l1, l2, lo_s[gl]);
+            r[2] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), I_.tz);
         }
-        // warp-cooperative emission: one atomic per warp, coalesced key writes
-        const uint32_t cnt = d.visible ? (uint32_t)((d.x1 - d.x0) * (d.y1 - d.y0)) : 0u;
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        if (total == 0) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.st->instances, (unsigned long long)total);
-        base = __shfl_sync(FULL, base, 0);
-        const uint32_t excl = incl - cnt;
-        const int nx = d.visible ? d.x1 - d.x0 : 1;
-        const uint32_t dbits = __float_as_uint(d.tz);
-        const uint32_t rid = (uint32_t)(V.rec_base + g);
-        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                uint32_t v = __shfl_sync(FULL, incl, j + step - 1);
-                if (v <= k) j += step;
-            }
-            const uint32_t oex = __shfl_sync(FULL, excl, j);
-            const int ox0 = __shfl_sync(FULL, d.x0, j);
-            const int oy0 = __shfl_sync(FULL, d.y0, j);
-            const int onx = __shfl_sync(FULL, nx, j);
-            const uint32_t odb = __shfl_sync(FULL, dbits, j);
-            const uint32_t orid = __shfl_sync(FULL, rid, j);
-            if (k < total) {
-                const uint32_t local = k - oex;
-                const int ty = oy0 + (int)(local / (uint32_t)onx);
-                const int tx = ox0 + (int)(local % (uint32_t)onx);
-                const unsigned long long tid =
-                    (unsigned long long)(V.tile_base + (int64_t)ty * V.gw + tx);
-                const unsigned long long pos = base + k;
-                if (pos < p.cap) {
-                    p.keys[pos] = (tid << 32) | odb;
-                    p.vals[pos] = orid;
-                    if (p.tile_cnt) atomicAdd(p.tile_cnt + tid, 1u);
-                }
-            }
-        }
-        if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
+        __syncthreads();
     }
-    if (nonfinite) atomicOr(&p.st->flags, ST_NONFINITE);
+    if (nonfinite_params || nonfinite_sh) atomicOr(&p.st->flags, ST_NONFINITE);
     if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
     // the CTA's shared memory must outlive its bulk copies
-    if (use_bulk && in && !sh_checked && !mbar_wait(&bar, 0, kBulkWaitIters))
-        atomicOr(&p.st->flags, ST_TIMEOUT);
+    if (use_bulk && in && !sh_checked && !mbar_wait(&bar, 0, kBulkWaitIters)) timed_out = true;
+    if (timed_out) atomicOr(&p.st->flags, ST_TIMEOUT);
 }
 
 // Principal points of the views, read by the blend kernels to build each
@@ -251,7 +295,7 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8
     p.tile_cnt = tile_cnt;
     p.st = st;
     p.cap = cap;
-    const int block = 128;
+    const int block = kPreThreads;
     const unsigned grid = grid_for(S.n, block);
     switch (S.K) {
         case 1: k_preprocess<1><<<grid, block, 0, stream>>>(vt, p); break;

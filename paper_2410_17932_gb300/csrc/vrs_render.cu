@@ -30,6 +30,7 @@ struct FwdArgs {
     const uint32_t *order;      // persistent: tile work order (heaviest first)
     int64_t n_tiles;
     int64_t n_records;
+    unsigned long long cap;
     int persistent;
 };
 
@@ -40,7 +41,9 @@ struct PixAcc {
 };
 
 // One splat at one pixel, front to back: skip below 1/255, stop before T would
-// drop under 1e-4, otherwise blend.  Written as selects (no branches).
+// drop under 1e-4, otherwise blend.  Written as selects (no branches).  COUNT
+// also tracks the stop position and the blend count for the work counters.
+template <bool COUNT>
 __device__ __forceinline__ void pix_update(PixAcc &P, float q, const float4 &B, const float4 &C,
                                            uint32_t &n_blend)
 {
@@ -57,12 +60,14 @@ __device__ __forceinline__ void pix_update(PixAcc &P, float q, const float4 &B, 
     const uint32_t pos = (uint32_t)__float_as_int(C.w);
     P.T = blend ? Tn : P.T;
     P.last = blend ? pos : P.last;
-    P.stop = stop ? pos : P.stop;
     P.done = P.done || stop;
-    n_blend += blend ? 1u : 0u;
+    if (COUNT) {
+        P.stop = stop ? pos : P.stop;
+        n_blend += blend ? 1u : 0u;
+    }
 }
 
-template <int TS>
+template <int TS, bool COUNT>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
         float oxh, oxl, oyh, oyl;
         tile_origin((float)(tx * TS), pp.x, oxh, oxl);
         tile_origin((float)(ty * TS), pp.y, oyh, oyl);
-        const uint2 range = a.ranges[t];
+        const uint2 range = live_range(a.ranges, t, a.st, a.cap);
 
         PixAcc P0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in0 ? range.y - range.x : 0u, !in0};
         PixAcc P1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in1 ? range.y - range.x : 0u, !in1};
@@ -152,18 +157,18 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                     float q00, q01, q10, q11;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
                     pair_q2(A1.x, A1.y, A1.z, A1.w, B1.x, pxc, pyc, q10, q11);
-                    pix_update(P0, q00, B0, C0, n_blend);
-                    pix_update(P1, q01, B0, C0, n_blend);
-                    pix_update(P0, q10, B1, C1, n_blend);
-                    pix_update(P1, q11, B1, C1, n_blend);
+                    pix_update<COUNT>(P0, q00, B0, C0, n_blend);
+                    pix_update<COUNT>(P1, q01, B0, C0, n_blend);
+                    pix_update<COUNT>(P0, q10, B1, C1, n_blend);
+                    pix_update<COUNT>(P1, q11, B1, C1, n_blend);
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
                     float q00, q01;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
-                    pix_update(P0, q00, B0, C0, n_blend);
-                    pix_update(P1, q01, B0, C0, n_blend);
+                    pix_update<COUNT>(P0, q00, B0, C0, n_blend);
+                    pix_update<COUNT>(P1, q01, B0, C0, n_blend);
                 }
             }
             __syncthreads();
@@ -190,6 +195,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             a.ncontrib[pix + 1] = P1.last;
         }
     }
+    if (!COUNT) return;
     // algorithmic work counters: warp sums, one shared add per warp, one RED per CTA
     const uint32_t ev = __reduce_add_sync(FULL, n_eval), bl = __reduce_add_sync(FULL, n_blend);
     if (lane == 0 && (ev | bl)) {
@@ -242,9 +248,10 @@ __global__ void k_order_scatter(const uint2 *ranges, int64_t n_tiles, const uint
 }
 
 template <int TS>
-static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, cudaStream_t s)
+static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
-    k_render_fwd<TS><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    if (count) k_render_fwd<TS, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    else k_render_fwd<TS, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
     return cudaGetLastError();
 }
 
@@ -252,9 +259,11 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              int persistent, int n_sms, cudaStream_t s)
+                              unsigned long long cap, int persistent, int count, int n_sms,
+                              cudaStream_t s)
 {
     FwdArgs a;
+    a.cap = cap;
     a.viewtab = viewtab;
     a.rec = rec;
     a.vals = vals;
@@ -286,9 +295,9 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
     }
     if (grid <= 0) return cudaSuccess;
     switch (vt.tile) {
-        case 8: return launch_fwd_ts<8>(vt, a, grid, s);
-        case 16: return launch_fwd_ts<16>(vt, a, grid, s);
-        case 32: return launch_fwd_ts<32>(vt, a, grid, s);
+        case 8: return launch_fwd_ts<8>(vt, a, grid, count != 0, s);
+        case 16: return launch_fwd_ts<16>(vt, a, grid, count != 0, s);
+        case 32: return launch_fwd_ts<32>(vt, a, grid, count != 0, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -62,7 +62,7 @@ __device__ __forceinline__ uint32_t block_sum1024(uint32_t v, uint32_t *sh)
 __global__ void __launch_bounds__(kScanBlock) k_tile_blocksum(const TileSortArgs a)
 {
     __shared__ uint32_t sh[32];
-    if (live_instances(a.st, a.cap) == 0) return;
+    if (a.st->flags & ST_CAPACITY) return;    // every tile range is written, even with no instances
     const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     const uint32_t v = t < a.n_tiles ? a.cnt[t] : 0u;
     const uint32_t s = block_sum1024(v, sh);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a)
 {
     __shared__ uint32_t sh[32];
     __shared__ uint32_t base_s;
-    if (live_instances(a.st, a.cap) == 0) return;
+    if (a.st->flags & ST_CAPACITY) return;    // every tile range is written, even with no instances
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // prefix of the block sums of the blocks before this one
     uint32_t p = 0;

@@ -102,7 +102,7 @@ class Rasterizer:
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
         opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), self.sort,
-                               int(max_instances))
+                               int(max_instances), 0, 0)
         plan = L.vrs_plan()
         L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
         self.plan = plan
@@ -143,6 +143,20 @@ class Rasterizer:
         self.preprocess(stream)
         self.bin_sort(stream)
         self.render_fwd(stream=stream)
+
+    def count_pairs(self, stream=None):
+        """Gaussian-pixel pairs evaluated and blended by one counting forward pass (untimed use)."""
+        self.preprocess(stream)
+        self.bin_sort(stream)
+        self.plan.count_pairs = 1
+        try:
+            self.render_fwd(stream=stream)
+        finally:
+            self.plan.count_pairs = 0
+        info = L.vrs_run_info()
+        L._check(L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(stream)),
+                 "count_pairs")
+        return int(info.pair_evals), int(info.pair_blends)
 
     def status(self, stream=None):
         info = L.vrs_run_info()
