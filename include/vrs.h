@@ -141,8 +141,9 @@ typedef struct {
     int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1 */
     int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
     int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */
-    int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] big-tile
-                                  list, [ceil(n_tiles / 1024)] block sums (bucketed sort) */
+    int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] list of
+                                  tiles sorted by a whole CTA, [ceil(n_tiles / 1024)] block sums
+                                  (bucketed sort) */
     int32_t sorted_buf;        /* which ping-pong buffer holds the sorted list */
     int32_t n_sms;
     int32_t sort_mode;         /* vrs_plan_opts.sort */

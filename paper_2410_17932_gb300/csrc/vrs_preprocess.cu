@@ -36,7 +36,7 @@ struct ShStage {
     static constexpr int kRow = kBulk ? 3 * K + 4 : 3 * K + 1;   // padded row (floats): 52 for SH-3
 };
 
-constexpr uint32_t kBulkWaitIters = 1u << 22;
+constexpr uint32_t kBulkWaitIters = 1u << 20;
 constexpr int kPreThreads = 128;
 constexpr int kViewChunk = 4;                       // views per queue round
 constexpr int kQueue = kPreThreads * kViewChunk;
