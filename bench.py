@@ -115,6 +115,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def reduce_max(value: float, world: int, device="cuda") -> float:
+    """Max of a per-rank value over all ranks (the slowest rank's step time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms_per_frame(max_step_ms: float, world: int) -> float:
+    """Every rank renders one frame per step (replicas), so the job delivers `world`
+    frames per slowest step."""
+    return max_step_ms / world
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -358,12 +375,8 @@ def main():
     srt = [e[1].elapsed_time(e[2]) for e in evs]
     bld = [e[2].elapsed_time(e[3]) for e in evs]
     step = [e[0].elapsed_time(e[3]) for e in evs]
-    ms = statistics.mean(step)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ms / world                   # whole-job ms per frame (world frames per step)
+    ms = reduce_max(statistics.mean(step), world)
+    value = whole_job_ms_per_frame(ms, world)
 
     # roofline of the dominant kernel
     peaks, src = measured_peaks()

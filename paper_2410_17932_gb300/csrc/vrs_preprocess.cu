@@ -39,7 +39,8 @@ struct ShStage {
 constexpr uint32_t kBulkWaitIters = 1u << 20;
 constexpr int kPreThreads = 128;
 constexpr int kViewChunk = 4;                       // views per queue round
-constexpr int kQueue = kPreThreads * kViewChunk;
+constexpr int kPreWarps = kPreThreads / 32;
+constexpr int kQueue = 32 * kViewChunk;             // per warp
 
 struct PreItem {
     float n1, b, det, tz;
@@ -53,15 +54,14 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
     __shared__ __align__(16) float sh_s[kPreThreads * SS::kRow];
     __shared__ float m_s[kPreThreads][3];
     __shared__ float lo_s[kPreThreads];
-    __shared__ PreItem items[kQueue];
-    __shared__ uint16_t item_g[kQueue];
-    __shared__ uint8_t item_v[kQueue];
-    __shared__ uint32_t qn;
+    __shared__ PreItem items[kPreWarps][kQueue];
+    __shared__ uint8_t item_g[kPreWarps][kQueue];
+    __shared__ uint8_t item_v[kPreWarps][kQueue];
     __shared__ __align__(8) uint64_t bar;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x;
     const int g = blockIdx.x * kPreThreads + tid;
-    const int lane = tid & 31;
+    const int lane = tid & 31, wp = tid >> 5;
     const bool in = g < p.S.n;
     const bool use_bulk = SS::kBulk && (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
     float *row = &sh_s[tid * SS::kRow];
@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
     lo_s[tid] = logit >= 0.f ? -__log2f(1.0f + __expf(-logit)) : logit * 1.4426950408889634f - __log2f(1.0f + __expf(logit));
     bool sh_checked = false, nonfinite_sh = false, timed_out = false;
 
+    __syncwarp();   // this warp's m_s, lo_s (and plainly loaded rows) are visible to its lanes
     for (int vc = 0; vc < p.n_views; vc += kViewChunk) {
-        if (tid == 0) qn = 0u;
-        __syncthreads();
+        uint32_t qn = 0;   // this warp's queue of visible (Gaussian, view) pairs
         const int vend = min(p.n_views, vc + kViewChunk);
         for (int vi = vc; vi < vend; ++vi) {
             const DevView &V = vt.v[p.views[vi]];
@@ -141,17 +141,15 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
                 sh_checked = true;
                 if (!ok) d.visible = false;
             }
-            // queue the visible pair (one shared atomic per warp)
+            // queue the visible pair
             const uint32_t vb = __ballot_sync(FULL, d.visible);
-            uint32_t qbase = 0;
-            if (lane == 0 && vb) qbase = atomicAdd(&qn, (uint32_t)__popc(vb));
-            qbase = __shfl_sync(FULL, qbase, 0);
             if (d.visible) {
-                const uint32_t slot = qbase + __popc(vb & lanemask_lt());
-                items[slot] = PreItem{d.n1, d.b, d.det, d.tz};
-                item_g[slot] = (uint16_t)tid;
-                item_v[slot] = (uint8_t)(vi - vc);
+                const uint32_t slot = qn + __popc(vb & lanemask_lt());
+                items[wp][slot] = PreItem{d.n1, d.b, d.det, d.tz};
+                item_g[wp][slot] = (uint8_t)lane;
+                item_v[wp][slot] = (uint8_t)(vi - vc);
             }
+            qn += __popc(vb);
             // warp-cooperative emission: one atomic per warp, coalesced key writes
             const uint32_t cnt = d.visible ? (uint32_t)((d.x1 - d.x0) * (d.y1 - d.y0)) : 0u;
             uint32_t incl = cnt;
@@ -199,15 +197,16 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
             }
             if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
         }
-        __syncthreads();
-        const uint32_t nq = qn;
-        if (nq && use_bulk && !sh_checked && !mbar_wait(&bar, 0, kBulkWaitIters)) timed_out = true;
-        sh_checked = sh_checked || nq != 0;
-        // drain the queue: one visible (Gaussian, view) pair per thread
-        for (uint32_t it = tid; it < nq && !timed_out; it += kPreThreads) {
-            const PreItem I_ = items[it];
-            const int gl = item_g[it];
-            const DevView &V = vt.v[p.views[vc + item_v[it]]];
+        __syncwarp();
+        // the rows read below belong to this warp's Gaussians; their bulk copies are
+        // complete once any lane of the CTA has seen the barrier's phase
+        if (qn && use_bulk && !mbar_wait(&bar, 0, kBulkWaitIters)) timed_out = true;
+        sh_checked = sh_checked || qn != 0;
+        // drain the warp's queue: one visible (Gaussian, view) pair per lane
+        for (uint32_t it = lane; it < qn && !timed_out; it += 32) {
+            const PreItem I_ = items[wp][it];
+            const int gl = wp * 32 + item_g[wp][it];
+            const DevView &V = vt.v[p.views[vc + item_v[wp][it]]];
             const float mx = m_s[gl][0], my = m_s[gl][1], mz = m_s[gl][2];
             // 2D mean relative to the principal point, as an unevaluated double-float sum
             float xh, xl, yh, yl, zh, zl, uh, ul, vh, vl;
@@ -254,7 +253,7 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
             r[1] = make_float4(l0, l1, l2, lo_s[gl]);
             r[2] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), I_.tz);
         }
-        __syncthreads();
+        __syncwarp();
     }
     if (nonfinite_params || nonfinite_sh) atomicOr(&p.st->flags, ST_NONFINITE);
     if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);

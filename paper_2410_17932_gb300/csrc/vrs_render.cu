@@ -43,11 +43,15 @@ struct PixAcc {
 // One splat at one pixel, front to back: skip below 1/255, stop before T would
 // drop under 1e-4, otherwise blend.  Written as selects (no branches).  COUNT
 // also tracks the stop position and the blend count for the work counters.
+__device__ __forceinline__ bool pix_hit(const PixAcc &P, float q, const float4 &B)
+{
+    return !P.done && q <= B.z;
+}
+
 template <bool COUNT>
-__device__ __forceinline__ void pix_update(PixAcc &P, float q, const float4 &B, const float4 &C,
+__device__ __forceinline__ void pix_update(PixAcc &P, float q, bool h, const float4 &B, const float4 &C,
                                            uint32_t &n_blend)
 {
-    const bool h = !P.done && q <= B.z;
     const float al = pair_alpha(B.y, q);
     const float Tn = P.T * (1.f - al);
     const bool stop = h && Tn < 1e-4f;
@@ -157,18 +161,29 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                     float q00, q01, q10, q11;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
                     pair_q2(A1.x, A1.y, A1.z, A1.w, B1.x, pxc, pyc, q10, q11);
-                    pix_update<COUNT>(P0, q00, B0, C0, n_blend);
-                    pix_update<COUNT>(P1, q01, B0, C0, n_blend);
-                    pix_update<COUNT>(P0, q10, B1, C1, n_blend);
-                    pix_update<COUNT>(P1, q11, B1, C1, n_blend);
+                    // a splat whose update changes no pixel of the warp is skipped as a whole
+                    bool h0 = pix_hit(P0, q00, B0), h1 = pix_hit(P1, q01, B0);
+                    if (__any_sync(FULL, h0 || h1)) {
+                        pix_update<COUNT>(P0, q00, h0, B0, C0, n_blend);
+                        pix_update<COUNT>(P1, q01, h1, B0, C0, n_blend);
+                    }
+                    h0 = pix_hit(P0, q10, B1);
+                    h1 = pix_hit(P1, q11, B1);
+                    if (__any_sync(FULL, h0 || h1)) {
+                        pix_update<COUNT>(P0, q10, h0, B1, C1, n_blend);
+                        pix_update<COUNT>(P1, q11, h1, B1, C1, n_blend);
+                    }
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
                     float q00, q01;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
-                    pix_update<COUNT>(P0, q00, B0, C0, n_blend);
-                    pix_update<COUNT>(P1, q01, B0, C0, n_blend);
+                    const bool h0 = pix_hit(P0, q00, B0), h1 = pix_hit(P1, q01, B0);
+                    if (__any_sync(FULL, h0 || h1)) {
+                        pix_update<COUNT>(P0, q00, h0, B0, C0, n_blend);
+                        pix_update<COUNT>(P1, q01, h1, B0, C0, n_blend);
+                    }
                 }
             }
             __syncthreads();

@@ -101,15 +101,30 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a)
     }
 }
 
-__global__ void k_tile_scatter(const TileSortArgs a)
+// Each thread keeps four instances in flight (loads, then the four atomics,
+// then the four stores): the scatter is bound by the latency of the position
+// atomics, not by bandwidth.
+__global__ void __launch_bounds__(256) k_tile_scatter(const TileSortArgs a)
 {
     const uint32_t M = live_instances(a.st, a.cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-        const unsigned long long key = a.keys_in[i];
-        const uint32_t t = (uint32_t)(key >> 32);
-        if ((int64_t)t >= a.n_tiles) continue;   // cannot happen for keys from vrs_preprocess
-        const uint32_t pos = atomicAdd(&a.cursor[t], 1u);
-        a.bucket[pos] = (key << 32) | (unsigned long long)a.vals_in[i];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += 4 * stride) {
+        unsigned long long key[4];
+        uint32_t val[4], pos[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = i0 + u * stride;
+            key[u] = i < M ? a.keys_in[i] : ~0ull;
+            val[u] = i < M ? a.vals_in[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = (uint32_t)(key[u] >> 32);
+            pos[u] = (int64_t)t < a.n_tiles ? atomicAdd(&a.cursor[t], 1u) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (pos[u] != 0xffffffffu) a.bucket[pos[u]] = (key[u] << 32) | (unsigned long long)val[u];
     }
 }
 
@@ -121,23 +136,37 @@ __device__ __forceinline__ void cmp_swap(unsigned long long &x, unsigned long lo
 }
 
 // Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i].
+// The per-element bodies are unrolled; the stage loops are not, which keeps the
+// four instantiations small enough for the instruction cache.
+template <int E>
+__device__ __forceinline__ void reg_stage(unsigned long long (&v)[E], int ji, int kk, int lane)
+{
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = i ^ ji;
+        if (p > i) {
+            const bool asc = ((i * 32 + lane) & kk) == 0;
+            unsigned long long x = v[i], y = v[p];
+            cmp_swap(x, y, asc);
+            v[i] = x;
+            v[p] = y;
+        }
+    }
+}
+
 template <int E>
 __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lane)
 {
     constexpr int P = 32 * E;
-#pragma unroll
+#pragma unroll 1
     for (int k = 2; k <= P; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32) {
                 const int ji = j >> 5;
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    if ((i & ji) == 0) {
-                        const int e = i * 32 + lane;
-                        cmp_swap(v[i], v[i | ji], (e & k) == 0);
-                    }
-                }
+                if (ji == 1) reg_stage<E>(v, 1, k, lane);
+                else if (E > 2 && ji == 2) reg_stage<E>(v, 2, k, lane);
+                else if (E > 4) reg_stage<E>(v, 4, k, lane);
             } else {
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
@@ -145,7 +174,8 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lan
                     const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], j);
                     const bool asc = (e & k) == 0, lower = (lane & j) == 0;
                     const bool take_min = lower == asc;
-                    v[i] = take_min ? (v[i] < o ? v[i] : o) : (v[i] < o ? o : v[i]);
+                    const bool less = v[i] < o;
+                    v[i] = (take_min == less) ? v[i] : o;
                 }
             }
         }
