@@ -161,29 +161,18 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                     float q00, q01, q10, q11;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
                     pair_q2(A1.x, A1.y, A1.z, A1.w, B1.x, pxc, pyc, q10, q11);
-                    // a splat whose update changes no pixel of the warp is skipped as a whole
-                    bool h0 = pix_hit(P0, q00, B0), h1 = pix_hit(P1, q01, B0);
-                    if (__any_sync(FULL, h0 || h1)) {
-                        pix_update<COUNT>(P0, q00, h0, B0, C0, n_blend);
-                        pix_update<COUNT>(P1, q01, h1, B0, C0, n_blend);
-                    }
-                    h0 = pix_hit(P0, q10, B1);
-                    h1 = pix_hit(P1, q11, B1);
-                    if (__any_sync(FULL, h0 || h1)) {
-                        pix_update<COUNT>(P0, q10, h0, B1, C1, n_blend);
-                        pix_update<COUNT>(P1, q11, h1, B1, C1, n_blend);
-                    }
+                    pix_update<COUNT>(P0, q00, pix_hit(P0, q00, B0), B0, C0, n_blend);
+                    pix_update<COUNT>(P1, q01, pix_hit(P1, q01, B0), B0, C0, n_blend);
+                    pix_update<COUNT>(P0, q10, pix_hit(P0, q10, B1), B1, C1, n_blend);
+                    pix_update<COUNT>(P1, q11, pix_hit(P1, q11, B1), B1, C1, n_blend);
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
                     float q00, q01;
                     pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
-                    const bool h0 = pix_hit(P0, q00, B0), h1 = pix_hit(P1, q01, B0);
-                    if (__any_sync(FULL, h0 || h1)) {
-                        pix_update<COUNT>(P0, q00, h0, B0, C0, n_blend);
-                        pix_update<COUNT>(P1, q01, h1, B0, C0, n_blend);
-                    }
+                    pix_update<COUNT>(P0, q00, pix_hit(P0, q00, B0), B0, C0, n_blend);
+                    pix_update<COUNT>(P1, q01, pix_hit(P1, q01, B0), B0, C0, n_blend);
                 }
             }
             __syncthreads();
