@@ -44,6 +44,7 @@ WORKLOADS = {
 # pixel-changing work (culling and early exit raise it; evaluating pairs that
 # cannot contribute lowers it).
 ALU_OPS_PER_BLEND = 25
+METRIC = "ms per stereo frame @2016x2240/eye (0.5M SH-3 Gaussians)"
 
 
 def load_workload(name):
@@ -142,46 +143,97 @@ def dist_setup():
 # ---------------------------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline object)
 
-def oracle_frame_estimate(scenes, views, budget_s: float, seed: int = 0, tile: int = 16):
-    """Times the FP64 oracle on a tile sample of the frame and extrapolates to the whole frame.
+class OracleFrameSampler:
+    """Times the FP64 oracle on a bounded sample of one frame and extrapolates to the whole frame.
 
-    Per view: decide + project over all Gaussians (timed in full), tile lists over all
-    Gaussians (timed in full), compositing on a random sample of tiles sized to the budget
-    (extrapolated by the tile count)."""
-    import oracle
-    rng = np.random.default_rng(seed)
-    total = 0.0
-    sampled = 0
-    n_tiles_all = 0
-    for cam in views:
-        sc = scenes[cam.scene]
-        t0 = time.perf_counter()
-        dec = oracle.decide(sc, cam, tile)
-        proj = oracle.project(sc, cam)
-        t1 = time.perf_counter()
-        gw, gh = oracle.grid(cam, tile)
-        nt = gw * gh
-        n_tiles_all += nt
-        empty = np.zeros(nt, np.uint8)
-        t2 = time.perf_counter()
-        oracle.render(sc, cam, tile, dec=dec, proj=proj, tile_mask=empty)
-        t3 = time.perf_counter()
-        lists = t3 - t2
-        k = 8
-        per_view_budget = budget_s / max(1, len(views))
-        while True:
-            mask = np.zeros(nt, np.uint8)
-            mask[rng.choice(nt, min(k, nt), replace=False)] = 1
-            t4 = time.perf_counter()
-            oracle.render(sc, cam, tile, dec=dec, proj=proj, tile_mask=mask)
-            t5 = time.perf_counter()
-            comp = max(0.0, (t5 - t4) - lists)
-            if comp * 4 > per_view_budget * 0.5 or k >= nt:
-                break
-            k = min(nt, k * 4)
-        sampled += int(mask.sum())
-        total += (t1 - t0) + lists + comp * nt / mask.sum()
-    return total * 1e3, sampled, n_tiles_all
+    Each sample, per view, times (a) decide + project over a random contiguous chunk of g
+    Gaussians, scaled by n / g, and (b) tile lists + compositing over random tile-aligned
+    blocks (8x8 tiles or smaller), each run as a cropped view over the Gaussians whose
+    rectangles overlap it, scaled by the view's tile count over the k tiles sampled.  g and
+    k follow the measured rates so that one sample takes about `budget_s`.  The full
+    decisions and projections that (b) takes as input are computed once, untimed."""
+
+    def __init__(self, scenes, views, tile: int = 16):
+        import oracle
+        from types import SimpleNamespace
+        self.oracle, self.NS = oracle, SimpleNamespace
+        self.scenes, self.views, self.tile = scenes, views, tile
+        self.full = []
+        for cam in views:
+            sc = scenes[cam.scene]
+            dec = oracle.decide(sc, cam, tile)
+            proj = oracle.project(sc, cam)
+            vis = np.nonzero(dec["visible"])[0]
+            self.full.append((dec, proj, vis, dec["rect"][vis]))
+        self.g_rate = [None] * len(views)      # Gaussians per second, stage (a)
+        self.k_rate = [None] * len(views)      # tiles per second, stage (b)
+        self.n_tiles = sum(int(np.prod(oracle.grid(c, tile))) for c in views)
+
+    def _chunk(self, sc, a, g):
+        return self.NS(means=sc.means[a:a + g], log_scales=sc.log_scales[a:a + g],
+                       quats=sc.quats[a:a + g], opacity_logits=sc.opacity_logits[a:a + g],
+                       sh=sc.sh[a:a + g], sh_degree=sc.sh_degree, n=g)
+
+    def _block(self, v, cam, bx, by, bw, bh):
+        """Oracle inputs for the tile block [bx, bx+bw) x [by, by+bh) as a cropped view."""
+        tile = self.tile
+        dec, proj, vis, rect = self.full[v]
+        hit = (rect[:, 0] < bx + bw) & (rect[:, 1] > bx) & (rect[:, 2] < by + bh) & (rect[:, 3] > by)
+        idx = vis[hit]
+        r = rect[hit].copy()
+        r[:, 0:2] = np.clip(r[:, 0:2] - bx, 0, bw)
+        r[:, 2:4] = np.clip(r[:, 2:4] - by, 0, bh)
+        x0, y0 = bx * tile, by * tile
+        crop = cam.crop(x0, y0, min(bw * tile, cam.width - x0), min(bh * tile, cam.height - y0))
+        sdec = {"visible": dec["visible"][idx], "depth": dec["depth"][idx], "rect": np.ascontiguousarray(r)}
+        return self.NS(n=len(idx)), crop, sdec, proj[idx]
+
+    def sample(self, budget_s: float, rng):
+        O, tile = self.oracle, self.tile
+        total = 0.0
+        g_sum = k_sum = 0
+        per_view = budget_s / max(1, len(self.views))
+        for v, cam in enumerate(self.views):
+            sc = self.scenes[cam.scene]
+            n = sc.n
+            gw, gh = O.grid(cam, tile)
+            nt = gw * gh
+            # (a) per-Gaussian stages on a contiguous chunk
+            g = 16384 if self.g_rate[v] is None else int(self.g_rate[v] * per_view / 2)
+            g = max(1, min(n, max(4096, g)))
+            a = int(rng.integers(0, n - g + 1))
+            sub = self._chunk(sc, a, g)
+            t0 = time.perf_counter()
+            O.decide(sub, cam, tile)
+            O.project(sub, cam)
+            ta = time.perf_counter() - t0
+            self.g_rate[v] = g / max(ta, 1e-6)
+            # (b) tile lists + compositing on random blocks of tiles
+            k = 16 if self.k_rate[v] is None else int(self.k_rate[v] * per_view / 2)
+            k = max(16, min(nt, k))
+            tb = 0.0
+            done = 0
+            while done < k:
+                side = min(8, max(1, int(math.isqrt(k - done))))
+                bw, bh = min(side, gw), min(side, gh)
+                bx = int(rng.integers(0, gw - bw + 1))
+                by = int(rng.integers(0, gh - bh + 1))
+                scn, crop, sdec, sproj = self._block(v, cam, bx, by, bw, bh)
+                t0 = time.perf_counter()
+                O.render(scn, crop, tile, dec=sdec, proj=sproj)
+                tb += time.perf_counter() - t0
+                done += bw * bh
+            self.k_rate[v] = done / max(tb, 1e-6)
+            total += ta * n / g + tb * nt / done
+            g_sum += g
+            k_sum += done
+        return total * 1e3, g_sum, k_sum
+
+    def describe(self, g_sum, k_sum):
+        n_all = sum(self.scenes[c.scene].n for c in self.views)
+        return (f"per view: decide+project on a random chunk of Gaussians, tile lists + FP64 compositing "
+                f"on random blocks of up to 8x8 tiles (last sample: {g_sum} of {n_all} Gaussian-views, "
+                f"{k_sum} of {self.n_tiles} tiles), extrapolated by Gaussian and tile counts")
 
 
 def run_reference(args, world, rank):
@@ -190,27 +242,25 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     scenes, views = load_workload(args.workload)
-    for _ in range(max(0, args.warmup)):
-        oracle_frame_estimate(scenes, views, budget_s=args.ref_budget / max(1, args.steps + args.warmup))
+    sampler = OracleFrameSampler(scenes, views, args.tile)
+    per_step = min(30.0, args.ref_budget / max(1, args.steps + args.warmup))
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        sampler.sample(per_step, rng)
     ests = []
-    info = None
-    for k in range(args.steps):
-        ms, sampled, nt = oracle_frame_estimate(scenes, views,
-                                                budget_s=args.ref_budget / max(1, args.steps + args.warmup),
-                                                seed=k)
+    g_sum = k_sum = 0
+    for _ in range(args.steps):
+        ms, g_sum, k_sum = sampler.sample(per_step, rng)
         ests.append(ms)
-        info = (sampled, nt)
     value = float(np.median(ests))
     line = {
-        "impl": "reference", "metric": "ms per stereo frame @2016x2240/eye", "value": round(value, 3),
+        "impl": "reference", "metric": METRIC, "value": round(value, 3),
         "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(value, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]},
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "tile": args.tile},
         "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": oracle.num_threads(),
-                         "kind": "oracle",
-                         "sample": f"decide+project+tile lists over all Gaussians; compositing on "
-                                   f"{info[0]} of {info[1]} tiles, extrapolated by tile count"},
+                         "kind": "oracle", "sample": sampler.describe(g_sum, k_sum)},
         "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -439,10 +489,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        est, sampled, nt = oracle_frame_estimate(scenes, views, budget_s=args.cpu_budget)
+        sampler_ = OracleFrameSampler(scenes, views, int(p.tile))
+        rng = np.random.default_rng(0)
+        sampler_.sample(1.0, rng)                       # sizes the sample from measured rates
+        est, g_sum, k_sum = sampler_.sample(args.cpu_budget, rng)
         cpu = {"value": round(est, 1), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"decide+project+tile lists over all Gaussians; FP64 compositing on {sampled} "
-                         f"of {nt} tiles, extrapolated by tile count"}
+               "sample": sampler_.describe(g_sum, k_sum)}
 
     extra = None
     if rank == 0 and not args.no_extras:
@@ -454,7 +506,7 @@ def main():
         launches_per_step = (1 + len(scenes)) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
     if rank == 0:
         line = {
-            "metric": "ms per stereo frame @2016x2240/eye (0.5M SH-3 Gaussians)",
+            "metric": METRIC,
             "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
