@@ -144,6 +144,9 @@ typedef struct {
     int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] list of
                                   tiles sorted by a whole CTA, [ceil(n_tiles / 1024)] block sums
                                   (bucketed sort) */
+    int64_t off_pairs;         /* [n_records] 32-byte visible (Gaussian, view) pairs, the
+                                  preprocess step's scratch; scene s's list starts at entry
+                                  sum over s' < s of scene_n[s'] * (views of s') */
     int32_t sorted_buf;        /* which ping-pong buffer holds the sorted list */
     int32_t n_sms;
     int32_t sort_mode;         /* vrs_plan_opts.sort */

@@ -48,7 +48,7 @@ class vrs_plan(ctypes.Structure):
                 ("off_status", _i64), ("off_records", _i64), ("off_keys", _i64 * 2),
                 ("off_vals", _i64 * 2), ("off_hist", _i64), ("off_ranges", _i64),
                 ("off_ncontrib", _i64), ("off_order", _i64), ("off_grad2d", _i64),
-                ("off_tilesort", _i64), ("sorted_buf", _i32), ("n_sms", _i32), ("sort_mode", _i32),
+                ("off_tilesort", _i64), ("off_pairs", _i64), ("sorted_buf", _i32), ("n_sms", _i32), ("sort_mode", _i32),
                 ("count_pairs", _i32),
                 ("scene_n", _i32 * VRS_MAX_SCENES), ("scene_deg", _i32 * VRS_MAX_SCENES),
                 ("view_scene", _i32 * VRS_MAX_VIEWS), ("view_w", _i32 * VRS_MAX_VIEWS),

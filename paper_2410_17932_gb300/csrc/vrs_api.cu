@@ -4,9 +4,10 @@
 #include "vrs_internal.cuh"
 
 namespace vrs {
-cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, const int8_t *views, int n_views,
-                              float4 *rec, unsigned long long *keys, uint32_t *vals, uint32_t *tile_cnt,
-                              DevStatus *st, unsigned long long cap, cudaStream_t stream);
+cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
+                              int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
+                              uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
+                              int n_sms, cudaStream_t stream);
 cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream);
 cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
                         uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
@@ -211,6 +212,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.off_order = take((tiles + kOrderTmp) * 4);
     P.off_grad2d = P.backward ? take(rec * kGrad2D * 4) : 0;
     P.off_tilesort = take((3 * tiles + (tiles + 1023) / 1024) * 4);
+    P.off_pairs = take(rec * 32);
     P.workspace_bytes = off;
     *plan = P;
     return VRS_OK;
@@ -240,15 +242,18 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
         e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)plan->n_tiles, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
     }
+    int64_t pair_base = 0;
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];
         const int nv = views_of_scene(plan, sc, vlist);
-        e = launch_preprocess(vt, dev_scene(scenes[sc]), vlist, nv,
+        e = launch_preprocess(vt, dev_scene(scenes[sc]), sc, vlist, nv,
+                              at<uint4>(workspace, plan->off_pairs) + 2 * pair_base,
                               at<float4>(workspace, plan->off_records),
                               at<unsigned long long>(workspace, plan->off_keys[0]),
                               at<uint32_t>(workspace, plan->off_vals[0]), tile_cnt, st,
-                              (unsigned long long)plan->max_instances, s);
+                              (unsigned long long)plan->max_instances, plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
+        pair_base += (int64_t)plan->scene_n[sc] * nv;
     }
     return VRS_OK;
 }

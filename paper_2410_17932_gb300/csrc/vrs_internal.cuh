@@ -38,7 +38,9 @@ struct DevStatus {
     unsigned long long pair_evals;
     unsigned long long pair_blends;
     uint32_t work[8];          // work-queue counters of persistent kernels
+    unsigned long long scene_pairs[VRS_MAX_SCENES];   // visible (Gaussian, view) pairs per scene
 };
+static_assert(sizeof(DevStatus) <= 256, "the status block is 256 bytes");
 
 enum : uint32_t {
     ST_ZERO_QUAT = 1u,
