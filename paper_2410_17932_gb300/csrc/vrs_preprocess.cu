@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
         const int nx = vis ? x1 - x0 : 1;
         const uint32_t dbits = e1.w;
         const uint32_t rid = (uint32_t)(V.rec_base + g);
-        const int64_t tbase = V.tile_base;
+        const long long first = V.tile_base + (long long)y0 * V.gw + x0;   // tile id of (x0, y0)
         const int gw = V.gw;
         for (uint32_t k0 = 0; k0 < total; k0 += 32) {
             const uint32_t k = k0 + lane;
@@ -224,18 +224,26 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
                 if (v <= k) j += step;
             }
             const uint32_t oex = __shfl_sync(FULL, excl, j);
-            const int ox0 = __shfl_sync(FULL, x0, j);
-            const int oy0 = __shfl_sync(FULL, y0, j);
+            const long long ofirst = __shfl_sync(FULL, first, j);
             const int onx = __shfl_sync(FULL, nx, j);
+            const int ogw = __shfl_sync(FULL, gw, j);
             const uint32_t odb = __shfl_sync(FULL, dbits, j);
             const uint32_t orid = __shfl_sync(FULL, rid, j);
-            const long long otb = __shfl_sync(FULL, (long long)tbase, j);
-            const int ogw = __shfl_sync(FULL, gw, j);
             if (k < total) {
-                const uint32_t local = k - oex;
-                const int ty = oy0 + (int)(local / (uint32_t)onx);
-                const int tx = ox0 + (int)(local % (uint32_t)onx);
-                const unsigned long long tid64 = (unsigned long long)(otb + (int64_t)ty * ogw + tx);
+                // (row, column) of the pair's local tile index: a reciprocal estimate
+                // (off by at most one below 2^23, and a rectangle holds at most 2^22
+                // tiles) and one correction step
+                const int local = (int)(k - oex);
+                int ty = (int)__fmul_rn((float)local, __frcp_rn((float)onx));
+                int tx = local - ty * onx;
+                if (tx < 0) {
+                    --ty;
+                    tx += onx;
+                } else if (tx >= onx) {
+                    ++ty;
+                    tx -= onx;
+                }
+                const unsigned long long tid64 = (unsigned long long)(ofirst + (long long)ty * ogw + tx);
                 const unsigned long long pos = base + k;
                 if (pos < p.cap) {
                     p.keys[pos] = (tid64 << 32) | odb;
@@ -287,10 +295,11 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // enough CTAs to fill every SM several times over; the kernel loops over the list
+    // one pair per thread up to the list's capacity; CTAs past the device-side
+    // count exit at once (the loop covers any remainder)
+    (void)n_sms;
     const int64_t want = grid_for((int64_t)S.n * n_views, kPairThreads);
-    const int64_t cap_ctas = (int64_t)(n_sms > 0 ? n_sms : 152) * 8;
-    const unsigned grid = (unsigned)(want < cap_ctas ? want : cap_ctas);
+    const unsigned grid = (unsigned)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     switch (S.K) {
         case 1: k_pairs<1><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
         case 4: k_pairs<4><<<grid, kPairThreads, 0, stream>>>(vt, p); break;

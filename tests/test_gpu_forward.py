@@ -196,3 +196,15 @@ def test_radix_and_bucketed_sorts_agree_multiview():
     kb, vb, rb = b.sorted_lists()
     assert torch.equal(ka, kb) and torch.equal(va, vb) and torch.equal(ra, rb)
     _check_sort(a, [s0], views)
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_emission_large_rectangles(tile):
+    """Splats whose rectangles span most of a 1024x768 view: the warp-cooperative key
+    emission's row/column split over rectangles of thousands of tiles, bit-exact."""
+    sc = I.uniform_box_scene(96, 77, xy=(-2.0, 2.0), z=(2.0, 4.0), log_scale=(-0.7, 0.4))
+    cam = I.identity_camera(1024, 768, 400.0)
+    ras = _run([sc], [cam], tile=tile)
+    bs = _check_sort(ras, [sc], [cam], tile)
+    r = bs["ranges"]
+    assert len(bs["keys"]) > 20 * 96 and (r[:, 1] - r[:, 0]).max() > 40
