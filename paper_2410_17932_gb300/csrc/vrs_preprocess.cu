@@ -38,7 +38,7 @@ struct PreParams {
 // (only visible Gaussians' colour coefficients are ever read), checks it,
 // evaluates the view-dependent colour, writes the projected record and emits
 // the pair's tile keys cooperatively across the warp (prefix sum of the
-// per-lane counts, one atomic per warp, coalesced key writes).
+// per-lane counts, one atomic per CTA for the slots, coalesced key writes).
 constexpr int kDecideThreads = 256;
 constexpr int kPairThreads = 128;
 
@@ -111,9 +111,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
     const unsigned long long n_pairs = n_pairs_raw < p.pair_cap ? n_pairs_raw : p.pair_cap;
     const bool vec = (12 * K) % 16 == 0 && (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
     bool nonfinite_sh = false;
+    __shared__ uint32_t s_wtot[kPairThreads / 32];
+    __shared__ unsigned long long s_wbase[kPairThreads / 32];
+    const int wp = threadIdx.x >> 5;
     const unsigned long long stride = (unsigned long long)gridDim.x * kPairThreads;
-    for (unsigned long long w0 = (unsigned long long)blockIdx.x * kPairThreads + (threadIdx.x & ~31);
-         w0 < n_pairs; w0 += stride) {
+    for (unsigned long long c0 = (unsigned long long)blockIdx.x * kPairThreads; c0 < n_pairs; c0 += stride) {
+        const unsigned long long w0 = c0 + (threadIdx.x & ~31);
         const unsigned long long i = w0 + lane;
         const bool act = i < n_pairs;
         uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = e0;
@@ -205,18 +208,33 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             if (lane >= o) incl += t;
         }
         const uint32_t total = __shfl_sync(FULL, incl, 31);
+        // one atomic per CTA: the warps' totals are summed and the CTA's slots split
+        if (lane == 0) s_wtot[wp] = total;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long sum = 0;
+            for (int q = 0; q < kPairThreads / 32; ++q) sum += s_wtot[q];
+            unsigned long long b = sum ? atomicAdd(&p.st->instances, sum) : 0ull;
+            for (int q = 0; q < kPairThreads / 32; ++q) {
+                s_wbase[q] = b;
+                b += s_wtot[q];
+            }
+        }
+        __syncthreads();
+        const unsigned long long base = s_wbase[wp];
+        __syncthreads();
         if (total == 0) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.st->instances, (unsigned long long)total);
-        base = __shfl_sync(FULL, base, 0);
         const uint32_t excl = incl - cnt;
         const int nx = vis ? x1 - x0 : 1;
         const uint32_t dbits = e1.w;
         const uint32_t rid = (uint32_t)(V.rec_base + g);
         const long long first = V.tile_base + (long long)y0 * V.gw + x0;   // tile id of (x0, y0)
         const int gw = V.gw;
-        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-            const uint32_t k = k0 + lane;
+        // two keys per lane per round: independent shuffle chains overlap
+        for (uint32_t k0 = 0; k0 < total; k0 += 64) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const uint32_t k = k0 + 32 * u + lane;
             int j = 0;
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1) {
@@ -251,6 +269,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
                     if (p.tile_cnt) atomicAdd(p.tile_cnt + tid64, 1u);
                 }
             }
+          }
         }
         if (lane == 0 && base + total > p.cap) atomicOr(&p.st->flags, ST_CAPACITY);
     }

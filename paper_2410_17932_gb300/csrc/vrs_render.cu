@@ -34,41 +34,62 @@ struct FwdArgs {
     int persistent;
 };
 
-struct PixAcc {
-    float T, r, g, b, D;
-    uint32_t last, stop;
-    bool done;
+// The state of a thread's two pixels, packed in pairs so that the blend's
+// multiplies and fused multiply-adds issue as FP32x2 instructions.  Each
+// component of a packed operation is the correctly rounded scalar operation,
+// so the result is bit for bit that of the scalar code.
+struct PixAcc2 {
+    float2 T, R, G, B, D;
+    uint32_t last0, last1, stop0, stop1;
+    bool done0, done1;
 };
 
-// One splat at one pixel, front to back: skip below 1/255, stop before T would
-// drop under 1e-4, otherwise blend.  Written as selects (no branches).  COUNT
-// also tracks the stop position and the blend count for the work counters.
-__device__ __forceinline__ bool pix_hit(const PixAcc &P, float q, const float4 &B)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// One splat at a thread's two pixels, front to back: skip below 1/255, stop
+// before T would drop under 1e-4, otherwise blend.  Written as selects (no
+// branches).  q holds the two pixels' quadratic forms; B = (l2, lo, lt,
+// depth), C = (r, g, b, list position).  COUNT also tracks the stop position
+// and the blend count for the work counters.
+template <bool COUNT>
+__device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &B, const float4 &C,
+                                            uint32_t &n_blend)
 {
-    return !P.done && q <= B.z;
+    const bool h0 = !P.done0 && q.x <= B.z, h1 = !P.done1 && q.y <= B.z;
+    const float2 e = __ffma2_rn(q, f2(-1.f), f2(B.y));                     // lo - q
+    const float2 al = make_float2(fminf(ex2_approx(e.x), 0.99f), fminf(ex2_approx(e.y), 0.99f));
+    const float2 Tn = __fmul2_rn(P.T, __ffma2_rn(al, f2(-1.f), f2(1.f)));  // T (1 - alpha)
+    const float2 w = __fmul2_rn(al, P.T);
+    const bool s0 = h0 && Tn.x < 1e-4f, s1 = h1 && Tn.y < 1e-4f;
+    const bool b0 = h0 && !s0, b1 = h1 && !s1;
+    const float2 wt = make_float2(b0 ? w.x : 0.f, b1 ? w.y : 0.f);
+    P.R = __ffma2_rn(f2(C.x), wt, P.R);
+    P.G = __ffma2_rn(f2(C.y), wt, P.G);
+    P.B = __ffma2_rn(f2(C.z), wt, P.B);
+    P.D = __ffma2_rn(f2(B.w), wt, P.D);
+    P.T = make_float2(b0 ? Tn.x : P.T.x, b1 ? Tn.y : P.T.y);
+    const uint32_t pos = (uint32_t)__float_as_int(C.w);
+    P.last0 = b0 ? pos : P.last0;
+    P.last1 = b1 ? pos : P.last1;
+    P.done0 = P.done0 || s0;
+    P.done1 = P.done1 || s1;
+    if (COUNT) {
+        P.stop0 = s0 ? pos : P.stop0;
+        P.stop1 = s1 ? pos : P.stop1;
+        n_blend += (b0 ? 1u : 0u) + (b1 ? 1u : 0u);
+    }
 }
 
-template <bool COUNT>
-__device__ __forceinline__ void pix_update(PixAcc &P, float q, bool h, const float4 &B, const float4 &C,
-                                           uint32_t &n_blend)
+// The two pixels' quadratic forms of one splat (see pair_q2), the last step packed.
+__device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc, float pyc)
 {
-    const float al = pair_alpha(B.y, q);
-    const float Tn = P.T * (1.f - al);
-    const bool stop = h && Tn < 1e-4f;
-    const bool blend = h && !stop;
-    const float wt = blend ? al * P.T : 0.f;
-    P.r = fmaf(C.x, wt, P.r);
-    P.g = fmaf(C.y, wt, P.g);
-    P.b = fmaf(C.z, wt, P.b);
-    P.D = fmaf(B.w, wt, P.D);
-    const uint32_t pos = (uint32_t)__float_as_int(C.w);
-    P.T = blend ? Tn : P.T;
-    P.last = blend ? pos : P.last;
-    P.done = P.done || stop;
-    if (COUNT) {
-        P.stop = stop ? pos : P.stop;
-        n_blend += blend ? 1u : 0u;
-    }
+    const float dy = __fsub_rn(A.y, pyc);
+    const float m = __fmul_rn(A.w, dy);
+    const float s = __fmul_rn(l2, dy);
+    const float s2 = __fmul_rn(s, s);
+    const float t0 = __fmaf_rn(A.z, __fsub_rn(A.x, pxc), m);
+    const float2 t = make_float2(t0, __fsub_rn(t0, A.z));
+    return __ffma2_rn(t, t, f2(s2));
 }
 
 template <int TS, bool COUNT>
@@ -119,11 +140,17 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
         tile_origin((float)(ty * TS), pp.y, oyh, oyl);
         const uint2 range = live_range(a.ranges, t, a.st, a.cap);
 
-        PixAcc P0{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in0 ? range.y - range.x : 0u, !in0};
-        PixAcc P1{1.f, 0.f, 0.f, 0.f, 0.f, 0u, in1 ? range.y - range.x : 0u, !in1};
+        PixAcc2 P;
+        P.T = f2(1.f);
+        P.R = P.G = P.B = P.D = f2(0.f);
+        P.last0 = P.last1 = 0u;
+        P.stop0 = in0 ? range.y - range.x : 0u;
+        P.stop1 = in1 ? range.y - range.x : 0u;
+        P.done0 = !in0;
+        P.done1 = !in1;
 
         for (uint32_t bs = range.x; bs < range.y; bs += Cfg::BATCH) {
-            if (__syncthreads_and(P0.done && P1.done)) break;
+            if (__syncthreads_and(P.done0 && P.done1)) break;
             const uint32_t j = bs + tid;
             const uint32_t rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
             uint32_t mask = 0u;
@@ -152,51 +179,45 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 cnt += __popc(bal);
             }
             __syncwarp();
-            if (!__all_sync(FULL, P0.done && P1.done)) {
+            if (!__all_sync(FULL, P.done0 && P.done1)) {
                 int k = 0;
                 for (; k + 1 < cnt; k += 2) {
                     const int j0 = slist[w][k], j1 = slist[w][k + 1];
                     const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
                     const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1];
-                    float q00, q01, q10, q11;
-                    pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
-                    pair_q2(A1.x, A1.y, A1.z, A1.w, B1.x, pxc, pyc, q10, q11);
-                    pix_update<COUNT>(P0, q00, pix_hit(P0, q00, B0), B0, C0, n_blend);
-                    pix_update<COUNT>(P1, q01, pix_hit(P1, q01, B0), B0, C0, n_blend);
-                    pix_update<COUNT>(P0, q10, pix_hit(P0, q10, B1), B1, C1, n_blend);
-                    pix_update<COUNT>(P1, q11, pix_hit(P1, q11, B1), B1, C1, n_blend);
+                    const float2 q0 = pair_q2v(A0, B0.x, pxc, pyc);
+                    const float2 q1 = pair_q2v(A1, B1.x, pxc, pyc);
+                    pix_update2<COUNT>(P, q0, B0, C0, n_blend);
+                    pix_update2<COUNT>(P, q1, B1, C1, n_blend);
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
-                    float q00, q01;
-                    pair_q2(A0.x, A0.y, A0.z, A0.w, B0.x, pxc, pyc, q00, q01);
-                    pix_update<COUNT>(P0, q00, pix_hit(P0, q00, B0), B0, C0, n_blend);
-                    pix_update<COUNT>(P1, q01, pix_hit(P1, q01, B0), B0, C0, n_blend);
+                    pix_update2<COUNT>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
                 }
             }
             __syncthreads();
         }
-        n_eval += (in0 ? P0.stop : 0u) + (in1 ? P1.stop : 0u);
+        n_eval += (in0 ? P.stop0 : 0u) + (in1 ? P.stop1 : 0u);
         const int64_t HW = (int64_t)V.w * V.h;
         const int64_t lp = (int64_t)py * V.w + px;
         const int64_t pix = V.pix_base + lp;
         float *rgb = a.rgb + 3 * V.pix_base;
         if (in0) {
-            rgb[lp] = P0.r;
-            rgb[HW + lp] = P0.g;
-            rgb[2 * HW + lp] = P0.b;
-            a.depth[pix] = P0.D;
-            a.Tf[pix] = P0.T;
-            a.ncontrib[pix] = P0.last;
+            rgb[lp] = P.R.x;
+            rgb[HW + lp] = P.G.x;
+            rgb[2 * HW + lp] = P.B.x;
+            a.depth[pix] = P.D.x;
+            a.Tf[pix] = P.T.x;
+            a.ncontrib[pix] = P.last0;
         }
         if (in1) {
-            rgb[lp + 1] = P1.r;
-            rgb[HW + lp + 1] = P1.g;
-            rgb[2 * HW + lp + 1] = P1.b;
-            a.depth[pix + 1] = P1.D;
-            a.Tf[pix + 1] = P1.T;
-            a.ncontrib[pix + 1] = P1.last;
+            rgb[lp + 1] = P.R.y;
+            rgb[HW + lp + 1] = P.G.y;
+            rgb[2 * HW + lp + 1] = P.B.y;
+            a.depth[pix + 1] = P.D.y;
+            a.Tf[pix + 1] = P.T.y;
+            a.ncontrib[pix + 1] = P.last1;
         }
     }
     if (!COUNT) return;
