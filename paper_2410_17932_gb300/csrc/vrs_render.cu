@@ -59,15 +59,17 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &
     const float2 e = __ffma2_rn(q, f2(-1.f), f2(B.y));                     // lo - q
     const float2 al = make_float2(fminf(ex2_approx(e.x), 0.99f), fminf(ex2_approx(e.y), 0.99f));
     const float2 Tn = __fmul2_rn(P.T, __ffma2_rn(al, f2(-1.f), f2(1.f)));  // T (1 - alpha)
-    const float2 w = __fmul2_rn(al, P.T);
     const bool s0 = h0 && Tn.x < 1e-4f, s1 = h1 && Tn.y < 1e-4f;
     const bool b0 = h0 && !s0, b1 = h1 && !s1;
-    const float2 wt = make_float2(b0 ? w.x : 0.f, b1 ? w.y : 0.f);
+    // alpha where the pixel blends, 0 elsewhere: then T (1 - a) is T' or T exactly,
+    // and a T is the weight or 0, without selects on T and the weight
+    const float2 a = make_float2(b0 ? al.x : 0.f, b1 ? al.y : 0.f);
+    const float2 wt = __fmul2_rn(a, P.T);
     P.R = __ffma2_rn(f2(C.x), wt, P.R);
     P.G = __ffma2_rn(f2(C.y), wt, P.G);
     P.B = __ffma2_rn(f2(C.z), wt, P.B);
     P.D = __ffma2_rn(f2(B.w), wt, P.D);
-    P.T = make_float2(b0 ? Tn.x : P.T.x, b1 ? Tn.y : P.T.y);
+    P.T = __fmul2_rn(P.T, __ffma2_rn(a, f2(-1.f), f2(1.f)));
     const uint32_t pos = (uint32_t)__float_as_int(C.w);
     P.last0 = b0 ? pos : P.last0;
     P.last1 = b1 ? pos : P.last1;
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
     using Cfg = BlendCfg<TS>;
-    __shared__ float4 sA[Cfg::BATCH], sB[Cfg::BATCH], sC[Cfg::BATCH];
+    __shared__ float4 sR[Cfg::BATCH][3];   // staged splats: A, B, C of one instance together
     __shared__ uint32_t smask[Cfg::BATCH];
     __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
     __shared__ int64_t s_tile;
@@ -164,9 +166,9 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 for (int ww = 0; ww < Cfg::WARPS; ++ww)
                     if (cull_block(cs, (float)((ww % Cfg::WGX) * 8) + 0.5f, (float)((ww / Cfg::WGX) * 8) + 0.5f))
                         mask |= 1u << ww;
-                sA[tid] = A;
-                sB[tid] = B;
-                sC[tid] = C;
+                sR[tid][0] = A;
+                sR[tid][1] = B;
+                sR[tid][2] = C;
             }
             smask[tid] = mask;
             __syncthreads();
@@ -183,8 +185,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 int k = 0;
                 for (; k + 1 < cnt; k += 2) {
                     const int j0 = slist[w][k], j1 = slist[w][k + 1];
-                    const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
-                    const float4 A1 = sA[j1], B1 = sB[j1], C1 = sC[j1];
+                    const float4 A0 = sR[j0][0], B0 = sR[j0][1], C0 = sR[j0][2];
+                    const float4 A1 = sR[j1][0], B1 = sR[j1][1], C1 = sR[j1][2];
                     const float2 q0 = pair_q2v(A0, B0.x, pxc, pyc);
                     const float2 q1 = pair_q2v(A1, B1.x, pxc, pyc);
                     pix_update2<COUNT>(P, q0, B0, C0, n_blend);
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
-                    const float4 A0 = sA[j0], B0 = sB[j0], C0 = sC[j0];
+                    const float4 A0 = sR[j0][0], B0 = sR[j0][1], C0 = sR[j0][2];
                     pix_update2<COUNT>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
                 }
             }
