@@ -410,7 +410,7 @@ def main():
     ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent)
     ras.forward()                       # sizes the instance list
     code, flags, inst = ras.last_status
-    pair_evals, pair_blends = ras.count_pairs()   # algorithmic units, one untimed counting pass
+    pair_evals, pair_blends, block_evals = ras.count_pairs()   # work units, one untimed counting pass
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -465,6 +465,7 @@ def main():
                 "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
                 "units": f"{pair_blends} blended Gaussian-pixel pairs x {ALU_OPS_PER_BLEND} ops",
                 "context": {"definitional_evaluations": pair_evals,
+                            "kernel_evaluations_after_culling": 64 * block_evals,
                             "evaluations_per_s": round(pair_evals / (stage['render_fwd'] * 1e-3), 1)}}
     else:
         n = sum(s.n for s in scenes)

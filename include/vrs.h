@@ -175,6 +175,9 @@ typedef struct {
                                   pixel, its tile-list position where it stopped, else the list
                                   length) */
     uint64_t pair_blends;      /* of those, pairs that were blended */
+    uint64_t block_evals;      /* with plan.count_pairs: (instance, 8x8 pixel block) pairs the
+                                  blend kernel evaluated after its culling (each covers 64
+                                  Gaussian-pixel evaluations) */
 } vrs_run_info;
 
 /* Sizes a batch of n_views views over n_scenes scenes and lays out the

@@ -41,6 +41,7 @@ __global__ void k_noalloc_begin(DevStatus *st, unsigned long long n)
     st->instances = n;
     st->pair_evals = 0ull;
     st->pair_blends = 0ull;
+    st->block_evals = 0ull;
 }
 
 namespace {

@@ -103,17 +103,17 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     __shared__ uint32_t smask[Cfg::BATCH];
     __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
     __shared__ int64_t s_tile;
-    __shared__ unsigned long long s_cnt[2];
+    __shared__ unsigned long long s_cnt[3];
 
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
     const uint32_t lmask = lanemask_lt();
-    if (tid == 0) s_cnt[0] = s_cnt[1] = 0ull;
+    if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0ull;
     __syncthreads();
     const bool skip_all = (a.st->flags & ST_CAPACITY) != 0;
-    uint32_t n_eval = 0, n_blend = 0;
+    uint32_t n_eval = 0, n_blend = 0, n_blk = 0;
 
     for (int64_t iter = 0; !skip_all; ++iter) {
         int64_t t;
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             }
             __syncwarp();
             if (!__all_sync(FULL, P.done0 && P.done1)) {
+                if (COUNT) n_blk += cnt;
                 int k = 0;
                 for (; k + 1 < cnt; k += 2) {
                     const int j0 = slist[w][k], j1 = slist[w][k + 1];
@@ -225,14 +226,16 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     if (!COUNT) return;
     // algorithmic work counters: warp sums, one shared add per warp, one RED per CTA
     const uint32_t ev = __reduce_add_sync(FULL, n_eval), bl = __reduce_add_sync(FULL, n_blend);
-    if (lane == 0 && (ev | bl)) {
+    if (lane == 0 && (ev | bl | n_blk)) {
         atomicAdd(&s_cnt[0], (unsigned long long)ev);
         atomicAdd(&s_cnt[1], (unsigned long long)bl);
+        atomicAdd(&s_cnt[2], (unsigned long long)n_blk);   // warp-uniform
     }
     __syncthreads();
-    if (tid == 0 && (s_cnt[0] | s_cnt[1])) {
+    if (tid == 0 && (s_cnt[0] | s_cnt[1] | s_cnt[2])) {
         atomicAdd(&a.st->pair_evals, s_cnt[0]);
         atomicAdd(&a.st->pair_blends, s_cnt[1]);
+        atomicAdd(&a.st->block_evals, s_cnt[2]);
     }
 }
 

@@ -145,7 +145,8 @@ class Rasterizer:
         self.render_fwd(stream=stream)
 
     def count_pairs(self, stream=None):
-        """Gaussian-pixel pairs evaluated and blended by one counting forward pass (untimed use)."""
+        """One counting forward pass (untimed use): Gaussian-pixel pairs evaluated by the
+        definition and blended, and (instance, 8x8 block) pairs the blend kernel evaluated."""
         self.preprocess(stream)
         self.bin_sort(stream)
         self.plan.count_pairs = 1
@@ -156,7 +157,7 @@ class Rasterizer:
         info = L.vrs_run_info()
         L._check(L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(stream)),
                  "count_pairs")
-        return int(info.pair_evals), int(info.pair_blends)
+        return int(info.pair_evals), int(info.pair_blends), int(info.block_evals)
 
     def status(self, stream=None):
         info = L.vrs_run_info()
