@@ -54,6 +54,17 @@ class OrcCamera(ctypes.Structure):
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
 
 
+class OrcCullOpts(ctypes.Structure):
+    _fields_ = [("alpha_min", ctypes.c_float), ("rel_margin", ctypes.c_float),
+                ("abs_margin", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+# Defaults of the occlusion test's reading of Sec. 3.3 (see orc_cull_points).
+CULL_ALPHA_MIN = 0.5
+CULL_REL_MARGIN = 0.02
+CULL_ABS_MARGIN = 0.05
+
+
 class OrcFlagOpts(ctypes.Structure):
     _fields_ = [("alpha_win", ctypes.c_double), ("t_win", ctypes.c_double)]
 
@@ -95,6 +106,10 @@ def lib():
             L.orc_param_grads.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                           ctypes.POINTER(OrcCamera), P, P, P, P, P, P, P]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_cull_points.restype = None
+            L.orc_cull_points.argtypes = [ctypes.c_int64, P, ctypes.POINTER(OrcCamera), ctypes.c_int32,
+                                          ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(OrcCullOpts), P]
             _lib = L
     return _lib
 
@@ -299,3 +314,23 @@ def bin_sort(scenes: Sequence, views: Sequence, tile: int = 16, decs: Optional[L
         ranges[ranges[:, 0] == ranges[:, 1]] = 0      # an empty tile's range is {0, 0}
     return dict(keys=keys, vals=vals, ranges=ranges, counts=counts, rec_base=rec_base,
                 tile_base=tile_base)
+
+
+def cull_points(points, cam, x0: int, y0: int, depth, T_final, alpha_min: float = CULL_ALPHA_MIN,
+                rel_margin: float = CULL_REL_MARGIN, abs_margin: float = CULL_ABS_MARGIN) -> np.ndarray:
+    """Sec. 3.3 occlusion culling of neural points against the Eq. 1 depth map.
+
+    points [m, 3] world positions; cam the subfrustum (foveal crop) camera whose
+    pixel (i, j) is pixel (i + x0, j + y0) of `depth` / `T_final` ([H, W]).
+    Returns uint8 [m]: 0 outside the subfrustum, 1 occluded, 2 kept (FP32 decisions)."""
+    pts = _f32(points).reshape(-1, 3)
+    d = _f32(depth)
+    t = _f32(T_final)
+    assert d.shape == t.shape and d.ndim == 2
+    out = np.zeros(len(pts), np.uint8)
+    o = OrcCullOpts(float(np.float32(alpha_min)), float(np.float32(rel_margin)),
+                    float(np.float32(abs_margin)), 0)
+    c = camera(cam)
+    lib().orc_cull_points(len(pts), _p(pts), ctypes.byref(c), int(x0), int(y0), _p(d), _p(t),
+                          d.shape[1], d.shape[0], ctypes.byref(o), _p(out))
+    return out

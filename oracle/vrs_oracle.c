@@ -866,3 +866,74 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Occlusion culling of the foveal neural points against the approximate depth
+ * buffer (Sec. 3.3: points are projected with the subfrustum's adapted
+ * projection, those outside it are discarded, and those hidden behind the
+ * Gaussians are culled with the Eq. 1 depth of Sec. 3.2).
+ *
+ * The paper does not spell out the occlusion test; this oracle states one
+ * reading.  Eq. 1 accumulates d_i alpha_i T_i without normalisation, so the
+ * surface depth of a pixel is taken as d / (1 - T_final), and a pixel occludes
+ * only where its accumulated opacity 1 - T_final is at least alpha_min.  A
+ * point is occluded when its view depth exceeds that surface depth scaled by
+ * (1 + rel_margin) plus abs_margin.
+ *
+ * Every step is one correctly rounded FP32 operation in the order written, so
+ * that the three-way decision is a definition the kernel can meet exactly.
+ * The subfrustum camera is the eye camera with its principal point moved by
+ * the crop origin (x0, y0); its pixel (i, j) is pixel (i + x0, j + y0) of the
+ * depth map (map_w x map_h, row-major).
+ * mask[p]: 0 outside the subfrustum (or behind znear, or non-finite), 1 occluded, 2 kept. */
+typedef struct { float alpha_min, rel_margin, abs_margin; int32_t reserved; } orc_cull_opts;
+
+void orc_cull_points(int64_t m, const float *pts, const orc_camera *cam, int32_t x0, int32_t y0,
+                     const float *depth, const float *Tfin, int32_t map_w, int32_t map_h,
+                     const orc_cull_opts *o, uint8_t *mask)
+{
+    const float *R = cam->R;
+    const float scale = 1.0f + o->rel_margin;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < m; ++p) {
+        const float px = pts[3 * p], py = pts[3 * p + 1], pz = pts[3 * p + 2];
+        uint8_t r = 0;
+        /* camera space, x_cam = R x + t */
+        float x = R[0] * px;
+        x = x + R[1] * py;
+        x = x + R[2] * pz;
+        x = x + cam->t[0];
+        float y = R[3] * px;
+        y = y + R[4] * py;
+        y = y + R[5] * pz;
+        y = y + cam->t[1];
+        float z = R[6] * px;
+        z = z + R[7] * py;
+        z = z + R[8] * pz;
+        z = z + cam->t[2];
+        if (z > cam->znear && f_isfinite(x) && f_isfinite(y)) {
+            const float iz = 1.0f / z;
+            float u = x * iz;
+            u = cam->fx * u;
+            u = u + cam->cx;
+            float v = y * iz;
+            v = cam->fy * v;
+            v = v + cam->cy;
+            if (u >= 0.0f && u < (float)cam->width && v >= 0.0f && v < (float)cam->height) {
+                const int32_t mi = (int32_t)u + x0, mj = (int32_t)v + y0;
+                if (mi >= 0 && mi < map_w && mj >= 0 && mj < map_h) {
+                    const int64_t pix = (int64_t)mj * map_w + mi;
+                    const float a = 1.0f - Tfin[pix];
+                    r = 2;
+                    if (a >= o->alpha_min) {
+                        const float dn = depth[pix] / a;
+                        float thr = dn * scale;
+                        thr = thr + o->abs_margin;
+                        if (z > thr) r = 1;
+                    }
+                }
+            }
+        }
+        mask[p] = r;
+    }
+}

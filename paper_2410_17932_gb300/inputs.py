@@ -122,6 +122,32 @@ def uniform_box_scene(n: int, seed: int, xy=(-1.0, 1.0), z=(2.0, 6.0),
     return Scene(means, log_scales, quats, opacity_logits, sh, sh_degree)
 
 
+def _room_clusters(rng, n_clusters: int, room: float):
+    """Cluster geometry of the room generator: centres ~ U(room), unit plane
+    normals, two in-plane axes and in-plane extents ~ U[0.3, 3] m."""
+    centres = rng.uniform(-room, room, (n_clusters, 3))
+    normals = rng.standard_normal((n_clusters, 3))
+    normals /= np.linalg.norm(normals, axis=1, keepdims=True)
+    helper = np.where(np.abs(normals[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]])
+    ax_u = np.cross(normals, helper)
+    ax_u /= np.linalg.norm(ax_u, axis=1, keepdims=True)
+    ax_v = np.cross(normals, ax_u)
+    ext = rng.uniform(0.3, 3.0, (n_clusters, 2))
+    return centres, normals, ax_u, ax_v, ext
+
+
+def _cluster_points(rng, clusters, n: int, room: float, thick: float = 0.02) -> np.ndarray:
+    """n points assigned uniformly to the clusters, Gaussian in-plane spread, 2 cm thickness."""
+    centres, normals, ax_u, ax_v, ext = clusters
+    cl = rng.integers(0, len(centres), n)
+    g = rng.standard_normal((n, 3))
+    pts = (centres[cl]
+           + ax_u[cl] * (g[:, :1] * ext[cl, :1])
+           + ax_v[cl] * (g[:, 1:2] * ext[cl, 1:2])
+           + normals[cl] * (g[:, 2:3] * thick))
+    return np.clip(pts, -room, room).astype(np.float32)
+
+
 def clustered_room_scene(n: int, seed: int, log_scale=(-4.0, 0.7),
                          opacity=(0.0, 1.0), n_clusters: int = 256,
                          room: float = 10.0, sh_degree: int = 3,
@@ -133,22 +159,8 @@ def clustered_room_scene(n: int, seed: int, log_scale=(-4.0, 0.7),
     assigned uniformly to clusters and clipped to the room.
     """
     rng = _rng(seed)
-    centres = rng.uniform(-room, room, (n_clusters, 3))
-    normals = rng.standard_normal((n_clusters, 3))
-    normals /= np.linalg.norm(normals, axis=1, keepdims=True)
-    helper = np.where(np.abs(normals[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]])
-    ax_u = np.cross(normals, helper)
-    ax_u /= np.linalg.norm(ax_u, axis=1, keepdims=True)
-    ax_v = np.cross(normals, ax_u)
-    ext = rng.uniform(0.3, 3.0, (n_clusters, 2))
-    thick = 0.02
-    cl = rng.integers(0, n_clusters, n)
-    g = rng.standard_normal((n, 3))
-    pts = (centres[cl]
-           + ax_u[cl] * (g[:, :1] * ext[cl, :1])
-           + ax_v[cl] * (g[:, 1:2] * ext[cl, 1:2])
-           + normals[cl] * (g[:, 2:3] * thick))
-    means = np.clip(pts, -room, room).astype(np.float32)
+    clusters = _room_clusters(rng, n_clusters, room)
+    means = _cluster_points(rng, clusters, n, room)
     log_scales = rng.normal(log_scale[0], log_scale[1], (n, 3)).astype(np.float32)
     quats = _random_quats(rng, n)
     opacity_logits = rng.normal(opacity[0], opacity[1], n).astype(np.float32)
@@ -158,6 +170,35 @@ def clustered_room_scene(n: int, seed: int, log_scale=(-4.0, 0.7),
     if K > 1:
         sh[:, 1:, :] = rng.normal(0.0, sh_hi_std, (n, K - 1, 3)).astype(np.float32)
     return Scene(means, log_scales, quats, opacity_logits, sh, sh_degree)
+
+
+def neural_points(n: int, seed: int, cluster_seed: int, n_clusters: int = 256,
+                  room: float = 10.0) -> np.ndarray:
+    """[n, 3] float32 neural-point positions on the planar clusters of the room
+    generator seeded with `cluster_seed` (the same surfaces as that scene's
+    Gaussians), drawn with their own seed."""
+    clusters = _room_clusters(_rng(cluster_seed), n_clusters, room)
+    return _cluster_points(_rng(seed), clusters, n, room)
+
+
+def synthetic_depth_map(width: int, height: int, seed: int, n_rects: int = 24):
+    """A float32 Eq. 1 depth map and final transmittance of `n_rects` layered
+    fronto-slanted planar patches: per pixel, depth = z_surface * (1 - T) as a
+    single surface of opacity 1 - T would give; the background has T = 1."""
+    rng = _rng(seed)
+    z = np.zeros((height, width), np.float64)
+    T = np.ones((height, width), np.float64)
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float64)
+    for _ in range(n_rects):
+        x0, y0 = rng.integers(0, width), rng.integers(0, height)
+        w, h = rng.integers(1, width // 2 + 2), rng.integers(1, height // 2 + 2)
+        a = rng.choice([rng.uniform(0.0, 0.3), rng.uniform(0.3, 0.7), rng.uniform(0.7, 0.9999)])
+        z0, gx, gy = rng.uniform(1.0, 8.0), rng.normal(0, 2e-3), rng.normal(0, 2e-3)
+        sel = (xx >= x0) & (xx < x0 + w) & (yy >= y0) & (yy < y0 + h)
+        z[sel] = np.maximum(0.3, z0 + gx * (xx[sel] - x0) + gy * (yy[sel] - y0))
+        T[sel] = 1.0 - a
+    depth = (z * (1.0 - T)).astype(np.float32)
+    return depth, T.astype(np.float32)
 
 
 def _yaw_pitch(yaw: float, pitch: float) -> np.ndarray:
@@ -238,6 +279,17 @@ def dense_stereo_3m(n: int = 3_000_000, seed: Optional[int] = None, aligned=True
     eyes = stereo_eyes(seed + 1000)
     crops = [foveal_crop(e, seed + 2000 + i, aligned=aligned) for i, e in enumerate(eyes)]
     return [sc], eyes + crops
+
+
+def foveal_points_5m(n_points: int = 5_000_000, seed: Optional[int] = None, size: int = 512):
+    """Foveal neural-point culling: the periphery scene's left eye, a size x size
+    foveal crop at a seeded gaze (the subfrustum), and 5 M neural points on the
+    same surfaces as the scene's 0.5 M Gaussians."""
+    seed = SEED_BASE + 1 if seed is None else seed
+    scenes, eyes = periphery_stereo_05m(seed=seed)
+    crop = foveal_crop(eyes[0], seed + 5000, size=size, aligned=False)
+    pts = neural_points(n_points, seed + 6000, cluster_seed=seed)
+    return scenes, eyes[0], crop, pts
 
 
 def training_view_1m(n: int = 1_000_000, seed: Optional[int] = None):
