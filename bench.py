@@ -367,6 +367,33 @@ def run_extras(args):
                                "speedup": round(ms_per_view / ms_batched, 3), "autotuned": best,
                                "identical_images": bool(same),
                                "pixels": int(batched.plan.n_pixels), "instances": int(batched.last_status[2])}
+    del batched, runner, singles, sts
+    # foveal neural-point culling (Sec. 3.3): 5 M points against the left eye's Eq. 1 depth
+    # inside a 512x512 subfrustum at a seeded gaze
+    from paper_2410_17932_gb300.cull import PointCuller
+    scenes, eye, crop, pts = I.foveal_points_5m()
+    ras = Rasterizer([SceneTensors.from_scene(s) for s in scenes], [eye])
+    ras.forward()
+    _, depth, T = ras.outputs(0)
+    x0, y0 = int(round(eye.cx - crop.cx)), int(round(eye.cy - crop.cy))
+    p = torch.as_tensor(pts, device="cuda")
+    culler = PointCuller(len(pts))
+    cull = lambda: culler.cull_async(p, crop, x0, y0, depth, T)    # noqa: E731
+    for _ in range(3):
+        cull()
+    ms_cull = _time_loop(cull, flush, args.extra_steps)
+    counts = np.bincount(culler.mask.cpu().numpy(), minlength=3)
+    n_kept = int(culler.n_kept.item())
+    m = len(pts)
+    byts = 12 * m + m + 4 * n_kept        # points read, decisions written, kept indices written
+    peaks, src = measured_peaks()
+    out["foveal_points_5m"] = {
+        "cull_ms": round(ms_cull, 4), "points_per_s": round(m / (ms_cull * 1e-3), 1),
+        "outside": int(counts[0]), "occluded": int(counts[1]), "kept": int(counts[2]),
+        "roofline": {"bound": "hbm", "kernel": "k_cull_points", "achieved": round(byts / (ms_cull * 1e-3) / 1e9, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(byts / (ms_cull * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "bytes_per_launch": byts, "peak_source": src}}
     return out
 
 

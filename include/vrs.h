@@ -280,6 +280,48 @@ vrs_status vrs_sort_pairs_noalloc(const uint64_t *keys_in, const uint32_t *vals_
                                   uint64_t *keys_out, uint32_t *vals_out, int64_t n,
                                   int32_t key_bits, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Occlusion culling of the foveal neural points (Sec. 3.3).  After the
+ * periphery is rendered, the fovea's subfrustum camera (the eye camera with its
+ * principal point moved to a crop window, an "adapted projection matrix")
+ * projects the neural point cloud; points outside the subfrustum are
+ * discarded, and points hidden behind the Gaussians are culled against the
+ * approximate depth buffer of Eq. 1 (Sec. 3.2) that vrs_render_fwd wrote.
+ *
+ * The paper does not spell the test out; the library's reading: Eq. 1 is
+ * unnormalised, so a pixel's surface depth is depth / (1 - T_final), and a
+ * pixel occludes only where its accumulated opacity 1 - T_final is at least
+ * alpha_min.  A point at view depth z on that pixel is occluded when
+ *   z > depth / (1 - T_final) * (1 + rel_margin) + abs_margin.
+ * Every step is a correctly rounded FP32 operation in a fixed order: camera
+ * space x = ((R0 px + R1 py) + R2 pz) + t0 (and y, z alike); outside when not
+ * z > znear or x, y non-finite; u = fx (x (1/z)) + cx, v alike; inside when
+ * 0 <= u < width and 0 <= v < height; map pixel (trunc(u) + x0, trunc(v) + y0). */
+typedef struct {
+    float alpha_min;           /* default 0.5 */
+    float rel_margin;          /* default 0.02 */
+    float abs_margin;          /* default 0.05 (scene units) */
+    int32_t reserved;          /* 0 */
+} vrs_cull_opts;
+
+/* points: device, [n_points][3] float world positions (4-byte aligned; 16-byte
+ * aligned bases load faster).  fovea: host, the subfrustum camera; its pixel
+ * (i, j) is pixel (i + x0, j + y0) of the depth map.  depth, T_final: device,
+ * [map_h][map_w] float (one view of vrs_render_fwd's outputs).  opts: host,
+ * NULL for the defaults.  Outputs, all device and written in full:
+ *   mask[n_points]   0 outside the subfrustum, 1 occluded, 2 kept;
+ *   kept[n_points]   (nullable) indices of the kept points, first *n_kept
+ *                    entries, in no particular order;
+ *   n_kept           one uint64, the number of kept points (set, not added).
+ * Returns VRS_ERR_INVALID for n_points < 0 or >= 2^32, a NULL required pointer,
+ * a camera or map size below 1, or a reserved field that is not 0;
+ * VRS_ERR_CUDA on a launch failure.  n_points == 0 writes *n_kept = 0.  No
+ * allocation, no synchronisation; stream ordered on `stream` and capturable. */
+vrs_status vrs_cull_points(const float *points, int64_t n_points, const vrs_camera *fovea,
+                           int32_t x0, int32_t y0, const float *depth, const float *T_final,
+                           int32_t map_w, int32_t map_h, const vrs_cull_opts *opts, uint8_t *mask,
+                           uint32_t *kept, uint64_t *n_kept, void *stream);
+
 /* A static, human-readable name of a status. */
 const char *vrs_status_string(vrs_status status);
 

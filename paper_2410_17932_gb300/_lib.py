@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+from typing import Optional
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvrs.so")
@@ -62,6 +63,10 @@ class vrs_run_info(ctypes.Structure):
                 ("pair_blends", _u64), ("block_evals", _u64)]
 
 
+class vrs_cull_opts(ctypes.Structure):
+    _fields_ = [("alpha_min", _f32), ("rel_margin", _f32), ("abs_margin", _f32), ("reserved", _i32)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/vrs.h
 SIGNATURES = [
     ("vrs_plan_batch", _i32, [ctypes.POINTER(vrs_scene), _i32, ctypes.POINTER(vrs_camera), _i32,
@@ -76,6 +81,8 @@ SIGNATURES = [
     ("vrs_query_status", _i32, [ctypes.POINTER(vrs_plan), _vp, ctypes.POINTER(vrs_run_info), _vp]),
     ("vrs_reset_status", _i32, [ctypes.POINTER(vrs_plan), _vp, _vp]),
     ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    ("vrs_cull_points", _i32, [_vp, _i64, ctypes.POINTER(vrs_camera), _i32, _i32, _vp, _vp, _i32, _i32,
+                               ctypes.POINTER(vrs_cull_opts), _vp, _vp, _vp, _vp]),
     ("vrs_status_string", ctypes.c_char_p, [_i32]),
 ]
 
@@ -156,3 +163,12 @@ def vrs_status_string(code: int) -> str:
 def vrs_sort_pairs_noalloc(keys_in: int, vals_in: int, keys_out: int, vals_out: int, n: int,
                            key_bits: int, stream: int) -> int:
     return load().vrs_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream)
+
+
+def vrs_cull_points(points: int, n_points: int, fovea, x0: int, y0: int, depth: int, T_final: int,
+                    map_w: int, map_h: int, opts, mask: int, kept: Optional[int], n_kept: int,
+                    stream: Optional[int]) -> int:
+    return load().vrs_cull_points(points, n_points, ctypes.byref(fovea) if fovea is not None else None,
+                                  x0, y0, depth, T_final, map_w, map_h,
+                                  ctypes.byref(opts) if opts is not None else None, mask, kept, n_kept,
+                                  stream)

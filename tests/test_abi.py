@@ -44,12 +44,14 @@ def _c_layout(tmp_path):
 #include "vrs.h"
 #define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
-  printf("vrs_scene %zu\nvrs_camera %zu\nvrs_plan_opts %zu\nvrs_plan %zu\nvrs_run_info %zu\n",
-         sizeof(vrs_scene), sizeof(vrs_camera), sizeof(vrs_plan_opts), sizeof(vrs_plan), sizeof(vrs_run_info));
+  printf("vrs_scene %zu\nvrs_camera %zu\nvrs_plan_opts %zu\nvrs_plan %zu\nvrs_run_info %zu\n"
+         "vrs_cull_opts %zu\n", sizeof(vrs_scene), sizeof(vrs_camera), sizeof(vrs_plan_opts),
+         sizeof(vrs_plan), sizeof(vrs_run_info), sizeof(vrs_cull_opts));
   P(vrs_plan, max_instances) P(vrs_plan, off_status) P(vrs_plan, off_grad2d) P(vrs_plan, sorted_buf)
   P(vrs_plan, scene_n) P(vrs_plan, view_scene) P(vrs_plan, view_rec_base) P(vrs_plan, view_pix_base)
   P(vrs_camera, fx) P(vrs_camera, width) P(vrs_camera, scene) P(vrs_scene, n)
-  P(vrs_run_info, instances) P(vrs_run_info, pair_blends) P(vrs_plan_opts, max_instances)
+  P(vrs_run_info, instances) P(vrs_run_info, pair_blends) P(vrs_run_info, block_evals)
+  P(vrs_plan_opts, max_instances) P(vrs_plan, off_pairs) P(vrs_cull_opts, abs_margin)
   return 0;
 }
 """
@@ -64,7 +66,7 @@ int main(void) {
 def test_struct_layouts_match_header(lib, tmp_path):
     c = _c_layout(tmp_path)
     L = lib
-    for name in ["vrs_scene", "vrs_camera", "vrs_plan_opts", "vrs_plan", "vrs_run_info"]:
+    for name in ["vrs_scene", "vrs_camera", "vrs_plan_opts", "vrs_plan", "vrs_run_info", "vrs_cull_opts"]:
         assert int(c[name]) == ctypes.sizeof(getattr(L, name)), name
     for key, val in c.items():
         if "." in key:
@@ -95,7 +97,8 @@ def test_plan_sizes_and_layout_on_host(lib):
     assert p.key_bits == 32 + 16 and p.sort_passes == 6 and p.sorted_buf == 0
     assert p.view_rec_base[1] == 1000 and p.view_tile_base[1] == 126 * 140
     offs = [p.off_status, p.off_records, p.off_keys[0], p.off_keys[1], p.off_vals[0], p.off_vals[1],
-            p.off_hist, p.off_ranges, p.off_ncontrib, p.off_order, p.off_grad2d]
+            p.off_hist, p.off_ranges, p.off_ncontrib, p.off_order, p.off_grad2d, p.off_tilesort,
+            p.off_pairs]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and p.workspace_bytes > offs[-1]
     assert p.off_keys[1] - p.off_keys[0] >= 8 * p.max_instances
@@ -130,3 +133,32 @@ def test_library_missing_fails_loudly(tmp_path):
             L.load(str(tmp_path / "nope.so"))
     finally:
         L._lib = saved
+
+
+def test_cull_points_rejects_bad_arguments_on_host(lib):
+    """Argument errors return before any CUDA call (so this runs without a GPU)."""
+    L = lib
+    cam = L.vrs_camera()
+    cam.width, cam.height, cam.fx, cam.fy = 16, 16, 10.0, 10.0
+    buf = ctypes.create_string_buffer(64)
+    ptr = ctypes.addressof(buf)
+    ptr = ptr + (-ptr % 16)
+    good = dict(points=ptr, n=4, cam=cam, depth=ptr, T=ptr, w=16, h=16, opts=None, mask=ptr, kept=None,
+                n_kept=ptr)
+
+    def call(**kw):
+        a = dict(good, **kw)
+        return L.vrs_cull_points(a["points"], a["n"], a["cam"], 0, 0, a["depth"], a["T"], a["w"], a["h"],
+                                 a["opts"], a["mask"], a["kept"], a["n_kept"], None)
+
+    assert call(n=-1) == L.VRS_ERR_INVALID
+    assert call(n=1 << 32) == L.VRS_ERR_INVALID
+    assert call(cam=None) == L.VRS_ERR_INVALID
+    assert call(n_kept=None) == L.VRS_ERR_INVALID
+    assert call(points=None) == L.VRS_ERR_INVALID
+    assert call(mask=None) == L.VRS_ERR_INVALID
+    assert call(points=ptr + 2) == L.VRS_ERR_INVALID
+    assert call(w=0) == L.VRS_ERR_INVALID
+    bad = L.vrs_camera()
+    assert call(cam=bad) == L.VRS_ERR_INVALID
+    assert call(opts=L.vrs_cull_opts(0.5, 0.02, 0.05, 1)) == L.VRS_ERR_INVALID
