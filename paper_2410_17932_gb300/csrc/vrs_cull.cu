@@ -3,12 +3,14 @@
 // point in, one byte of decision and a 4-byte index per kept point out; the
 // depth and transmittance of the foveal window (a few MB) stay in L2.
 //
-// Each CTA takes chunks of 1024 points: the chunk's 12 KB are loaded with
-// 16-byte vector loads into shared memory (three per thread, all issued before
-// any is used), then each thread decides four points at a stride of 256 (so
-// its shared reads, three consecutive words per point, are conflict-free),
-// writes their mask bytes, and the kept indices are compacted with one
-// atomic per CTA and chunk.
+// Every warp streams chunks of 128 points: lane L loads the three 16-byte
+// words 3L..3L+2 of the chunk, which hold its four whole points 4L..4L+3 (a
+// resident wave of 56 warps per SM keeps about 90 KB of loads in flight).
+// The decision runs without branches (x and y in packed FP32x2 operations,
+// each component rounded as the scalar operation would be), the lane writes
+// its four mask bytes as one word, and a warp with kept points takes their
+// slots with one atomic.  Only the rare points inside an opaque-enough pixel
+// take the divide of the depth test.
 #include "vrs_internal.cuh"
 
 namespace vrs {
@@ -27,100 +29,109 @@ struct CullArgs {
 };
 
 constexpr int kCullThreads = 256;
-constexpr int kCullPer = 4;                        // points per thread and chunk
-constexpr int kCullChunk = kCullThreads * kCullPer;
+constexpr int kCullWarps = kCullThreads / 32;
+constexpr int kCullPer = 4;                        // points per lane and chunk
+constexpr int kCullChunk = 32 * kCullPer;          // points per warp chunk
+
+__device__ __forceinline__ float2 f2c(float a) { return make_float2(a, a); }
 
 // The three-way decision of one point, every step a correctly rounded FP32
 // operation in the order the C-ABI states.
-__device__ __forceinline__ uint8_t cull_decide(const CullArgs &a, float px, float py, float pz)
+__device__ __forceinline__ uint32_t cull_decide(const CullArgs &a, float px, float py, float pz)
 {
-    float x = __fmul_rn(a.R[0], px);
-    x = __fadd_rn(x, __fmul_rn(a.R[1], py));
-    x = __fadd_rn(x, __fmul_rn(a.R[2], pz));
-    x = __fadd_rn(x, a.t[0]);
-    float y = __fmul_rn(a.R[3], px);
-    y = __fadd_rn(y, __fmul_rn(a.R[4], py));
-    y = __fadd_rn(y, __fmul_rn(a.R[5], pz));
-    y = __fadd_rn(y, a.t[1]);
     float z = __fmul_rn(a.R[6], px);
     z = __fadd_rn(z, __fmul_rn(a.R[7], py));
     z = __fadd_rn(z, __fmul_rn(a.R[8], pz));
     z = __fadd_rn(z, a.t[2]);
-    if (!(z > a.znear) || !isfinite(x) || !isfinite(y)) return 0;
-    const float iz = __fdiv_rn(1.0f, z);
-    const float u = __fadd_rn(__fmul_rn(a.fx, __fmul_rn(x, iz)), a.cx);
-    const float v = __fadd_rn(__fmul_rn(a.fy, __fmul_rn(y, iz)), a.cy);
-    if (!(u >= 0.0f && u < (float)a.w && v >= 0.0f && v < (float)a.h)) return 0;
-    const int mi = (int)u + a.x0, mj = (int)v + a.y0;
-    if (mi < 0 || mi >= a.map_w || mj < 0 || mj >= a.map_h) return 0;
-    const int64_t pix = (int64_t)mj * a.map_w + mi;
-    const float al = __fsub_rn(1.0f, __ldg(a.Tf + pix));
-    if (!(al >= a.alpha_min)) return 2;
-    const float thr = __fadd_rn(__fmul_rn(__fdiv_rn(__ldg(a.depth + pix), al), a.scale), a.abs_margin);
-    return z > thr ? 1 : 2;
+    float2 xy = __fmul2_rn(make_float2(a.R[0], a.R[3]), f2c(px));
+    xy = __fadd2_rn(xy, __fmul2_rn(make_float2(a.R[1], a.R[4]), f2c(py)));
+    xy = __fadd2_rn(xy, __fmul2_rn(make_float2(a.R[2], a.R[5]), f2c(pz)));
+    xy = __fadd2_rn(xy, make_float2(a.t[0], a.t[1]));
+    const bool front = z > a.znear && isfinite(xy.x) && isfinite(xy.y);
+    const float iz = __frcp_rn(z);                  // 1/z, correctly rounded
+    float2 uv = __fmul2_rn(xy, f2c(iz));
+    uv = __fmul2_rn(make_float2(a.fx, a.fy), uv);
+    uv = __fadd2_rn(uv, make_float2(a.cx, a.cy));
+    const bool in = front && uv.x >= 0.0f && uv.x < (float)a.w && uv.y >= 0.0f && uv.y < (float)a.h;
+    const int mi = in ? __float2int_rz(uv.x) + a.x0 : -1, mj = in ? __float2int_rz(uv.y) + a.y0 : -1;
+    const bool inmap = in && mi >= 0 && mi < a.map_w && mj >= 0 && mj < a.map_h;
+    uint32_t r = inmap ? 2u : 0u;
+    if (inmap) {
+        const int64_t pix = (int64_t)mj * a.map_w + mi;
+        const float al = __fsub_rn(1.0f, __ldg(a.Tf + pix));
+        if (al >= a.alpha_min) {
+            const float thr = __fadd_rn(__fmul_rn(__fdiv_rn(__ldg(a.depth + pix), al), a.scale), a.abs_margin);
+            if (z > thr) r = 1u;
+        }
+    }
+    return r;
 }
 
 __global__ void __launch_bounds__(kCullThreads) k_cull_points(const __grid_constant__ CullArgs a)
 {
-    __shared__ __align__(16) float sp[3 * kCullChunk];
-    __shared__ uint32_t s_wcnt[kCullThreads / 32];
-    __shared__ unsigned long long s_base[kCullThreads / 32];
     const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(a.pts) & 15u) == 0;
-    for (int64_t c0 = (int64_t)blockIdx.x * kCullChunk; c0 < a.n; c0 += (int64_t)gridDim.x * kCullChunk) {
-        const int64_t left = a.n - c0;
-        const int cnt = left < kCullChunk ? (int)left : kCullChunk;
-        // stage the chunk (12 bytes per point, contiguous)
-        if (vec && cnt == kCullChunk) {
-            const float4 *src = reinterpret_cast<const float4 *>(a.pts + 3 * c0);
-            float4 *dst = reinterpret_cast<float4 *>(sp);
-            float4 r[3 * kCullPer / 4];
+    const int64_t n_chunks = (a.n + kCullChunk - 1) / kCullChunk;
+    const int64_t stride = (int64_t)gridDim.x * kCullWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kCullWarps + wp; c < n_chunks; c += stride) {
+        // the lane's four points: 12 consecutive floats from float 12 * lane of the chunk
+        const int64_t p0 = c * kCullChunk + kCullPer * lane;
+        const bool whole = c * kCullChunk + kCullChunk <= a.n;
+        float f[12];
+        if (vec && whole) {
+            const float4 *src = reinterpret_cast<const float4 *>(a.pts + 3 * p0);
 #pragma unroll
-            for (int k = 0; k < 3 * kCullPer / 4; ++k) r[k] = __ldg(src + k * kCullThreads + tid);
-#pragma unroll
-            for (int k = 0; k < 3 * kCullPer / 4; ++k) dst[k * kCullThreads + tid] = r[k];
+            for (int k = 0; k < 3; ++k) {
+                const float4 v = __ldg(src + k);
+                f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+            }
         } else {
-            for (int k = tid; k < 3 * cnt; k += kCullThreads) sp[k] = __ldg(a.pts + 3 * c0 + k);
-        }
-        __syncthreads();
-        uint32_t bal[kCullPer];
-        uint32_t total = 0;
+            const int64_t lim = 3 * a.n;
 #pragma unroll
-        for (int k = 0; k < kCullPer; ++k) {
-            const int li = k * kCullThreads + tid;
-            uint8_t r = 0;
-            if (li < cnt) {
-                r = cull_decide(a, sp[3 * li], sp[3 * li + 1], sp[3 * li + 2]);
-                a.mask[c0 + li] = r;
-            }
-            bal[k] = __ballot_sync(FULL, r == 2);
-            total += __popc(bal[k]);
+            for (int e = 0; e < 12; ++e) f[e] = 3 * p0 + e < lim ? __ldg(a.pts + 3 * p0 + e) : 0.f;
         }
-        // one atomic per CTA and chunk for the kept slots
-        if (lane == 0) s_wcnt[wp] = total;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long sum = 0;
-            for (int q = 0; q < kCullThreads / 32; ++q) sum += s_wcnt[q];
-            unsigned long long b = sum ? atomicAdd(a.n_kept, sum) : 0ull;
-            for (int q = 0; q < kCullThreads / 32; ++q) {
-                s_base[q] = b;
-                b += s_wcnt[q];
-            }
-        }
-        __syncthreads();
-        if (a.kept) {
-            unsigned long long base = s_base[wp];
-            const uint32_t lt = lanemask_lt();
+        uint32_t word = 0, keep = 0;
+        if (whole) {                                         // a whole chunk: no per-point guard
 #pragma unroll
             for (int k = 0; k < kCullPer; ++k) {
-                if ((bal[k] >> lane) & 1u)
-                    a.kept[base + __popc(bal[k] & lt)] = (uint32_t)(c0 + k * kCullThreads + tid);
-                base += __popc(bal[k]);
+                const uint32_t r = cull_decide(a, f[3 * k], f[3 * k + 1], f[3 * k + 2]);
+                word |= r << (8 * k);
+                keep |= (r == 2u ? 1u : 0u) << k;
+            }
+        } else {
+            for (int k = 0; k < kCullPer; ++k) {
+                const uint32_t r = p0 + k < a.n ? cull_decide(a, f[3 * k], f[3 * k + 1], f[3 * k + 2]) : 0u;
+                word |= r << (8 * k);
+                keep |= (r == 2u ? 1u : 0u) << k;
             }
         }
-        __syncthreads();   // sp and s_base are rewritten by the next chunk
+        if (p0 + kCullPer <= a.n && (reinterpret_cast<uintptr_t>(a.mask + p0) & 3u) == 0) {
+            *reinterpret_cast<uint32_t *>(a.mask + p0) = word;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kCullPer; ++k)
+                if (p0 + k < a.n) a.mask[p0 + k] = (uint8_t)(word >> (8 * k));
+        }
+        // kept slots: one atomic per warp that has kept points
+        const uint32_t nk = __popc(keep);
+        if (__any_sync(FULL, nk != 0)) {
+            uint32_t incl = nk;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.n_kept, (unsigned long long)total);
+            base = __shfl_sync(FULL, base, 0) + (incl - nk);
+            if (a.kept) {
+#pragma unroll
+                for (int k = 0; k < kCullPer; ++k)
+                    if ((keep >> k) & 1u) a.kept[base++] = (uint32_t)(p0 + k);
+            }
+        }
     }
 }
 
@@ -174,9 +185,14 @@ extern "C" vrs_status vrs_cull_points(const float *points, int64_t n_points, con
         cudaGetLastError();
         sms = 152;
     }
-    const int64_t chunks = (n_points + kCullChunk - 1) / kCullChunk;
-    const int64_t cap = (int64_t)sms * 8;
-    const unsigned grid = (unsigned)(chunks < cap ? chunks : cap);
-    k_cull_points<<<grid, kCullThreads, 0, s>>>(a);
+    const int64_t ctas = (n_points + (int64_t)kCullChunk * kCullWarps - 1) / ((int64_t)kCullChunk * kCullWarps);
+    int per_sm = 0;                            // one resident wave; warps loop over the chunks
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cull_points, kCullThreads, 0) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 4;
+    }
+    const int64_t cap = (int64_t)sms * per_sm;
+    k_cull_points<<<(unsigned)(ctas < cap ? ctas : cap), kCullThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
 }
