@@ -303,43 +303,60 @@ def _time_loop(fn, flush, iters):
     return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
 
 
+EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m")
+
+
 def run_extras(args):
+    import torch
+    from paper_2410_17932_gb300 import inputs as I
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+    want = set(EXTRAS) if args.extras == "all" else set(args.extras.split(","))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    if "dense_3m" in want:
+        # dense stereo frame, 3 M Gaussians, two eyes + two 512x512 foveal crops (forward)
+        scenes, views = I.dense_stereo_3m()
+        sts = [SceneTensors.from_scene(s) for s in scenes]
+        ras = Rasterizer(sts, views)
+        ras.forward()
+        for _ in range(3):
+            ras.forward_async()
+        out["dense_stereo_3m_ms_per_frame"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+        out["dense_stereo_3m_instances"] = ras.last_status[2]
+        del ras, sts
+    if "training_1m" in want:
+        # training step: forward + backward of one 1264x832 view over 1 M Gaussians
+        scenes, views = I.training_view_1m()
+        sts = [SceneTensors.from_scene(s) for s in scenes]
+        ras = Rasterizer(sts, views, backward=True)
+        ras.forward()
+        g = I.upstream_grads(views, 7)[0]
+        gC = torch.as_tensor(g[0].reshape(-1), device="cuda")
+        gD = torch.as_tensor(g[1].reshape(-1), device="cuda")
+        grads = [s.zeros_like() for s in sts]
+
+        def step():
+            ras.forward_async()
+            ras.backward_params(gC, gD, None, grads)
+
+        for _ in range(3):
+            step()
+        out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(step, flush, args.extra_steps), 4)
+        out["training_view_1m_fwd_ms"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+        del ras, sts, grads
+    if "batched_32" in want:
+        out["batched_32_views"] = _batched_32(args, flush)
+    if "foveal_points_5m" in want:
+        out["foveal_points_5m"] = _foveal_points(args, flush)
+    return out
+
+
+def _batched_32(args, flush):
+    """32 views of uneven size over 4 scenes: batched persistent under a CUDA graph vs per-view launches."""
     import torch
     from paper_2410_17932_gb300 import autotune
     from paper_2410_17932_gb300 import inputs as I
     from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {}
-    # dense stereo frame, 3 M Gaussians, two eyes + two 512x512 foveal crops (forward)
-    scenes, views = I.dense_stereo_3m()
-    sts = [SceneTensors.from_scene(s) for s in scenes]
-    ras = Rasterizer(sts, views)
-    ras.forward()
-    for _ in range(3):
-        ras.forward_async()
-    out["dense_stereo_3m_ms_per_frame"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
-    out["dense_stereo_3m_instances"] = ras.last_status[2]
-    del ras, sts
-    # training step: forward + backward of one 1264x832 view over 1 M Gaussians
-    scenes, views = I.training_view_1m()
-    sts = [SceneTensors.from_scene(s) for s in scenes]
-    ras = Rasterizer(sts, views, backward=True)
-    ras.forward()
-    g = I.upstream_grads(views, 7)[0]
-    gC = torch.as_tensor(g[0].reshape(-1), device="cuda")
-    gD = torch.as_tensor(g[1].reshape(-1), device="cuda")
-    grads = [s.zeros_like() for s in sts]
-
-    def step():
-        ras.forward_async()
-        ras.backward_params(gC, gD, None, grads)
-
-    for _ in range(3):
-        step()
-    out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(step, flush, args.extra_steps), 4)
-    out["training_view_1m_fwd_ms"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
-    del ras, sts, grads
-    # 32 views of uneven size over 4 scenes: batched persistent under a CUDA graph vs per-view launches
     scenes, views = I.batched_multiview()
     sts = [SceneTensors.from_scene(s) for s in scenes]
     best = autotune.tune(sts, views, iters=5, use_cache=False)
@@ -363,14 +380,19 @@ def run_extras(args):
     ms_per_view = _time_loop(per_view, flush, max(3, args.extra_steps // 4))
     same = all(torch.equal(x, y) for v, r in enumerate(singles)
                for x, y in zip(batched.outputs(v), r.outputs(0)))
-    out["batched_32_views"] = {"batched_graph_ms": round(ms_batched, 4), "per_view_launches_ms": round(ms_per_view, 4),
-                               "speedup": round(ms_per_view / ms_batched, 3), "autotuned": best,
-                               "identical_images": bool(same),
-                               "pixels": int(batched.plan.n_pixels), "instances": int(batched.last_status[2])}
-    del batched, runner, singles, sts
-    # foveal neural-point culling (Sec. 3.3): 5 M points against the left eye's Eq. 1 depth
-    # inside a 512x512 subfrustum at a seeded gaze
+    return {"batched_graph_ms": round(ms_batched, 4), "per_view_launches_ms": round(ms_per_view, 4),
+            "speedup": round(ms_per_view / ms_batched, 3), "autotuned": best,
+            "identical_images": bool(same),
+            "pixels": int(batched.plan.n_pixels), "instances": int(batched.last_status[2])}
+
+
+def _foveal_points(args, flush):
+    """Foveal neural-point culling (Sec. 3.3): 5 M points against the left eye's Eq. 1 depth
+    inside a 512x512 subfrustum at a seeded gaze, timed as CUDA-graph replays."""
+    import torch
+    from paper_2410_17932_gb300 import inputs as I
     from paper_2410_17932_gb300.cull import PointCuller
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
     scenes, eye, crop, pts = I.foveal_points_5m()
     ras = Rasterizer([SceneTensors.from_scene(s) for s in scenes], [eye])
     ras.forward()
@@ -396,14 +418,14 @@ def run_extras(args):
     m = len(pts)
     byts = 12 * m + m + 4 * n_kept        # points read, decisions written, kept indices written
     peaks, src = measured_peaks()
-    out["foveal_points_5m"] = {
+    return {
         "cull_ms": round(ms_cull, 4), "points_per_s": round(m / (ms_cull * 1e-3), 1),
         "outside": int(counts[0]), "occluded": int(counts[1]), "kept": int(counts[2]),
         "roofline": {"bound": "hbm", "kernel": "k_cull_points", "achieved": round(byts / (ms_cull * 1e-3) / 1e9, 1),
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(byts / (ms_cull * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
-                     "bytes_per_launch": byts, "peak_source": src}}
-    return out
+                     "bytes_per_launch": byts, "peak_source": src,
+                     "timed": "one vrs_cull_points call: the n_kept reset and the kernel"}}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -422,7 +444,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--no-extras", action="store_true", help="skip the 3M, training and 32-view runs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
+    ap.add_argument("--extras", default="all", help="comma list of " + ",".join(EXTRAS) + ", or all")
     ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--blend-traffic", type=float, default=None,
                     help="DRAM bytes per blend launch from an ncu capture of the current kernel")
