@@ -529,8 +529,15 @@ def main():
     else:
         n = sum(s.n for s in scenes)
         if dominant == "preprocess":
-            K_ = [(s.sh_degree + 1) ** 2 for s in scenes]
-            byts = sum(s.n * (4 * (3 + 3 + 4 + 1) + 12 * k) for s, k in zip(scenes, K_)) + 48 * int(p.n_records) + 12 * inst
+            # geometry of every Gaussian; per visible pair: its list entry written and read, mean
+            # and logit, SH row, record; per instance: key and value
+            K_ = max((s.sh_degree + 1) ** 2 for s in scenes)
+            pairs = ras.visible_pairs
+            byts = n * 44 + pairs * (64 + 16 + 12 * K_ + 48) + 12 * inst
+        elif p.sort_mode == 0:
+            # bucketed: scatter reads key + value, takes a cursor, writes the composite; the
+            # per-tile sort reads the composite and writes key + value; counts, cursors, ranges
+            byts = inst * (12 + 4 + 8 + 8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
         else:
             byts = 24 * inst * int(p.sort_passes) + 8 * inst * int(p.sort_passes)
         achieved = byts / (stage[dominant] * 1e-3) / 1e9

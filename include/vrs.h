@@ -178,6 +178,8 @@ typedef struct {
     uint64_t block_evals;      /* with plan.count_pairs: (instance, 8x8 pixel block) pairs the
                                   blend kernel evaluated after its culling (each covers 64
                                   Gaussian-pixel evaluations) */
+    uint64_t visible_pairs[VRS_MAX_SCENES]; /* (Gaussian, view) pairs of each scene that the last
+                                  vrs_preprocess found visible (one 48-byte record each) */
 } vrs_run_info;
 
 /* Sizes a batch of n_views views over n_scenes scenes and lays out the

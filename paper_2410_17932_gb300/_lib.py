@@ -60,7 +60,7 @@ class vrs_plan(ctypes.Structure):
 
 class vrs_run_info(ctypes.Structure):
     _fields_ = [("flags", _u32), ("reserved", _u32), ("instances", _u64), ("pair_evals", _u64),
-                ("pair_blends", _u64), ("block_evals", _u64)]
+                ("pair_blends", _u64), ("block_evals", _u64), ("visible_pairs", _u64 * VRS_MAX_SCENES)]
 
 
 class vrs_cull_opts(ctypes.Structure):

@@ -38,8 +38,8 @@ struct DevStatus {
     unsigned long long pair_evals;
     unsigned long long pair_blends;
     unsigned long long block_evals;
-    uint32_t work[8];          // work-queue counters of persistent kernels
     unsigned long long scene_pairs[VRS_MAX_SCENES];   // visible (Gaussian, view) pairs per scene
+    uint32_t work[8];          // work-queue counters of persistent kernels
 };
 static_assert(sizeof(DevStatus) <= 256, "the status block is 256 bytes");
 

@@ -162,6 +162,7 @@ class Rasterizer:
     def status(self, stream=None):
         info = L.vrs_run_info()
         code = L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(stream))
+        self.visible_pairs = int(sum(info.visible_pairs[: len(self.scenes)]))
         return code, int(info.flags), int(info.instances)
 
     def forward(self, stream=None, check: bool = True, grow: bool = True):
