@@ -106,6 +106,9 @@ def lib():
             L.orc_param_grads.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                           ctypes.POINTER(OrcCamera), P, P, P, P, P, P, P]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_combine.restype = None
+            L.orc_combine.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [P, P]
             L.orc_cull_points.restype = None
             L.orc_cull_points.argtypes = [ctypes.c_int64, P, ctypes.POINTER(OrcCamera), ctypes.c_int32,
                                           ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
@@ -334,3 +337,23 @@ def cull_points(points, cam, x0: int, y0: int, depth, T_final, alpha_min: float 
     lib().orc_cull_points(len(pts), _p(pts), ctypes.byref(c), int(x0), int(y0), _p(d), _p(t),
                           d.shape[1], d.shape[0], ctypes.byref(o), _p(out))
     return out
+
+
+# Defaults of Sec. 3.4: fovea radius 256 px, blending interval start m = 0.75, edge weight 0.2.
+COMBINE_DF, COMBINE_M, COMBINE_GAMMA = 256.0, 0.75, 0.2
+
+
+def combine(P, F, x0: int, y0: int, ex: float, ey: float, d_f: float = COMBINE_DF, m: float = COMBINE_M,
+            gamma: float = COMBINE_GAMMA):
+    """Sec. 3.4 combination of the periphery P [3, H, W] and the foveal crop image F [3, h, w]
+    placed at (x0, y0) in P, fixation (ex, ey) in P's pixel frame.  Returns (out [3, h, w], c [h, w])."""
+    Pf = _f32(P)
+    Ff = _f32(F)
+    _, ph, pw = Pf.shape
+    _, h, w = Ff.shape
+    assert 0 <= x0 and 0 <= y0 and x0 + w <= pw and y0 + h <= ph
+    out = np.zeros((3, h, w), np.float64)
+    c = np.zeros((h, w), np.float64)
+    lib().orc_combine(_p(Pf), pw, ph, _p(Ff), w, h, int(x0), int(y0), float(ex), float(ey), float(d_f),
+                      float(m), float(gamma), _p(out), _p(c))
+    return out, c

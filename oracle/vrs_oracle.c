@@ -937,3 +937,53 @@ void orc_cull_points(int64_t m, const float *pts, const orc_camera *cam, int32_t
         mask[p] = r;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Combination of the peripheral image P and the foveal image F (Sec. 3.4), in
+ * FP64 over the foveal crop window [x0, x0 + w) x [y0, y0 + h) of P.
+ *
+ * For crop pixel (i, j), at P-frame position (u, v) = (x0 + i + 0.5, y0 + j + 0.5):
+ *   r_norm = clamp(|(u, v) - (e_x, e_y)| / d_f, 0, 1)
+ *   f_p    = (r_norm - m) / (1 - m)
+ *   f_e    = S(F, i, j): the magnitude of the Sobel gradient of F's channel mean
+ *            (3x3 kernels, weights 1-2-1 across and -1/0/+1 along, divided by 8 so a
+ *            unit-slope ramp gives 1), the crop's border replicated
+ *   c      = 1 - S2(clamp(f_p + gamma f_e, 0, 1)),  S2(x) = 6x^5 - 15x^4 + 10x^3
+ *   out    = (1 - c) p + c f per channel.
+ * P is [3][ph][pw], F and out are [3][h][w], c_out (nullable) is [h][w]. */
+static double orc_chan_mean(const float *F, int w, int h, int i, int j)
+{
+    i = i < 0 ? 0 : (i >= w ? w - 1 : i);
+    j = j < 0 ? 0 : (j >= h ? h - 1 : j);
+    const size_t hw = (size_t)w * h, p = (size_t)j * w + i;
+    return ((double)F[p] + (double)F[hw + p] + (double)F[2 * hw + p]) / 3.0;
+}
+
+void orc_combine(const float *P, int pw, int ph, const float *F, int w, int h, int x0, int y0,
+                 double ex, double ey, double d_f, double m, double gamma, double *out, double *c_out)
+{
+    const size_t hw = (size_t)w * h, phw = (size_t)pw * ph;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            double du = (x0 + i + 0.5) - ex, dv = (y0 + j + 0.5) - ey;
+            double r = sqrt(du * du + dv * dv) / d_f;
+            r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+            double fp = (r - m) / (1.0 - m);
+            double L[3][3];
+            for (int b = -1; b <= 1; ++b)
+                for (int a = -1; a <= 1; ++a) L[b + 1][a + 1] = orc_chan_mean(F, w, h, i + a, j + b);
+            double gx = ((L[0][2] + 2.0 * L[1][2] + L[2][2]) - (L[0][0] + 2.0 * L[1][0] + L[2][0])) / 8.0;
+            double gy = ((L[2][0] + 2.0 * L[2][1] + L[2][2]) - (L[0][0] + 2.0 * L[0][1] + L[0][2])) / 8.0;
+            double fe = sqrt(gx * gx + gy * gy);
+            double x = fp + gamma * fe;
+            x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+            double s2 = x * x * x * (x * (6.0 * x - 15.0) + 10.0);
+            double c = 1.0 - s2;
+            const size_t q = (size_t)j * w + i;
+            const size_t pp = (size_t)(y0 + j) * pw + (x0 + i);
+            for (int ch = 0; ch < 3; ++ch)
+                out[ch * hw + q] = (1.0 - c) * (double)P[ch * phw + pp] + c * (double)F[ch * hw + q];
+            if (c_out) c_out[q] = c;
+        }
+}
