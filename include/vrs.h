@@ -324,6 +324,36 @@ vrs_status vrs_cull_points(const float *points, int64_t n_points, const vrs_came
                            int32_t map_w, int32_t map_h, const vrs_cull_opts *opts, uint8_t *mask,
                            uint32_t *kept, uint64_t *n_kept, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Combination of the peripheral image P and the foveal image F (Sec. 3.4).
+ * Over the foveal crop window [x0, x0 + w) x [y0, y0 + h) of P, for crop pixel
+ * (i, j) at P-frame position (u, v) = (x0 + i + 0.5, y0 + j + 0.5):
+ *   r_norm = clamp(|(u, v) - (ex, ey)| / d_f, 0, 1),  f_p = (r_norm - m) / (1 - m),
+ *   f_e    = magnitude of the Sobel gradient of F's channel mean (3x3 kernels
+ *            weighted 1-2-1, divided by 8; the crop's border replicated),
+ *   c      = 1 - S2(clamp(f_p + gamma f_e, 0, 1)),  S2(x) = 6x^5 - 15x^4 + 10x^3,
+ *   out    = (1 - c) p + c f per channel.
+ * The library's readings where the paper is silent: the Sobel filter acts on the
+ * mean of F's three channels, is normalised so that a unit-slope ramp gives 1,
+ * and replicates the border; S2's argument is clamped to [0, 1].  FP32. */
+typedef struct {
+    float d_f;                 /* fovea radius in pixels, default 256 */
+    float m;                   /* start of the blending interval, default 0.75 */
+    float gamma;               /* edge weight, default 0.2 */
+    int32_t reserved;          /* 0 */
+} vrs_combine_opts;
+
+/* P: device [3][ph][pw] float (one view of vrs_render_fwd's RGB).  F: device
+ * [3][h][w] float, the foveal image of the crop.  (ex, ey): the fixation in P's
+ * pixel frame.  opts: host, NULL for the defaults.  out: device [3][h][w], must
+ * not overlap F.  c_out: device [h][w] (nullable), the factor c.  Returns
+ * VRS_ERR_INVALID for NULL required pointers, sizes below 1, a window not
+ * inside P, out overlapping F, d_f <= 0, m >= 1 or a reserved field that is
+ * not 0; VRS_ERR_CUDA on a launch failure.  No allocation; stream ordered. */
+vrs_status vrs_foveal_combine(const float *P, int32_t pw, int32_t ph, const float *F, int32_t w, int32_t h,
+                              int32_t x0, int32_t y0, float ex, float ey, const vrs_combine_opts *opts,
+                              float *out, float *c_out, void *stream);
+
 /* A static, human-readable name of a status. */
 const char *vrs_status_string(vrs_status status);
 

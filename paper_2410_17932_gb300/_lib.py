@@ -63,6 +63,10 @@ class vrs_run_info(ctypes.Structure):
                 ("pair_blends", _u64), ("block_evals", _u64), ("visible_pairs", _u64 * VRS_MAX_SCENES)]
 
 
+class vrs_combine_opts(ctypes.Structure):
+    _fields_ = [("d_f", _f32), ("m", _f32), ("gamma", _f32), ("reserved", _i32)]
+
+
 class vrs_cull_opts(ctypes.Structure):
     _fields_ = [("alpha_min", _f32), ("rel_margin", _f32), ("abs_margin", _f32), ("reserved", _i32)]
 
@@ -81,6 +85,8 @@ SIGNATURES = [
     ("vrs_query_status", _i32, [ctypes.POINTER(vrs_plan), _vp, ctypes.POINTER(vrs_run_info), _vp]),
     ("vrs_reset_status", _i32, [ctypes.POINTER(vrs_plan), _vp, _vp]),
     ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    ("vrs_foveal_combine", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
+                                  ctypes.POINTER(vrs_combine_opts), _vp, _vp, _vp]),
     ("vrs_cull_points", _i32, [_vp, _i64, ctypes.POINTER(vrs_camera), _i32, _i32, _vp, _vp, _i32, _i32,
                                ctypes.POINTER(vrs_cull_opts), _vp, _vp, _vp, _vp]),
     ("vrs_status_string", ctypes.c_char_p, [_i32]),
@@ -172,3 +178,9 @@ def vrs_cull_points(points: int, n_points: int, fovea, x0: int, y0: int, depth: 
                                   x0, y0, depth, T_final, map_w, map_h,
                                   ctypes.byref(opts) if opts is not None else None, mask, kept, n_kept,
                                   stream)
+
+
+def vrs_foveal_combine(P: int, pw: int, ph: int, F: int, w: int, h: int, x0: int, y0: int, ex: float,
+                       ey: float, opts, out: int, c_out: Optional[int], stream: Optional[int]) -> int:
+    return load().vrs_foveal_combine(P, pw, ph, F, w, h, x0, y0, ex, ey,
+                                     ctypes.byref(opts) if opts is not None else None, out, c_out, stream)

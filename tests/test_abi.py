@@ -45,8 +45,9 @@ def _c_layout(tmp_path):
 #define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
   printf("vrs_scene %zu\nvrs_camera %zu\nvrs_plan_opts %zu\nvrs_plan %zu\nvrs_run_info %zu\n"
-         "vrs_cull_opts %zu\n", sizeof(vrs_scene), sizeof(vrs_camera), sizeof(vrs_plan_opts),
-         sizeof(vrs_plan), sizeof(vrs_run_info), sizeof(vrs_cull_opts));
+         "vrs_cull_opts %zu\nvrs_combine_opts %zu\n", sizeof(vrs_scene), sizeof(vrs_camera),
+         sizeof(vrs_plan_opts), sizeof(vrs_plan), sizeof(vrs_run_info), sizeof(vrs_cull_opts),
+         sizeof(vrs_combine_opts));
   P(vrs_plan, max_instances) P(vrs_plan, off_status) P(vrs_plan, off_grad2d) P(vrs_plan, sorted_buf)
   P(vrs_plan, scene_n) P(vrs_plan, view_scene) P(vrs_plan, view_rec_base) P(vrs_plan, view_pix_base)
   P(vrs_camera, fx) P(vrs_camera, width) P(vrs_camera, scene) P(vrs_scene, n)
@@ -67,7 +68,8 @@ int main(void) {
 def test_struct_layouts_match_header(lib, tmp_path):
     c = _c_layout(tmp_path)
     L = lib
-    for name in ["vrs_scene", "vrs_camera", "vrs_plan_opts", "vrs_plan", "vrs_run_info", "vrs_cull_opts"]:
+    for name in ["vrs_scene", "vrs_camera", "vrs_plan_opts", "vrs_plan", "vrs_run_info", "vrs_cull_opts",
+                 "vrs_combine_opts"]:
         assert int(c[name]) == ctypes.sizeof(getattr(L, name)), name
     for key, val in c.items():
         if "." in key:
@@ -163,3 +165,26 @@ def test_cull_points_rejects_bad_arguments_on_host(lib):
     bad = L.vrs_camera()
     assert call(cam=bad) == L.VRS_ERR_INVALID
     assert call(opts=L.vrs_cull_opts(0.5, 0.02, 0.05, 1)) == L.VRS_ERR_INVALID
+
+
+def test_foveal_combine_rejects_bad_arguments_on_host(lib):
+    """Argument errors return before any CUDA call (so this runs without a GPU)."""
+    L = lib
+    buf = ctypes.create_string_buffer(4096)
+    base = ctypes.addressof(buf)
+    P, F, out = base, base + 1024, base + 2048
+
+    def call(**kw):
+        a = dict(P=P, pw=16, ph=16, F=F, w=4, h=4, x0=2, y0=3, opts=None, out=out)
+        a.update(kw)
+        return L.vrs_foveal_combine(a["P"], a["pw"], a["ph"], a["F"], a["w"], a["h"], a["x0"], a["y0"], 8.0,
+                                    8.0, a["opts"], a["out"], None, None)
+
+    assert call(P=None) == L.VRS_ERR_INVALID
+    assert call(w=0) == L.VRS_ERR_INVALID
+    assert call(x0=13) == L.VRS_ERR_INVALID          # window not inside P
+    assert call(y0=-1) == L.VRS_ERR_INVALID
+    assert call(out=F + 8) == L.VRS_ERR_INVALID      # out overlaps F
+    assert call(opts=L.vrs_combine_opts(0.0, 0.75, 0.2, 0)) == L.VRS_ERR_INVALID
+    assert call(opts=L.vrs_combine_opts(256.0, 1.0, 0.2, 0)) == L.VRS_ERR_INVALID
+    assert call(opts=L.vrs_combine_opts(256.0, 0.75, 0.2, 3)) == L.VRS_ERR_INVALID
