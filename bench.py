@@ -418,7 +418,34 @@ def _foveal_points(args, flush):
     m = len(pts)
     byts = 12 * m + m + 4 * n_kept        # points read, decisions written, kept indices written
     peaks, src = measured_peaks()
+    # Sec. 3.4 combination over the same crop: P = the eye's image, F = a foveal image of the crop
+    # (a seeded stand-in for the neural renderer's output), timed as graph replays
+    from paper_2410_17932_gb300.combine import foveal_combine
+    rgb, _, _ = ras.outputs(0)
+    P = rgb.contiguous()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    F = (P[:, y0:y0 + crop.height, x0:x0 + crop.width] +
+         0.05 * torch.randn((3, crop.height, crop.width), device="cuda", generator=g)).contiguous()
+    out = torch.empty_like(F)
+    cmap = torch.empty(F.shape[1:], dtype=torch.float32, device="cuda")
+    ex, ey = x0 + crop.width / 2.0, y0 + crop.height / 2.0
+    graph2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cs):
+        for _ in range(3):
+            foveal_combine(P, F, x0, y0, ex, ey, out=out, c_out=cmap, stream=cs)
+        cs.synchronize()
+        with torch.cuda.graph(graph2, stream=cs):
+            foveal_combine(P, F, x0, y0, ex, ey, out=out, c_out=cmap, stream=cs)
+    torch.cuda.synchronize()
+    ms_comb = _time_loop(graph2.replay, flush, args.extra_steps)
+    cb_bytes = 4 * crop.width * crop.height * (3 + 3 + 3 + 1)
     return {
+        "combine": {"ms": round(ms_comb, 4), "pixels": crop.width * crop.height,
+                    "roofline": {"bound": "hbm", "kernel": "k_foveal_combine",
+                                 "achieved": round(cb_bytes / (ms_comb * 1e-3) / 1e9, 1),
+                                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": round(cb_bytes / (ms_comb * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                                 "bytes_per_launch": cb_bytes, "peak_source": src}},
         "cull_ms": round(ms_cull, 4), "points_per_s": round(m / (ms_cull * 1e-3), 1),
         "outside": int(counts[0]), "occluded": int(counts[1]), "kept": int(counts[2]),
         "roofline": {"bound": "hbm", "kernel": "k_cull_points", "achieved": round(byts / (ms_cull * 1e-3) / 1e9, 1),
