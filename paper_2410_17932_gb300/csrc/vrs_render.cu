@@ -95,7 +95,7 @@ __device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc,
 }
 
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
+__global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCKS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
     using Cfg = BlendCfg<TS>;
