@@ -83,10 +83,12 @@ def lib():
             P = ctypes.c_void_p
             L.orc_exp32.restype = ctypes.c_float
             L.orc_exp32.argtypes = [ctypes.c_float]
+            L.orc_log32.restype = ctypes.c_float
+            L.orc_log32.argtypes = [ctypes.c_float]
             L.orc_sh_basis_xyz.restype = None
             L.orc_sh_basis_xyz.argtypes = [ctypes.c_double] * 3 + [P]
             L.orc_decide.restype = ctypes.c_int
-            L.orc_decide.argtypes = [ctypes.c_int, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
+            L.orc_decide.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
                                      P, P, P, P, P, P]
             L.orc_project.restype = None
             L.orc_project.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
@@ -149,6 +151,10 @@ def exp32(x: float) -> float:
     return float(lib().orc_exp32(float(np.float32(x))))
 
 
+def log32(x: float) -> float:
+    return float(lib().orc_log32(float(np.float32(x))))
+
+
 def sh_basis(x: float, y: float, z: float) -> np.ndarray:
     out = np.zeros(16, np.float64)
     lib().orc_sh_basis_xyz(float(x), float(y), float(z), _p(out))
@@ -163,7 +169,8 @@ def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
                ubar=np.zeros(n, np.float32), vbar=np.zeros(n, np.float32),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32))
     c = camera(cam)
-    st = lib().orc_decide(n, _p(means), _p(ls), _p(q), ctypes.byref(c), tile,
+    lg = _f32(scene.opacity_logits)
+    st = lib().orc_decide(n, _p(means), _p(ls), _p(q), _p(lg), ctypes.byref(c), tile,
                           _p(out["visible"]), _p(out["depth"]), _p(out["ubar"]), _p(out["vbar"]),
                           _p(out["radius"]), _p(out["rect"]))
     # a Gaussian with any non-finite parameter is skipped (the C-ABI's NONFINITE rule)

@@ -149,6 +149,36 @@ float orc_exp32(float x)
     return p * scale;
 }
 
+/* FP32 natural logarithm used by the decision path, for finite normal x > 0:
+ * x = 2^e m with m in [sqrt(1/2), sqrt(2)) (exponent and mantissa split off
+ * the bit pattern, exact), ln x = e ln2 + 2 atanh(s) with s = (m - 1)/(m + 1),
+ * |s| < 0.172, and 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) by
+ * Horner's rule (truncation below 2e-9 relative).  Every step is one correctly
+ * rounded FP32 operation in the order written. */
+float orc_log32(float x)
+{
+    uint32_t bits;
+    memcpy(&bits, &x, 4);
+    int e = (int)((bits >> 23) & 0xffu) - 126;
+    bits = (bits & 0x807fffffu) | 0x3f000000u;        /* mantissa into [0.5, 1) */
+    float m;
+    memcpy(&m, &bits, 4);
+    if (m < 0.70710678f) { m = m * 2.0f; e = e - 1; }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float z = s * s;
+    float p = 0.111111111f;
+    p = p * z;
+    p = p + 0.142857143f;
+    p = p * z;
+    p = p + 0.2f;
+    p = p * z;
+    p = p + 0.333333333f;
+    p = p * z;
+    p = p + 1.0f;
+    const float r = (2.0f * s) * p;
+    return (float)e * 0.693147182f + r;
+}
+
 static int f_isfinite(float v) { return isfinite(v) ? 1 : 0; }
 
 /* keeps a tile index inside the int range before conversion */
@@ -176,7 +206,7 @@ static int floor_sum_div(float a, float b, int tile)
  * status bit 1: a quaternion had zero norm; bit 2: a non-finite parameter.
  */
 int orc_decide(int n, const float *means, const float *log_scales, const float *quats,
-               const orc_camera *cam, int tile, uint8_t *visible, float *depth,
+               const float *logits, const orc_camera *cam, int tile, uint8_t *visible, float *depth,
                float *ubar, float *vbar, int32_t *radius, int32_t *rect)
 {
     int status = 0;
@@ -276,11 +306,30 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         int x1 = floor_sum_div(xhi, cam->cx, tile) + 1;
         int y0 = floor_sum_div(ylo, cam->cy, tile);
         int y1 = floor_sum_div(yhi, cam->cy, tile) + 1;
+        /* clipped to the bounding box of the ellipse where alpha >= 1/255:
+         * x^T Sigma'^-1 x <= thr = 2 ln(255 o), o = sigmoid(logit), its half extents
+         * sqrt(thr Sigma'_xx) and sqrt(thr Sigma'_yy); thr carries a margin far above
+         * the rounding of any FP32 evaluation of alpha */
+        float eo = orc_exp32(-logits[g]);
+        float op = 1.0f / (1.0f + eo);
+        float thr = 2.0f * orc_log32(255.0f * op);
+        thr = thr * 1.001f;
+        thr = thr + 0.001f;
+        if (!(thr > 0.0f)) continue;
+        float hx = sqrtf(thr * a_), hy = sqrtf(thr * c_);
+        int bx0 = floor_sum_div(ub - hx, cam->cx, tile);
+        int bx1 = floor_sum_div(ub + hx, cam->cx, tile) + 1;
+        int by0 = floor_sum_div(vb - hy, cam->cy, tile);
+        int by1 = floor_sum_div(vb + hy, cam->cy, tile) + 1;
+        x0 = x0 > bx0 ? x0 : bx0;
+        x1 = x1 < bx1 ? x1 : bx1;
+        y0 = y0 > by0 ? y0 : by0;
+        y1 = y1 < by1 ? y1 : by1;
         x0 = x0 < 0 ? 0 : (x0 > gw ? gw : x0);
         x1 = x1 < 0 ? 0 : (x1 > gw ? gw : x1);
         y0 = y0 < 0 ? 0 : (y0 > gh ? gh : y0);
         y1 = y1 < 0 ? 0 : (y1 > gh ? gh : y1);
-        if ((x1 - x0) * (y1 - y0) == 0) continue;
+        if (x1 <= x0 || y1 <= y0) continue;
         visible[g] = 1;
         depth[g] = tz;
         ubar[g] = ub; vbar[g] = vb;

@@ -474,3 +474,52 @@ def test_numpy_projection_restatement_matches_c(orc):
         np.testing.assert_allclose(a[k], b[k], rtol=1e-12)
     np.testing.assert_allclose(a["conic"], b["conic"], rtol=1e-9)
     np.testing.assert_allclose(a["rgb"], b["rgb"], rtol=1e-12, atol=1e-14)
+
+
+def test_log32_within_four_ulp_of_libm(orc):
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([np.exp(rng.uniform(-80, 80, 4000)), rng.uniform(0.5, 2.0, 4000),
+                         [1.0, 2.0, 0.5, 255.0, 1e-30, 3e38]]).astype(np.float32)
+    for x in xs:
+        got = np.float32(orc.log32(float(x)))
+        ref = np.float32(math.log(float(x)))
+        ulp = np.spacing(np.abs(ref)) if ref != 0 else np.float32(1e-45)
+        assert abs(float(got) - math.log(float(x))) <= 4 * float(ulp) + 1e-12, x
+
+
+def test_tile_rectangle_holds_every_contributing_pixel(orc):
+    """The rectangle is the 3-sigma one clipped to the bounding box of the alpha >= 1/255
+    ellipse: every pixel of the 3-sigma rectangle whose FP64 alpha reaches 1/255 stays in it,
+    the clip only removes tiles outside that ellipse's FP64 bounding box (plus one tile), and
+    splats whose opacity cannot reach 1/255 get no tiles."""
+    scs, cams = I.plain_200()
+    sc = scs[0].subset(np.arange(1500))
+    sc.opacity_logits[:40] = -7.0                      # 255 o < 1: never 1/255
+    cam = cams[0]
+    d = orc.decide(sc, cam)
+    p = orc.project(sc, cam)
+    assert not d["visible"][:40].any()
+    jj, ii = np.mgrid[0:cam.height, 0:cam.width]
+    px, py = ii + 0.5 - cam.cx, jj + 0.5 - cam.cy
+    tight = 0
+    for g in np.nonzero(d["visible"])[0]:
+        a, b, c = p["conic"][g]
+        dx, dy = p["ubar"][g] - px, p["vbar"][g] - py
+        al = p["opacity"][g] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+        x0, x1, y0, y1 = d["rect"][g]
+        u, v = p["ubar"][g] + cam.cx, p["vbar"][g] + cam.cy
+        r = d["radius"][g]
+        # the 3-sigma rectangle (R7) before the clip, away from its tile edges
+        ox0, ox1 = math.floor((u - r) / 16), math.floor((u + r) / 16) + 1
+        oy0, oy1 = math.floor((v - r) / 16), math.floor((v + r) / 16) + 1
+        in_old = (ii // 16 > ox0) & (ii // 16 < ox1 - 1) & (jj // 16 > oy0) & (jj // 16 < oy1 - 1)
+        hit = (al >= 1 / 255) & in_old
+        assert np.all((ii[hit] // 16 >= x0) & (ii[hit] // 16 < x1) & (jj[hit] // 16 >= y0) & (jj[hit] // 16 < y1))
+        thr = 2 * math.log(255 * p["opacity"][g])
+        det = a * c - b * b
+        hx, hy = math.sqrt(thr * c / det), math.sqrt(thr * a / det)
+        assert x0 >= math.floor((u - hx) / 16) - 1 and x1 <= math.floor((u + hx) / 16) + 2
+        assert y0 >= math.floor((v - hy) / 16) - 1 and y1 <= math.floor((v + hy) / 16) + 2
+        tight += (x1 - x0) * (y1 - y0) < (math.floor((u + r) / 16) - math.floor((u - r) / 16) + 1) * \
+            (math.floor((v + r) / 16) - math.floor((v - r) / 16) + 1)
+    assert tight > 50                                   # the clip is active on this scene
