@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__
         }
         if (!nz) continue;
         Decision d;
-        decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+        decide(V, pre, m[0], m[1], m[2], logit, vt.tile, d);
         if (!d.visible) continue;
         any = true;
         // opacity

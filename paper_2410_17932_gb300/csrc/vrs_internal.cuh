@@ -118,6 +118,31 @@ __device__ __forceinline__ float exp32_cw(float x)
     return FMUL(p, __int_as_float((k + 127) << 23));
 }
 
+// FP32 natural logarithm of the decision path, for finite normal x > 0:
+// x = 2^e m with m in [sqrt(1/2), sqrt(2)) split off the bit pattern (exact),
+// ln x = e ln2 + 2 atanh(s), s = (m - 1)/(m + 1), |s| < 0.172, and
+// 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) by Horner's rule.
+// Each step is one correctly rounded operation, in this order.
+__device__ __forceinline__ float log32_cw(float x)
+{
+    uint32_t bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xffu) - 126;
+    float m = __uint_as_float((bits & 0x807fffffu) | 0x3f000000u);
+    if (m < 0.70710678f) {
+        m = FMUL(m, 2.0f);
+        e = e - 1;
+    }
+    const float s = FDIV(FSUB(m, 1.0f), FADD(m, 1.0f));
+    const float z = FMUL(s, s);
+    float p = 0.111111111f;
+    p = FADD(FMUL(p, z), 0.142857143f);
+    p = FADD(FMUL(p, z), 0.2f);
+    p = FADD(FMUL(p, z), 0.333333333f);
+    p = FADD(FMUL(p, z), 1.0f);
+    const float r = FMUL(FMUL(2.0f, s), p);
+    return FADD(FMUL((float)e, 0.693147182f), r);
+}
+
 // Per-Gaussian part: scales, rotation of the normalised quaternion, M = Rq S.
 struct GaussPre {
     float s[3];
@@ -188,7 +213,7 @@ struct Decision {
 
 // Per view.  `tile` is the tile edge; gw, gh the view's tile grid.
 __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, float mx, float my,
-                                       float mz, int tile, Decision &d)
+                                       float mz, float logit, int tile, Decision &d)
 {
     d.visible = false;
     const float *W = V.R;
@@ -277,6 +302,21 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     const float inv = 1.0f / (float)tile;    // a power of two: exact
     int x0 = floor_sum_div(xlo, V.cx, inv), x1 = floor_sum_div(xhi, V.cx, inv) + 1;
     int y0 = floor_sum_div(ylo, V.cy, inv), y1 = floor_sum_div(yhi, V.cy, inv) + 1;
+    // clipped to the bounding box of the ellipse where alpha >= 1/255:
+    // x^T Sigma'^-1 x <= thr = 2 ln(255 o), o = sigmoid(logit), half extents
+    // sqrt(thr Sigma'_xx) and sqrt(thr Sigma'_yy); thr carries a margin far above
+    // the rounding of any FP32 evaluation of alpha, so no tile that can hold a
+    // pixel with alpha >= 1/255 is dropped
+    const float eo = exp32_cw(-logit);
+    const float op = FDIV(1.0f, FADD(1.0f, eo));
+    float thr = FMUL(2.0f, log32_cw(FMUL(255.0f, op)));
+    thr = FADD(FMUL(thr, 1.001f), 0.001f);
+    if (!(thr > 0.0f)) return;
+    const float hx = __fsqrt_rn(FMUL(thr, a_)), hy = __fsqrt_rn(FMUL(thr, c_));
+    x0 = max(x0, floor_sum_div(FSUB(d.ub, hx), V.cx, inv));
+    x1 = min(x1, floor_sum_div(FADD(d.ub, hx), V.cx, inv) + 1);
+    y0 = max(y0, floor_sum_div(FSUB(d.vb, hy), V.cy, inv));
+    y1 = min(y1, floor_sum_div(FADD(d.vb, hy), V.cy, inv) + 1);
     x0 = min(max(x0, 0), V.gw);
     x1 = min(max(x1, 0), V.gw);
     y0 = min(max(y0, 0), V.gh);
@@ -285,7 +325,7 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     d.x1 = x1;
     d.y0 = y0;
     d.y1 = y1;
-    d.visible = (x1 - x0) * (y1 - y0) > 0;
+    d.visible = x1 > x0 && y1 > y0;
 }
 
 #undef FMUL

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
     const int lane = threadIdx.x & 31;
     const bool in = g < p.S.n;
     float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
+    float logit = 0.f;
     bool ok = in;
     if (in) {
         m[0] = __ldg(p.S.means + 3 * g);
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
 #pragma unroll
             for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
         }
-        const float logit = __ldg(p.S.logits + g);
+        logit = __ldg(p.S.logits + g);
         const float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
         if (!isfinite(chk)) ok = false;
     }
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
         const DevView &V = vt.v[p.views[vi]];
         Decision d;
         d.visible = false;
-        if (ok) decide(V, pre, m[0], m[1], m[2], vt.tile, d);
+        if (ok) decide(V, pre, m[0], m[1], m[2], logit, vt.tile, d);
         const uint32_t vb = __ballot_sync(FULL, d.visible);
         if (vb == 0u) continue;
         unsigned long long base = 0;
