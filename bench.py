@@ -201,28 +201,12 @@ class OracleFrameSampler:
         dec, proj, vis, rect = self.full[v]
         hit = (rect[:, 0] < bx + bw) & (rect[:, 1] > bx) & (rect[:, 2] < by + bh) & (rect[:, 3] > by)
         idx = vis[hit]
-        old = rect[hit].astype(np.int64)
-        r = old.copy()
+        r = rect[hit].copy()
         r[:, 0:2] = np.clip(r[:, 0:2] - bx, 0, bw)
         r[:, 2:4] = np.clip(r[:, 2:4] - by, 0, bh)
-        # the tile masks, re-indexed from the whole rectangle to its part inside the block
-        m_old = dec["tmask"][idx]
-        m_new = np.zeros(len(idx), np.uint64)
-        nx_o, nx_n = old[:, 1] - old[:, 0], r[:, 1] - r[:, 0]
-        area_n = nx_n * (r[:, 3] - r[:, 2])
-        for k in range(64):
-            ok = (m_old != 0) & (k < area_n)
-            kx, ky = k % np.maximum(nx_n, 1), k // np.maximum(nx_n, 1)
-            ob = (ky + r[:, 2] + by - old[:, 2]) * nx_o + (kx + r[:, 0] + bx - old[:, 0])
-            ob = np.clip(ob, 0, 63).astype(np.uint64)
-            setb = ok & (((m_old >> ob) & np.uint64(1)) == 1)
-            m_new |= np.where(setb, np.uint64(1) << np.uint64(k), np.uint64(0))
         x0, y0 = bx * tile, by * tile
         crop = cam.crop(x0, y0, min(bw * tile, cam.width - x0), min(bh * tile, cam.height - y0))
-        vis_b = dec["visible"][idx].copy()
-        vis_b[(m_old != 0) & (m_new == 0)] = 0          # a mask with no tile in the block
-        sdec = {"visible": vis_b, "depth": dec["depth"][idx],
-                "rect": np.ascontiguousarray(r.astype(np.int32)), "tmask": m_new}
+        sdec = {"visible": dec["visible"][idx], "depth": dec["depth"][idx], "rect": np.ascontiguousarray(r)}
         return self.NS(n=len(idx)), crop, sdec, proj[idx]
 
     def sample(self, budget_s: float, rng):

@@ -89,20 +89,20 @@ def lib():
             L.orc_sh_basis_xyz.argtypes = [ctypes.c_double] * 3 + [P]
             L.orc_decide.restype = ctypes.c_int
             L.orc_decide.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
-                                     P, P, P, P, P, P, P]
+                                     P, P, P, P, P, P]
             L.orc_project.restype = None
             L.orc_project.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                       ctypes.POINTER(OrcCamera), P]
             L.orc_render_brute.restype = None
-            L.orc_render_brute.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(OrcCamera),
+            L.orc_render_brute.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
                                            ctypes.c_int, ctypes.POINTER(OrcFlagOpts), P, P, P, P, P,
                                            P]
             L.orc_render_bucketed.restype = None
-            L.orc_render_bucketed.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(OrcCamera),
+            L.orc_render_bucketed.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
                                               ctypes.c_int, ctypes.POINTER(OrcFlagOpts), P, P, P, P,
                                               P, P, P]
             L.orc_render_bwd.restype = None
-            L.orc_render_bwd.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(OrcCamera),
+            L.orc_render_bwd.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
                                          ctypes.c_int, P, P, P, P]
             L.orc_param_grads.restype = None
             L.orc_param_grads.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
@@ -167,13 +167,12 @@ def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
     means, ls, q = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)
     out = dict(visible=np.zeros(n, np.uint8), depth=np.zeros(n, np.float32),
                ubar=np.zeros(n, np.float32), vbar=np.zeros(n, np.float32),
-               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
-               tmask=np.zeros(n, np.uint64))
+               radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32))
     c = camera(cam)
     lg = _f32(scene.opacity_logits)
     st = lib().orc_decide(n, _p(means), _p(ls), _p(q), _p(lg), ctypes.byref(c), tile,
                           _p(out["visible"]), _p(out["depth"]), _p(out["ubar"]), _p(out["vbar"]),
-                          _p(out["radius"]), _p(out["rect"]), _p(out["tmask"]))
+                          _p(out["radius"]), _p(out["rect"]))
     # a Gaussian with any non-finite parameter is skipped (the C-ABI's NONFINITE rule)
     bad = ~np.isfinite(np.asarray(scene.opacity_logits, np.float32))
     if n:
@@ -181,7 +180,6 @@ def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
     if bad.any():
         out["visible"][bad] = 0
         out["rect"][bad] = 0
-        out["tmask"][bad] = 0
         st |= 2
     out["status"] = int(st)
     return out
@@ -211,7 +209,7 @@ def render(scene, cam, tile: int = 16, mode: str = "bucketed", dec=None, proj=No
                sig=np.zeros((H, W), np.int32))
     c = camera(cam)
     fo = OrcFlagOpts(alpha_win, t_win)
-    args = (scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(dec["tmask"]), _p(proj),
+    args = (scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(proj),
             ctypes.byref(c), tile, ctypes.byref(fo))
     if mode == "brute":
         lib().orc_render_brute(*args, _p(out["rgb"]), _p(out["depth"]), _p(out["T"]),
@@ -233,7 +231,7 @@ def render_bwd(scene, cam, dL_drgb, dL_ddepth, dL_dT=None, tile: int = 16, dec=N
     gd = np.ascontiguousarray(dL_ddepth, np.float64)
     gt = None if dL_dT is None else np.ascontiguousarray(dL_dT, np.float64)
     c = camera(cam)
-    lib().orc_render_bwd(scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(dec["tmask"]), _p(proj),
+    lib().orc_render_bwd(scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(proj),
                          ctypes.byref(c), tile, _p(gr), _p(gd), None if gt is None else _p(gt),
                          _p(g2))
     return g2
@@ -294,20 +292,15 @@ def bin_sort(scenes: Sequence, views: Sequence, tile: int = 16, decs: Optional[L
         rect = d["rect"][vis].astype(np.int64)
         nx = rect[:, 1] - rect[:, 0]
         ny = rect[:, 3] - rect[:, 2]
-        area = nx * ny
-        if area.sum() == 0:
-            continue
-        # every tile of each rectangle, then only those the tile mask keeps (mask 0: all)
-        owner = np.repeat(np.arange(len(vis)), area)
-        start = np.cumsum(area) - area
-        k = np.arange(area.sum()) - np.repeat(start, area)
-        mask = d["tmask"][vis][owner]
-        keep = (mask == 0) | (((mask >> k.astype(np.uint64)) & np.uint64(1)) == 1)
-        owner, k = owner[keep], k[keep]
-        cnt = np.bincount(owner, minlength=len(vis))
+        cnt = nx * ny
         counts[rec_base[vi] + vis] = cnt
-        ox = k % nx[owner]
-        oy = k // nx[owner]
+        if cnt.sum() == 0:
+            continue
+        owner = np.repeat(np.arange(len(vis)), cnt)
+        start = np.cumsum(cnt) - cnt
+        k = np.arange(cnt.sum()) - np.repeat(start, cnt)
+        ox = k % np.repeat(nx, cnt)
+        oy = k // np.repeat(nx, cnt)
         tx = rect[owner, 0] + ox
         ty = rect[owner, 2] + oy
         tid = tile_base[vi] + ty * gw + tx

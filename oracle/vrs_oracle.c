@@ -198,41 +198,6 @@ static int floor_sum_div(float a, float b, int tile)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Whether tile (tx, ty) can hold a pixel centre where the splat reaches the
- * threshold: the minimum of the quadratic form x^T Q x, Q = [[A, B], [B, C]],
- * over the tile's rectangle of pixel centres, taken relative to the splat's
- * centre (U, V), is at most thr.  The form is convex: the minimum is 0 when the
- * centre lies in the rectangle, else it lies on an edge, where it is a 1D
- * quadratic minimised at a clamped vertex.  FP32, in the order written. */
-static int tile_hits(float U, float V, float A, float B, float C, float thr, int tile, int tx, int ty)
-{
-    const float X0 = (float)(tx * tile) + 0.5f, X1 = (float)(tx * tile + tile) - 0.5f;
-    const float Y0 = (float)(ty * tile) + 0.5f, Y1 = (float)(ty * tile + tile) - 0.5f;
-    const float u0 = X0 - U, u1 = X1 - U, v0 = Y0 - V, v1 = Y1 - V;
-    if (u0 <= 0.0f && u1 >= 0.0f && v0 <= 0.0f && v1 >= 0.0f) return 1;
-    const float B2 = 2.0f * B;
-    float best = 3.0e38f;
-    for (int e = 0; e < 2; ++e) {
-        /* a horizontal edge: v fixed, u at the clamped stationary point -B v / A */
-        const float v = e ? v1 : v0;
-        float u = -((B * v) / A);
-        u = fminf(fmaxf(u, u0), u1);
-        float q = (A * u) * u;
-        q = q + (B2 * u) * v;
-        q = q + (C * v) * v;
-        best = fminf(best, q);
-        /* a vertical edge: u fixed, v at -B u / C */
-        const float uu = e ? u1 : u0;
-        float vv = -((B * uu) / C);
-        vv = fminf(fmaxf(vv, v0), v1);
-        float q2 = (A * uu) * uu;
-        q2 = q2 + (B2 * uu) * vv;
-        q2 = q2 + (C * vv) * vv;
-        best = fminf(best, q2);
-    }
-    return best <= thr;
-}
-
 /* The integer decisions, in FP32.  Each statement below is one correctly
  * rounded IEEE operation; the order is part of the definition.
  *
@@ -242,7 +207,7 @@ static int tile_hits(float U, float V, float A, float B, float C, float thr, int
  */
 int orc_decide(int n, const float *means, const float *log_scales, const float *quats,
                const float *logits, const orc_camera *cam, int tile, uint8_t *visible, float *depth,
-               float *ubar, float *vbar, int32_t *radius, int32_t *rect, uint64_t *tmask)
+               float *ubar, float *vbar, int32_t *radius, int32_t *rect)
 {
     int status = 0;
     const float *W = cam->R;
@@ -253,7 +218,6 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
     for (int g = 0; g < n; ++g) {
         visible[g] = 0; depth[g] = 0.f; ubar[g] = 0.f; vbar[g] = 0.f; radius[g] = 0;
         rect[4 * g + 0] = rect[4 * g + 1] = rect[4 * g + 2] = rect[4 * g + 3] = 0;
-        tmask[g] = 0;
         const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
         const float *ls = log_scales + 3 * g;
         const float *q = quats + 4 * g;
@@ -316,7 +280,6 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         }
         float n0 = v0[0] * v0[0]; n0 = n0 + v0[1] * v0[1]; n0 = n0 + v0[2] * v0[2];
         float n1 = v1[0] * v1[0]; n1 = n1 + v1[1] * v1[1]; n1 = n1 + v1[2] * v1[2];
-        float bb = v0[0] * v1[0]; bb = bb + v0[1] * v1[1]; bb = bb + v0[2] * v1[2];
         /* det(V V^T) = |v0 x v1|^2, with v0 x v1 = diag(s1 s2, s0 s2, s0 s1) Rq^T (T0 x T1) */
         float c0 = T0[1] * T1[2] - T0[2] * T1[1];
         float c1 = T0[2] * T1[0] - T0[0] * T1[2];
@@ -367,19 +330,6 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         y0 = y0 < 0 ? 0 : (y0 > gh ? gh : y0);
         y1 = y1 < 0 ? 0 : (y1 > gh ? gh : y1);
         if (x1 <= x0 || y1 <= y0) continue;
-        /* rectangles of at most 64 tiles keep only the tiles the ellipse reaches,
-         * as a bit mask in row-major order (0 = every tile of the rectangle) */
-        uint64_t mask = 0;
-        if ((x1 - x0) * (y1 - y0) <= 64) {
-            const float U = ub + cam->cx, V = vb + cam->cy;
-            const float A = c_ / det, B = -(bb / det), C = a_ / det;
-            for (int ty = y0; ty < y1; ++ty)
-                for (int tx = x0; tx < x1; ++tx)
-                    if (tile_hits(U, V, A, B, C, thr, tile, tx, ty))
-                        mask |= 1ull << ((ty - y0) * (x1 - x0) + (tx - x0));
-            if (mask == 0) continue;
-        }
-        tmask[g] = mask;
         visible[g] = 1;
         depth[g] = tz;
         ubar[g] = ub; vbar[g] = vb;
@@ -518,13 +468,6 @@ typedef struct {
     double t_win;       /* relative window around 1e-4 that flags a pixel */
 } orc_flag_opts;
 
-/* The tiles of Gaussian g: its rectangle, restricted to the set bits of its mask
- * (row-major over the rectangle) when the mask is not 0. */
-static int in_mask(const int32_t *r, uint64_t m, int x, int y)
-{
-    return m == 0 || ((m >> ((y - r[2]) * (r[1] - r[0]) + (x - r[0]))) & 1ull) != 0;
-}
-
 static void composite_pixel(const cand_t *cands, int nc, const orc_proj *P, double pxc, double pyc,
                             const orc_flag_opts *fo, double *rgb, double *dep, double *Tout,
                             int32_t *last_out, uint8_t *flag_out, int32_t *sig_out)
@@ -563,7 +506,7 @@ static void composite_pixel(const cand_t *cands, int nc, const orc_proj *P, doub
 
 /* Brute force: every pixel scans all n Gaussians.  Outputs are CHW. */
 void orc_render_brute(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
-                      const uint64_t *tmask, const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
+                      const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
                       double *rgb, double *depth, double *Tfin, int32_t *n_contrib, uint8_t *flags,
                       int32_t *sig)
 {
@@ -580,7 +523,6 @@ void orc_render_brute(int n, const uint8_t *visible, const float *depth_key, con
                     if (!visible[g]) continue;
                     const int32_t *r = rect + 4 * g;
                     if (tx < r[0] || tx >= r[1] || ty < r[2] || ty >= r[3]) continue;
-                    if (!in_mask(r, tmask[g], tx, ty)) continue;
                     cands[nc].key = depth_key[g];
                     cands[nc].idx = g;
                     ++nc;
@@ -604,7 +546,7 @@ void orc_render_brute(int n, const uint8_t *visible, const float *depth_key, con
 typedef struct { int32_t *start; int32_t *count; cand_t *items; int ntiles; } tile_lists;
 
 static void build_tile_lists(int n, const uint8_t *visible, const float *depth_key,
-                             const int32_t *rect, const uint64_t *tmask, int gw, int gh, tile_lists *L)
+                             const int32_t *rect, int gw, int gh, tile_lists *L)
 {
     int nt = gw * gh;
     L->ntiles = nt;
@@ -615,8 +557,7 @@ static void build_tile_lists(int n, const uint8_t *visible, const float *depth_k
         if (!visible[g]) continue;
         const int32_t *r = rect + 4 * g;
         for (int y = r[2]; y < r[3]; ++y)
-            for (int x = r[0]; x < r[1]; ++x)
-                if (in_mask(r, tmask[g], x, y)) { L->count[y * gw + x]++; ++total; }
+            for (int x = r[0]; x < r[1]; ++x) { L->count[y * gw + x]++; ++total; }
     }
     int64_t acc = 0;
     for (int t = 0; t < nt; ++t) { L->start[t] = (int32_t)acc; acc += L->count[t]; }
@@ -628,7 +569,6 @@ static void build_tile_lists(int n, const uint8_t *visible, const float *depth_k
         const int32_t *r = rect + 4 * g;
         for (int y = r[2]; y < r[3]; ++y)
             for (int x = r[0]; x < r[1]; ++x) {
-                if (!in_mask(r, tmask[g], x, y)) continue;
                 int t = y * gw + x;
                 cand_t *c = L->items + L->start[t] + fill[t]++;
                 c->key = depth_key[g];
@@ -647,7 +587,7 @@ static void free_tile_lists(tile_lists *L) { free(L->start); free(L->count); fre
  * brute force.  `tile_mask` (nullable, gw*gh bytes) restricts the work to the
  * tiles marked 1; other pixels are left untouched (used for bounded timing). */
 void orc_render_bucketed(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
-                         const uint64_t *tmask, const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
+                         const orc_proj *P, const orc_camera *cam, int tile, const orc_flag_opts *fo,
                          const uint8_t *tile_mask, double *rgb, double *depth, double *Tfin,
                          int32_t *n_contrib, uint8_t *flags, int32_t *sig)
 {
@@ -655,7 +595,7 @@ void orc_render_bucketed(int n, const uint8_t *visible, const float *depth_key, 
     const size_t HW = (size_t)W * H;
     const int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
     tile_lists L;
-    build_tile_lists(n, visible, depth_key, rect, tmask, gw, gh, &L);
+    build_tile_lists(n, visible, depth_key, rect, gw, gh, &L);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < gw * gh; ++t) {
         if (tile_mask && !tile_mask[t]) continue;
@@ -745,14 +685,14 @@ static void reverse_pixel(const cand_t *cands, int nc, const orc_proj *P, double
 
 /* dL_drgb [3,H,W], dL_ddepth [H,W], dL_dT [H,W] (nullable); g2 is [n, 10], accumulated. */
 void orc_render_bwd(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
-                    const uint64_t *tmask, const orc_proj *P, const orc_camera *cam, int tile, const double *dL_drgb,
+                    const orc_proj *P, const orc_camera *cam, int tile, const double *dL_drgb,
                     const double *dL_ddepth, const double *dL_dT, double *g2)
 {
     const int W = cam->width, H = cam->height;
     const size_t HW = (size_t)W * H;
     const int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
     tile_lists L;
-    build_tile_lists(n, visible, depth_key, rect, tmask, gw, gh, &L);
+    build_tile_lists(n, visible, depth_key, rect, gw, gh, &L);
     int maxc = 1;
     for (int t = 0; t < gw * gh; ++t) if (L.count[t] > maxc) maxc = L.count[t];
     int nthreads = 1;
