@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
         P.done1 = !in1;
 
         for (uint32_t bs = range.x; bs < range.y; bs += Cfg::BATCH) {
-            if (__syncthreads_and(P.done0 && P.done1)) break;
+            // before a later batch: the previous one is no longer read, and the CTA leaves
+            // when all of its pixels have stopped (the first batch needs neither)
+            if (bs != range.x && __syncthreads_and(P.done0 && P.done1)) break;
             const uint32_t j = bs + tid;
             const uint32_t rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
             uint32_t mask = 0u;
@@ -199,7 +201,6 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                     pix_update2<COUNT>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
                 }
             }
-            __syncthreads();
         }
         n_eval += (in0 ? P.stop0 : 0u) + (in1 ? P.stop1 : 0u);
         const int64_t HW = (int64_t)V.w * V.h;
