@@ -108,6 +108,9 @@ def lib():
             L.orc_param_grads.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                           ctypes.POINTER(OrcCamera), P, P, P, P, P, P, P]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_combine_bwd.restype = None
+            L.orc_combine_bwd.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [P, P, P]
             L.orc_combine.restype = None
             L.orc_combine.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [P, P]
@@ -364,3 +367,19 @@ def combine(P, F, x0: int, y0: int, ex: float, ey: float, d_f: float = COMBINE_D
     lib().orc_combine(_p(Pf), pw, ph, _p(Ff), w, h, int(x0), int(y0), float(ex), float(ey), float(d_f),
                       float(m), float(gamma), _p(out), _p(c))
     return out, c
+
+
+def combine_bwd(P, F, x0: int, y0: int, ex: float, ey: float, g, d_f: float = COMBINE_DF,
+                m: float = COMBINE_M, gamma: float = COMBINE_GAMMA):
+    """Reverse pass of `combine`: (dL/dP [3, H, W] (nonzero on the window only), dL/dF [3, h, w])
+    for the upstream gradient g = dL/dout [3, h, w]."""
+    Pf = _f32(P)
+    Ff = _f32(F)
+    _, ph, pw = Pf.shape
+    _, h, w = Ff.shape
+    gg = np.ascontiguousarray(g, np.float64)
+    dP = np.zeros((3, ph, pw), np.float64)
+    dF = np.zeros((3, h, w), np.float64)
+    lib().orc_combine_bwd(_p(Pf), pw, ph, _p(Ff), w, h, int(x0), int(y0), float(ex), float(ey), float(d_f),
+                          float(m), float(gamma), _p(gg), _p(dP), _p(dF))
+    return dP, dF

@@ -1036,3 +1036,65 @@ void orc_combine(const float *P, int pw, int ph, const float *F, int w, int h, i
             if (c_out) c_out[q] = c;
         }
 }
+
+/* Reverse pass of the combination (Sec. 3.4, for the end-to-end training of
+ * Sec. 3.5), in FP64.  With out = p + c (f - p) per channel and
+ * c = 1 - S2(x), x = clamp(f_p + gamma f_e, 0, 1):
+ *   dL/dp += (1 - c) g,   dL/df += c g (direct),
+ *   dL/dc  = sum_ch g (f - p),   dc/dx = -S2'(x) = -30 x^2 (1 - x)^2 inside (0, 1), else 0,
+ *   dx/df_e = gamma,   f_e = |(g_x, g_y)| (its gradient taken as 0 where f_e = 0),
+ *   g_x, g_y: the Sobel sums over the channel mean L of F (border replicated),
+ *   dL/dL at each clamped tap += dL/dg_x k_x / 8 + dL/dg_y k_y / 8,
+ *   dL/df_ch += dL/dL / 3.
+ * g = dL/dout [3][h][w]; dP [3][ph][pw] (the window is written by +=), dF [3][h][w] (+=). */
+void orc_combine_bwd(const float *P, int pw, int ph, const float *F, int w, int h, int x0, int y0,
+                     double ex, double ey, double d_f, double m, double gamma, const double *g,
+                     double *dP, double *dF)
+{
+    const size_t hw = (size_t)w * h, phw = (size_t)pw * ph;
+    double *dL = (double *)calloc(hw > 0 ? hw : 1, sizeof(double));
+    static const int kx[3][3] = {{-1, 0, 1}, {-2, 0, 2}, {-1, 0, 1}};
+    static const int ky[3][3] = {{-1, -2, -1}, {0, 0, 0}, {1, 2, 1}};
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            double du = (x0 + i + 0.5) - ex, dv = (y0 + j + 0.5) - ey;
+            double r = sqrt(du * du + dv * dv) / d_f;
+            r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+            double fp = (r - m) / (1.0 - m);
+            double gx = 0.0, gy = 0.0;
+            for (int b = -1; b <= 1; ++b)
+                for (int a = -1; a <= 1; ++a) {
+                    double L = orc_chan_mean(F, w, h, i + a, j + b);
+                    gx += kx[b + 1][a + 1] * L;
+                    gy += ky[b + 1][a + 1] * L;
+                }
+            gx /= 8.0;
+            gy /= 8.0;
+            double fe = sqrt(gx * gx + gy * gy);
+            double x = fp + gamma * fe;
+            double xc = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+            double c = 1.0 - xc * xc * xc * (xc * (6.0 * xc - 15.0) + 10.0);
+            const size_t q = (size_t)j * w + i;
+            const size_t pp = (size_t)(y0 + j) * pw + (x0 + i);
+            double dLdc = 0.0;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double gc = g[ch * hw + q];
+                dP[ch * phw + pp] += (1.0 - c) * gc;
+                dF[ch * hw + q] += c * gc;
+                dLdc += gc * ((double)F[ch * hw + q] - (double)P[ch * phw + pp]);
+            }
+            if (!(x > 0.0 && x < 1.0) || fe == 0.0) continue;
+            double dLdfe = dLdc * (-30.0 * x * x * (1.0 - x) * (1.0 - x)) * gamma;
+            double dgx = dLdfe * gx / fe, dgy = dLdfe * gy / fe;
+            for (int b = -1; b <= 1; ++b)
+                for (int a = -1; a <= 1; ++a) {
+                    int ii = i + a, jj = j + b;
+                    ii = ii < 0 ? 0 : (ii >= w ? w - 1 : ii);
+                    jj = jj < 0 ? 0 : (jj >= h ? h - 1 : jj);
+                    dL[(size_t)jj * w + ii] += (dgx * kx[b + 1][a + 1] + dgy * ky[b + 1][a + 1]) / 8.0;
+                }
+        }
+    for (size_t q = 0; q < hw; ++q)
+        for (int ch = 0; ch < 3; ++ch) dF[ch * hw + q] += dL[q] / 3.0;
+    free(dL);
+}

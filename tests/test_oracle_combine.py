@@ -82,3 +82,40 @@ def test_identity_convexity_and_transpose(orc):
     outT, cT = oracle.combine(np.ascontiguousarray(P.transpose(0, 2, 1)), np.ascontiguousarray(F.transpose(0, 2, 1)),
                               y0, x0, ey, ex, d_f=d_f)
     assert np.allclose(outT, out.transpose(0, 2, 1), atol=1e-12) and np.allclose(cT, c.T, atol=1e-12)
+
+
+def test_reverse_pass_matches_central_differences(orc):
+    """The oracle's reverse pass against FP64 central differences of its forward, on images
+    quantised to 2^-10 so that the +-h perturbations (h = 2^-10) are exact in FP32, with the
+    blending band over the whole crop so that the edge-factor path is exercised."""
+    rng = np.random.default_rng(21)
+    H, W, h, w, x0, y0 = 24, 30, 14, 16, 6, 5
+    q = 1.0 / 1024
+    P = (np.round(rng.uniform(0.1, 0.9, (3, H, W)) / q) * q).astype(np.float32)
+    yy, xx = np.mgrid[0:h, 0:w]
+    F = 0.5 + 0.3 * np.sin(xx / 3.0)[None] * np.cos(yy / 2.5)[None] + 0.05 * rng.standard_normal((3, h, w))
+    F = (np.round(F / q) * q).astype(np.float32)
+    ex, ey, d_f, m, gamma = x0 + 3.3, y0 + 2.2, 14.0, 0.2, 0.8
+    g = rng.standard_normal((3, h, w))
+    dP, dF = orc.combine_bwd(P, F, x0, y0, ex, ey, g, d_f=d_f, m=m, gamma=gamma)
+    _, c = orc.combine(P, F, x0, y0, ex, ey, d_f=d_f, m=m, gamma=gamma)
+    assert ((c > 0.02) & (c < 0.98)).mean() > 0.5            # most of the crop is on the band
+
+    def loss(Pv, Fv):
+        out, _ = orc.combine(Pv, Fv, x0, y0, ex, ey, d_f=d_f, m=m, gamma=gamma)
+        return float((out * g).sum())
+
+    hh = q
+    picks_F = [(ch, jy, ix) for ch in range(3) for jy, ix in ((0, 0), (h - 1, w - 1), (0, 7), (5, 0), (6, 9), (9, 4))]
+    for ch, jy, ix in picks_F:
+        Fp, Fm = F.copy(), F.copy()
+        Fp[ch, jy, ix] += hh
+        Fm[ch, jy, ix] -= hh
+        fd = (loss(P, Fp) - loss(P, Fm)) / (2 * hh)
+        assert abs(fd - dF[ch, jy, ix]) <= 2e-4 * (1 + abs(fd)), (ch, jy, ix, fd, dF[ch, jy, ix])
+    for ch, jy, ix in ((0, y0, x0), (1, y0 + 7, x0 + 9), (2, y0 + h - 1, x0 + w - 1), (0, 0, 0)):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[ch, jy, ix] += hh
+        Pm[ch, jy, ix] -= hh
+        fd = (loss(Pp, F) - loss(Pm, F)) / (2 * hh)
+        assert abs(fd - dP[ch, jy, ix]) <= 2e-4 * (1 + abs(fd)), (ch, jy, ix, fd, dP[ch, jy, ix])
