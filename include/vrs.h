@@ -354,6 +354,22 @@ vrs_status vrs_foveal_combine(const float *P, int32_t pw, int32_t ph, const floa
                               int32_t x0, int32_t y0, float ex, float ey, const vrs_combine_opts *opts,
                               float *out, float *c_out, void *stream);
 
+/* Reverse pass of vrs_foveal_combine, for the end-to-end training of Sec. 3.5.
+ * With out = p + c (f - p) and c = 1 - S2(x), x = clamp(f_p + gamma f_e, 0, 1):
+ * dL/dp = (1 - c) g and dL/df = c g directly, and dL/dc = sum_ch g (f - p) flows
+ * through dc/dx = -S2'(x) (0 where x is clamped), gamma, f_e = |grad| (0 where
+ * f_e = 0), the Sobel taps (border replicated) and the channel mean into F.
+ * dL_dout: device [3][h][w].  dL_dP: device [3][ph][pw], accumulated (+=) on
+ * the window.  dL_dF: device [3][h][w], accumulated (+=).  scratch: device
+ * [h][w] float, overwritten.  Other arguments and errors as vrs_foveal_combine;
+ * also VRS_ERR_INVALID for a NULL gradient or scratch pointer.  The edge
+ * path's taps are summed with atomics, so its last bits may vary from run to
+ * run.  No allocation; stream ordered. */
+vrs_status vrs_foveal_combine_bwd(const float *P, int32_t pw, int32_t ph, const float *F, int32_t w,
+                                  int32_t h, int32_t x0, int32_t y0, float ex, float ey,
+                                  const vrs_combine_opts *opts, const float *dL_dout, float *dL_dP,
+                                  float *dL_dF, float *scratch, void *stream);
+
 /* A static, human-readable name of a status. */
 const char *vrs_status_string(vrs_status status);
 

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     ("vrs_foveal_combine", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
                                   ctypes.POINTER(vrs_combine_opts), _vp, _vp, _vp]),
+    ("vrs_foveal_combine_bwd", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
+                                      ctypes.POINTER(vrs_combine_opts), _vp, _vp, _vp, _vp, _vp]),
     ("vrs_cull_points", _i32, [_vp, _i64, ctypes.POINTER(vrs_camera), _i32, _i32, _vp, _vp, _i32, _i32,
                                ctypes.POINTER(vrs_cull_opts), _vp, _vp, _vp, _vp]),
     ("vrs_status_string", ctypes.c_char_p, [_i32]),
@@ -184,3 +186,11 @@ def vrs_foveal_combine(P: int, pw: int, ph: int, F: int, w: int, h: int, x0: int
                        ey: float, opts, out: int, c_out: Optional[int], stream: Optional[int]) -> int:
     return load().vrs_foveal_combine(P, pw, ph, F, w, h, x0, y0, ex, ey,
                                      ctypes.byref(opts) if opts is not None else None, out, c_out, stream)
+
+
+def vrs_foveal_combine_bwd(P: int, pw: int, ph: int, F: int, w: int, h: int, x0: int, y0: int, ex: float,
+                           ey: float, opts, dL_dout: int, dL_dP: int, dL_dF: int, scratch: int,
+                           stream: Optional[int]) -> int:
+    return load().vrs_foveal_combine_bwd(P, pw, ph, F, w, h, x0, y0, ex, ey,
+                                         ctypes.byref(opts) if opts is not None else None, dL_dout, dL_dP,
+                                         dL_dF, scratch, stream)

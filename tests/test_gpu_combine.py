@@ -59,3 +59,35 @@ def test_combine_options():
     P, F = _images(200, 260, 150, 170, 9)
     _check(P, F, 40, 30, 120.0, 100.0, d_f=60.0, m=0.5, gamma=1.5)
     _check(P, F, 40, 30, 120.0, 100.0, d_f=300.0, m=-0.5, gamma=0.0)
+
+
+def test_combine_reverse_pass_matches_oracle():
+    torch = torch_cuda()
+    from paper_2410_17932_gb300.combine import foveal_combine_bwd
+    P, F = _images(90, 120, 60, 70, 5)
+    x0, y0, ex, ey, d_f, m, gamma = 20, 15, 52.0, 41.0, 40.0, 0.3, 0.6
+    rng = np.random.default_rng(6)
+    g = rng.standard_normal(F.shape).astype(np.float32)
+    dP_ref, dF_ref = oracle.combine_bwd(P, F, x0, y0, ex, ey, g, d_f=d_f, m=m, gamma=gamma)
+    Pt, Ft = torch.as_tensor(P, device="cuda"), torch.as_tensor(F, device="cuda")
+    dP, dF = foveal_combine_bwd(Pt, Ft, x0, y0, ex, ey, torch.as_tensor(g, device="cuda"), d_f=d_f, m=m,
+                                gamma=gamma)
+    dP, dF = dP.cpu().numpy(), dF.cpu().numpy()
+    for got, ref in ((dP, dP_ref), (dF, dF_ref)):
+        assert np.abs(got - ref).max() <= 1e-4 * (1 + np.abs(ref).max())
+    assert np.abs(dF_ref).max() > 0.1 and np.abs(dP_ref).max() > 0.1
+
+
+def test_combine_autograd_function():
+    torch = torch_cuda()
+    from paper_2410_17932_gb300.combine import FovealCombineFunction
+    P, F = _images(50, 60, 30, 34, 8)
+    Pt = torch.as_tensor(P, device="cuda").requires_grad_(True)
+    Ft = torch.as_tensor(F, device="cuda").requires_grad_(True)
+    out = FovealCombineFunction.apply(Pt, Ft, 10, 9, 27.0, 24.0, 20.0, 0.4, 0.5)
+    ref, _ = oracle.combine(P, F, 10, 9, 27.0, 24.0, d_f=20.0, m=0.4, gamma=0.5)
+    assert np.abs(out.detach().cpu().numpy() - ref).max() <= TOL
+    (out * out).sum().backward()
+    dP_ref, dF_ref = oracle.combine_bwd(P, F, 10, 9, 27.0, 24.0, 2 * ref, d_f=20.0, m=0.4, gamma=0.5)
+    assert np.abs(Pt.grad.cpu().numpy() - dP_ref).max() <= 1e-4 * (1 + np.abs(dP_ref).max())
+    assert np.abs(Ft.grad.cpu().numpy() - dF_ref).max() <= 1e-4 * (1 + np.abs(dF_ref).max())
