@@ -207,7 +207,18 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
         const int64_t lp = (int64_t)py * V.w + px;
         const int64_t pix = V.pix_base + lp;
         float *rgb = a.rgb + 3 * V.pix_base;
-        if (in0) {
+        // both pixels at once when every plane's pair is 8-byte aligned
+        const bool bases8 = ((reinterpret_cast<uintptr_t>(a.rgb) | reinterpret_cast<uintptr_t>(a.depth) |
+                              reinterpret_cast<uintptr_t>(a.Tf) | reinterpret_cast<uintptr_t>(a.ncontrib)) & 7u) == 0;
+        const bool pair = bases8 && in1 && ((3 * V.pix_base + lp) & 1) == 0 && (HW & 1) == 0 && (pix & 1) == 0;
+        if (pair) {
+            *reinterpret_cast<float2 *>(rgb + lp) = P.R;
+            *reinterpret_cast<float2 *>(rgb + HW + lp) = P.G;
+            *reinterpret_cast<float2 *>(rgb + 2 * HW + lp) = P.B;
+            *reinterpret_cast<float2 *>(a.depth + pix) = P.D;
+            *reinterpret_cast<float2 *>(a.Tf + pix) = P.T;
+            *reinterpret_cast<uint2 *>(a.ncontrib + pix) = make_uint2(P.last0, P.last1);
+        } else if (in0) {
             rgb[lp] = P.R.x;
             rgb[HW + lp] = P.G.x;
             rgb[2 * HW + lp] = P.B.x;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
             a.Tf[pix] = P.T.x;
             a.ncontrib[pix] = P.last0;
         }
-        if (in1) {
+        if (in1 && !pair) {
             rgb[lp + 1] = P.R.y;
             rgb[HW + lp + 1] = P.G.y;
             rgb[2 * HW + lp + 1] = P.B.y;
