@@ -50,14 +50,15 @@ __device__ __forceinline__ void pixel_adjoint(PixState &p, float q, float dx, fl
     const float e = ex2_approx(__fsub_rn(B.y, q));
     const float al = fminf(e, 0.99f);
     const float om = 1.0f - al;
-    const float Tb = p.T / om;
+    const float rom = __frcp_rn(om);           // 1 / (1 - alpha)
+    const float Tb = p.T * rom;
     const float w = al * Tb;
     g[6] += p.gC0 * w;
     g[7] += p.gC1 * w;
     g[8] += p.gC2 * w;
     g[9] += p.gD * w;
     const float dLda = Tb * (p.gC0 * C.x + p.gC1 * C.y + p.gC2 * C.z + p.gD * B.w) -
-                       (p.gC0 * p.SC0 + p.gC1 * p.SC1 + p.gC2 * p.SC2 + p.gD * p.SD + p.gT * p.Tfin) / om;
+                       (p.gC0 * p.SC0 + p.gC1 * p.SC1 + p.gC2 * p.SC2 + p.gD * p.SD + p.gT * p.Tfin) * rom;
     p.SC0 = fmaf(C.x, w, p.SC0);
     p.SC1 = fmaf(C.y, w, p.SC1);
     p.SC2 = fmaf(C.z, w, p.SC2);
@@ -176,17 +177,25 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float dx = Ak.x - pxc, dy = Ak.y - pyc;
             if (c0) pixel_adjoint(P0, q0, dx, dy, Ak, Bk, Ck, g);
             if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, Ak, Bk, Ck, g);
+            // reduce-scatter over the warp: at each level a lane keeps one half of its
+            // values and adds its partner's copy of that half, so the 10 (padded to 16)
+            // sums take 16 shuffles; value s ends in lanes 2s and 2s + 1
+            float r16[16];
 #pragma unroll
-            for (int i = 0; i < kGrad2D; ++i) {
+            for (int i = 0; i < 16; ++i) r16[i] = i < kGrad2D ? g[i] : 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) g[i] += __shfl_xor_sync(FULL, g[i], o);
+            for (int c = 16, o = 16; c > 1; c >>= 1, o >>= 1) {
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int i = 0; i < c / 2; ++i) {
+                    const float keep = upper ? r16[i + c / 2] : r16[i];
+                    const float send = upper ? r16[i] : r16[i + c / 2];
+                    r16[i] = keep + __shfl_xor_sync(FULL, send, o);
+                }
             }
-            if (lane < kGrad2D) {
-                float v = g[0];
-#pragma unroll
-                for (int i = 1; i < kGrad2D; ++i) v = lane == i ? g[i] : v;
-                atomicAdd(a.grad2d + (size_t)wR[w][k] * kGrad2D + lane, v);
-            }
+            const float v = r16[0] + __shfl_xor_sync(FULL, r16[0], 1);
+            const int s = (lane >> 1) & 15;
+            if ((lane & 1) == 0 && s < kGrad2D) atomicAdd(a.grad2d + (size_t)wR[w][k] * kGrad2D + s, v);
         }
         __syncwarp();
     }
@@ -273,6 +282,17 @@ __global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= p.S.n) return;
     if (p.st->flags & ST_CAPACITY) return;
+    // most Gaussians touch no pixel of any view: leave before reading their parameters
+    bool touched = false;
+    for (int vi = 0; vi < p.n_views && !touched; ++vi) {
+        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(vt.v[p.views[vi]].rec_base + g) * kGrad2D);
+#pragma unroll
+        for (int i = 0; i < kGrad2D / 2; ++i) {
+            const float2 v = __ldg(G2 + i);
+            touched |= v.x != 0.f || v.y != 0.f;
+        }
+    }
+    if (!touched) return;
     const float m[3] = {p.S.means[3 * g], p.S.means[3 * g + 1], p.S.means[3 * g + 2]};
     const float ls[3] = {p.S.log_scales[3 * g], p.S.log_scales[3 * g + 1], p.S.log_scales[3 * g + 2]};
     const float q[4] = {p.S.quats[4 * g], p.S.quats[4 * g + 1], p.S.quats[4 * g + 2], p.S.quats[4 * g + 3]};
