@@ -30,8 +30,8 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               const float *dL_ddepth, const float *dL_dT, float *grad2d,
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
-                                   const int8_t *views, int n_views, const float *grad2d,
-                                   const DevStatus *st, cudaStream_t s);
+                                   const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
+                                   uint32_t *list, int n_sms, cudaStream_t s);
 }  // namespace vrs
 
 using namespace vrs;
@@ -337,7 +337,9 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];
         const int nv = views_of_scene(plan, sc, vlist);
-        e = launch_backward_params(vt, dev_scene(scenes[sc]), dev_scene(grads[sc]), vlist, nv, g2, st, s);
+        e = launch_backward_params(vt, dev_scene(scenes[sc]), dev_scene(grads[sc]), vlist, nv, g2,
+                                   at<DevStatus>(workspace, plan->off_status),
+                                   at<uint32_t>(workspace, plan->off_pairs), plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
     }
     return VRS_OK;

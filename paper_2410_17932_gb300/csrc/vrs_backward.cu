@@ -273,26 +273,13 @@ struct ParamArgs {
     int8_t views[VRS_MAX_VIEWS];
     const float *grad2d;
     const DevStatus *st;
+    uint32_t *list;            // Gaussians with a nonzero record gradient (scratch)
+    uint32_t *list_count;
 };
 
 template <int K>
-__global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__ ViewTable vt,
-                                                         const __grid_constant__ ParamArgs p)
+__device__ __forceinline__ void param_grads_one(const ViewTable &vt, const ParamArgs &p, int g)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.S.n) return;
-    if (p.st->flags & ST_CAPACITY) return;
-    // most Gaussians touch no pixel of any view: leave before reading their parameters
-    bool touched = false;
-    for (int vi = 0; vi < p.n_views && !touched; ++vi) {
-        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(vt.v[p.views[vi]].rec_base + g) * kGrad2D);
-#pragma unroll
-        for (int i = 0; i < kGrad2D / 2; ++i) {
-            const float2 v = __ldg(G2 + i);
-            touched |= v.x != 0.f || v.y != 0.f;
-        }
-    }
-    if (!touched) return;
     const float m[3] = {p.S.means[3 * g], p.S.means[3 * g + 1], p.S.means[3 * g + 2]};
     const float ls[3] = {p.S.log_scales[3 * g], p.S.log_scales[3 * g + 1], p.S.log_scales[3 * g + 2]};
     const float q[4] = {p.S.quats[4 * g], p.S.quats[4 * g + 1], p.S.quats[4 * g + 2], p.S.quats[4 * g + 3]};
@@ -450,9 +437,65 @@ __global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__
     for (int i = 0; i < 3 * K; ++i) gs_out[i] += gsh[i];
 }
 
+// Whether Gaussian g has a nonzero record gradient in some view of the scene.
+__device__ __forceinline__ bool touched_any(const ViewTable &vt, const ParamArgs &p, int g)
+{
+    bool touched = false;
+    for (int vi = 0; vi < p.n_views && !touched; ++vi) {
+        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(vt.v[p.views[vi]].rec_base + g) * kGrad2D);
+#pragma unroll
+        for (int i = 0; i < kGrad2D / 2; ++i) {
+            const float2 v = __ldg(G2 + i);
+            touched |= v.x != 0.f || v.y != 0.f;
+        }
+    }
+    return touched;
+}
+
+// Most Gaussians touch no pixel of any view: a light pass lists those that do
+// (one warp-aggregated atomic per warp), and the chain rule, heavy in registers,
+// then walks that list densely.
+__global__ void __launch_bounds__(256) k_touched(const __grid_constant__ ViewTable vt,
+                                                 const __grid_constant__ ParamArgs p)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (p.st->flags & ST_CAPACITY) return;
+    const bool t = g < p.S.n && touched_any(vt, p, g);
+    const uint32_t b = __ballot_sync(0xffffffffu, t);
+    if (b == 0u) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(p.list_count, (uint32_t)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (t) p.list[base + __popc(b & lanemask_lt())] = (uint32_t)g;
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__ ViewTable vt,
+                                                         const __grid_constant__ ParamArgs p)
+{
+    if (p.st->flags & ST_CAPACITY) return;
+    const uint32_t n = *p.list_count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        param_grads_one<K>(vt, p, (int)p.list[i]);
+}
+
+template <int K>
+static cudaError_t launch_params_k(const ViewTable &vt, const ParamArgs &p, int n_sms, cudaStream_t s)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_params<K>, 128, 0) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 2;
+    }
+    k_backward_params<K><<<(unsigned)(n_sms * per_sm), 128, 0, s>>>(vt, p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
-                                   const int8_t *views, int n_views, const float *grad2d,
-                                   const DevStatus *st, cudaStream_t s)
+                                   const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
+                                   uint32_t *list, int n_sms, cudaStream_t s)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     ParamArgs p;
@@ -462,15 +505,21 @@ cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const
     for (int i = 0; i < VRS_MAX_VIEWS; ++i) p.views[i] = i < n_views ? views[i] : 0;
     p.grad2d = grad2d;
     p.st = st;
-    const unsigned grid = grid_for(S.n, 128);
+    p.list = list;
+    p.list_count = &st->work[4];
+    cudaError_t e = cudaMemsetAsync(&st->work[4], 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_touched<<<grid_for(S.n, 256), 256, 0, s>>>(vt, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (n_sms <= 0) n_sms = 152;
     switch (S.K) {
-        case 1: k_backward_params<1><<<grid, 128, 0, s>>>(vt, p); break;
-        case 4: k_backward_params<4><<<grid, 128, 0, s>>>(vt, p); break;
-        case 9: k_backward_params<9><<<grid, 128, 0, s>>>(vt, p); break;
-        case 16: k_backward_params<16><<<grid, 128, 0, s>>>(vt, p); break;
+        case 1: return launch_params_k<1>(vt, p, n_sms, s);
+        case 4: return launch_params_k<4>(vt, p, n_sms, s);
+        case 9: return launch_params_k<9>(vt, p, n_sms, s);
+        case 16: return launch_params_k<16>(vt, p, n_sms, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace vrs
