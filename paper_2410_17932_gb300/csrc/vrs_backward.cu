@@ -77,6 +77,28 @@ __device__ __forceinline__ void pixel_adjoint(PixState &p, float q, float dx, fl
     }
 }
 
+constexpr int kGroup = 3;     // splats whose gradients are reduced together (3 x 10 rows <= 32 lanes)
+constexpr int kGStride = 36;  // row pitch in floats: lane-column writes and float4 row reads are conflict-free
+
+// Sums the 32 lanes' contributions of each (splat, value) of a group and adds
+// them to the splats' record gradients: lane p reduces row p.
+__device__ __forceinline__ void flush_group(float (*G)[kGStride], const uint32_t *R, int ng, int lane, float *grad2d)
+{
+    __syncwarp();
+    for (int p = lane; p < ng * kGrad2D; p += 32) {
+        const float4 *row = reinterpret_cast<const float4 *>(G[p]);
+        float4 acc = row[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            const float4 q = row[j];
+            acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
+        }
+        const int sp = p / kGrad2D, v = p - sp * kGrad2D;
+        atomicAdd(grad2d + (size_t)R[sp] * kGrad2D + v, (acc.x + acc.y) + (acc.z + acc.w));
+    }
+    __syncwarp();
+}
+
 template <int TS>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_bwd(const __grid_constant__ ViewTable vt, const BwdArgs a)
@@ -84,6 +106,10 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     using Cfg = BlendCfg<TS>;
     __shared__ float4 wA[Cfg::WARPS][32], wB[Cfg::WARPS][32], wC[Cfg::WARPS][32];
     __shared__ uint32_t wR[Cfg::WARPS][32];
+    // per-lane gradient contributions of up to kGroup splats, reduced together
+    __shared__ __align__(16) float wG[Cfg::WARPS][kGroup * kGrad2D][kGStride];
+    __shared__ uint32_t wGR[Cfg::WARPS][kGroup];
+    int ng = 0;
 
     if (a.st->flags & ST_CAPACITY) return;
     const unsigned FULL = 0xffffffffu;
@@ -177,28 +203,19 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float dx = Ak.x - pxc, dy = Ak.y - pyc;
             if (c0) pixel_adjoint(P0, q0, dx, dy, Ak, Bk, Ck, g);
             if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, Ak, Bk, Ck, g);
-            // reduce-scatter over the warp: at each level a lane keeps one half of its
-            // values and adds its partner's copy of that half, so the 10 (padded to 16)
-            // sums take 16 shuffles; value s ends in lanes 2s and 2s + 1
-            float r16[16];
+            // the lane's contributions go to the group buffer; the group is reduced
+            // when full: each lane sums whole 32-lane rows, one (splat, value) at a time
 #pragma unroll
-            for (int i = 0; i < 16; ++i) r16[i] = i < kGrad2D ? g[i] : 0.f;
-#pragma unroll
-            for (int c = 16, o = 16; c > 1; c >>= 1, o >>= 1) {
-                const bool upper = (lane & o) != 0;
-#pragma unroll
-                for (int i = 0; i < c / 2; ++i) {
-                    const float keep = upper ? r16[i + c / 2] : r16[i];
-                    const float send = upper ? r16[i] : r16[i + c / 2];
-                    r16[i] = keep + __shfl_xor_sync(FULL, send, o);
-                }
+            for (int i = 0; i < kGrad2D; ++i) wG[w][ng * kGrad2D + i][lane] = g[i];
+            if (lane == 0) wGR[w][ng] = wR[w][k];
+            if (++ng == kGroup) {
+                flush_group(wG[w], wGR[w], ng, lane, a.grad2d);
+                ng = 0;
             }
-            const float v = r16[0] + __shfl_xor_sync(FULL, r16[0], 1);
-            const int s = (lane >> 1) & 15;
-            if ((lane & 1) == 0 && s < kGrad2D) atomicAdd(a.grad2d + (size_t)wR[w][k] * kGrad2D + s, v);
         }
         __syncwarp();
     }
+    if (ng) flush_group(wG[w], wGR[w], ng, lane, a.grad2d);
 }
 
 template <int TS>
