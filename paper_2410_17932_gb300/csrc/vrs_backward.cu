@@ -304,12 +304,7 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
     const float *shg = p.S.sh + (size_t)g * 3 * K;
     GaussPre pre;
     if (!gauss_pre(ls, q, pre)) return;
-    float sh[3 * K];
-#pragma unroll
-    for (int i = 0; i < 3 * K; ++i) sh[i] = shg[i];
-    float gsh[3 * K];
-#pragma unroll
-    for (int i = 0; i < 3 * K; ++i) gsh[i] = 0.f;
+    float *gs_out = const_cast<float *>(p.G.sh) + (size_t)g * 3 * K;
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gqh[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
     const float o = 1.0f / (1.0f + expf(-logit));
     bool any = false;
@@ -338,24 +333,35 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
         const float v0_ = m[0] - cc0, v1_ = m[1] - cc1, v2_ = m[2] - cc2;
         const float vn = sqrtf(v0_ * v0_ + v1_ * v1_ + v2_ * v2_);
         const float dx = v0_ / vn, dy = v1_ / vn, dz = v2_ / vn;
-        float Y[16], Yx[16], Yy[16], Yz[16];
+        // (the SH row is streamed from L1 twice and the SH gradient is added to
+        // memory per view, so that neither row is held in registers)
+        float Y[16];
         sh_basis(dx, dy, dz, K, Y);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) col[ch] += Y[k] * __ldg(shg + 3 * k + ch);
+        // max(0, .) clamped channels pass no gradient
+        const float gc[3] = {col[0] < 0.f ? 0.f : G[6], col[1] < 0.f ? 0.f : G[7], col[2] < 0.f ? 0.f : G[8]};
+        float wY[16];                                 // dL/dY_k
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            wY[k] = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                wY[k] += gc[ch] * __ldg(shg + 3 * k + ch);
+                gs_out[3 * k + ch] += gc[ch] * Y[k];
+            }
+        }
+        float Yx[16], Yy[16], Yz[16];
         sh_basis_grad(dx, dy, dz, K, Yx, Yy, Yz);
         float gd0 = 0.f, gd1 = 0.f, gd2 = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc += Y[k] * sh[3 * k + ch];
-            if (acc < 0.f) continue;                 // max(0, .) clamped this channel
-            const float gc = G[6 + ch];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                gsh[3 * k + ch] += gc * Y[k];
-                gd0 += gc * sh[3 * k + ch] * Yx[k];
-                gd1 += gc * sh[3 * k + ch] * Yy[k];
-                gd2 += gc * sh[3 * k + ch] * Yz[k];
-            }
+        for (int k = 0; k < K; ++k) {
+            gd0 += wY[k] * Yx[k];
+            gd1 += wY[k] * Yy[k];
+            gd2 += wY[k] * Yz[k];
         }
         const float dd = dx * gd0 + dy * gd1 + dz * gd2;
         gm[0] += (gd0 - dx * dd) / vn;
@@ -437,7 +443,6 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
     if (!any) return;
     float *Gm = const_cast<float *>(p.G.means), *Gl = const_cast<float *>(p.G.log_scales);
     float *Gq = const_cast<float *>(p.G.quats), *Go = const_cast<float *>(p.G.logits);
-    float *Gs = const_cast<float *>(p.G.sh);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         Gm[3 * g + i] += gm[i];
@@ -449,24 +454,32 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
 #pragma unroll
     for (int i = 0; i < 4; ++i) Gq[4 * g + i] += (gqh[i] - qh[i] * dot) / qn;
     Go[g] += glogit;
-    float *gs_out = Gs + (size_t)g * 3 * K;
-#pragma unroll
-    for (int i = 0; i < 3 * K; ++i) gs_out[i] += gsh[i];
 }
 
-// Whether Gaussian g has a nonzero record gradient in some view of the scene.
-__device__ __forceinline__ bool touched_any(const ViewTable &vt, const ParamArgs &p, int g)
+// Whether the warp's Gaussian g0 + lane has a nonzero record gradient in some
+// view of the scene.  The 32 records of a view are 160 contiguous float2: the
+// warp reads them coalesced (five loads per lane), one ballot per load marks the
+// nonzero float2, and the lane takes the five bits of its own record.
+__device__ __forceinline__ bool touched_warp(const ViewTable &vt, const ParamArgs &p, int g0, int lane)
 {
-    bool touched = false;
-    for (int vi = 0; vi < p.n_views && !touched; ++vi) {
-        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(vt.v[p.views[vi]].rec_base + g) * kGrad2D);
+    static_assert(kGrad2D == 10, "five float2 per record");
+    const int n2 = min(32, p.S.n - g0) * 5;   // float2 of the warp's valid records
+    uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u, m4 = 0u;
+    for (int vi = 0; vi < p.n_views; ++vi) {
+        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(vt.v[p.views[vi]].rec_base + g0) * kGrad2D);
+        float2 v[5];
 #pragma unroll
-        for (int i = 0; i < kGrad2D / 2; ++i) {
-            const float2 v = __ldg(G2 + i);
-            touched |= v.x != 0.f || v.y != 0.f;
-        }
+        for (int i = 0; i < 5; ++i) v[i] = 32 * i + lane < n2 ? __ldg(G2 + 32 * i + lane) : make_float2(0.f, 0.f);
+        m0 |= __ballot_sync(0xffffffffu, v[0].x != 0.f || v[0].y != 0.f);
+        m1 |= __ballot_sync(0xffffffffu, v[1].x != 0.f || v[1].y != 0.f);
+        m2 |= __ballot_sync(0xffffffffu, v[2].x != 0.f || v[2].y != 0.f);
+        m3 |= __ballot_sync(0xffffffffu, v[3].x != 0.f || v[3].y != 0.f);
+        m4 |= __ballot_sync(0xffffffffu, v[4].x != 0.f || v[4].y != 0.f);
     }
-    return touched;
+    const int bit = 5 * lane, w = bit >> 5, off = bit & 31;
+    const uint32_t lo = w == 0 ? m0 : w == 1 ? m1 : w == 2 ? m2 : w == 3 ? m3 : m4;
+    const uint32_t hi = w == 0 ? m1 : w == 1 ? m2 : w == 2 ? m3 : w == 3 ? m4 : 0u;
+    return ((((uint64_t)hi << 32) | lo) >> off & 31u) != 0u;
 }
 
 // Most Gaussians touch no pixel of any view: a light pass lists those that do
@@ -475,10 +488,12 @@ __device__ __forceinline__ bool touched_any(const ViewTable &vt, const ParamArgs
 __global__ void __launch_bounds__(256) k_touched(const __grid_constant__ ViewTable vt,
                                                  const __grid_constant__ ParamArgs p)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) - lane;
     if (p.st->flags & ST_CAPACITY) return;
-    const bool t = g < p.S.n && touched_any(vt, p, g);
+    if (g0 >= p.S.n) return;   // uniform over the warp
+    const int g = g0 + lane;
+    const bool t = touched_warp(vt, p, g0, lane) && g < p.S.n;
     const uint32_t b = __ballot_sync(0xffffffffu, t);
     if (b == 0u) return;
     uint32_t base = 0;
