@@ -135,21 +135,47 @@ __device__ __forceinline__ void cmp_swap(unsigned long long &x, unsigned long lo
     y = asc ? hi : lo;
 }
 
-// Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i].
+// Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i],
+// in the form whose comparators all put the minimum at the lower element: each
+// merge of width k starts by comparing e with its mirror e ^ (k - 1), then
+// half-cleans with partners e ^ j.  No comparator needs a direction bit.
 // The per-element bodies are unrolled; the stage loops are not, which keeps the
 // four instantiations small enough for the instruction cache.
 template <int E>
-__device__ __forceinline__ void reg_stage(unsigned long long (&v)[E], int ji, int kk, int lane)
+__device__ __forceinline__ void shfl_stage(unsigned long long (&v)[E], int mask, int lowbit, int lane)
+{
+    const bool lower = (lane & lowbit) == 0;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], mask);
+        v[i] = (lower == (v[i] < o)) ? v[i] : o;
+    }
+}
+
+// Mirror step of a merge wider than a warp: partner register i ^ M, lane ^ 31.
+template <int E, int M>
+__device__ __forceinline__ void flip_regs(unsigned long long (&v)[E])
+{
+    if constexpr (M < E) {
+        unsigned long long o[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i ^ M], 31);
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = ((i < (i ^ M)) == (v[i] < o[i])) ? v[i] : o[i];
+    }
+}
+
+// Half-cleaner step across registers: partners i and i ^ JI in the same lane.
+template <int E, int JI>
+__device__ __forceinline__ void reg_half(unsigned long long (&v)[E])
 {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-        const int p = i ^ ji;
-        if (p > i) {
-            const bool asc = ((i * 32 + lane) & kk) == 0;
-            unsigned long long x = v[i], y = v[p];
-            cmp_swap(x, y, asc);
-            v[i] = x;
-            v[p] = y;
+        const int p = i ^ JI;
+        if (p > i && p < E) {
+            const unsigned long long x = v[i], y = v[p];
+            v[i] = x < y ? x : y;
+            v[p] = x < y ? y : x;
         }
     }
 }
@@ -160,23 +186,18 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lan
     constexpr int P = 32 * E;
 #pragma unroll 1
     for (int k = 2; k <= P; k <<= 1) {
+        if (k <= 32) shfl_stage<E>(v, k - 1, k >> 1, lane);
+        else if (k == 64) flip_regs<E, 1>(v);
+        else if (k == 128) flip_regs<E, 3>(v);
+        else flip_regs<E, 7>(v);
 #pragma unroll 1
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int j = k >> 2; j > 0; j >>= 1) {
             if (j >= 32) {
-                const int ji = j >> 5;
-                if (ji == 1) reg_stage<E>(v, 1, k, lane);
-                else if (E > 2 && ji == 2) reg_stage<E>(v, 2, k, lane);
-                else if (E > 4) reg_stage<E>(v, 4, k, lane);
+                if (j == 32) reg_half<E, 1>(v);
+                else if (j == 64) reg_half<E, 2>(v);
+                else reg_half<E, 4>(v);
             } else {
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const int e = i * 32 + lane;
-                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], j);
-                    const bool asc = (e & k) == 0, lower = (lane & j) == 0;
-                    const bool take_min = lower == asc;
-                    const bool less = v[i] < o;
-                    v[i] = (take_min == less) ? v[i] : o;
-                }
+                shfl_stage<E>(v, j, j, lane);
             }
         }
     }
