@@ -5,11 +5,12 @@
 //   k_tile_blocksum, k_tile_scan   exclusive scan of the counts -> tile ranges
 //   k_tile_scatter                 each instance into its tile's bucket as the
 //                                  composite (depth bits << 32 | record index)
-//   k_tile_sort_small              one warp per tile of <= 256 instances: a
-//                                  bitonic network in registers and shuffles
-//   k_tile_sort_big                larger tiles, one CTA each: a bitonic network
-//                                  in shared memory up to 4096, beyond that
-//                                  sorted 4096-runs merged in global memory
+//   k_tile_sort                    one launch for both sizes: one warp per tile
+//                                  of <= 256 instances (a bitonic network in
+//                                  registers and shuffles), and larger tiles one
+//                                  CTA each (a bitonic network in shared memory
+//                                  up to 4096, beyond that sorted 4096-runs
+//                                  merged in global memory)
 // Sorting the composite orders equal depths by record index, so the result is
 // the unique (tile, depth, record) order and matches the radix path bit for bit.
 #include "vrs_internal.cuh"
@@ -225,14 +226,12 @@ __device__ __forceinline__ void warp_sort_tile(const TileSortArgs &a, uint32_t t
     }
 }
 
-__global__ void __launch_bounds__(128) k_tile_sort_small(const TileSortArgs a)
+// One warp sorts tile t if it holds 1..256 instances (larger tiles go to the CTA path).
+__device__ __forceinline__ void sort_small_tile(const TileSortArgs &a, int64_t t, int lane)
 {
-    if (live_instances(a.st, a.cap) == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
     if (t >= a.n_tiles) return;
     const uint32_t n = a.cnt[t];
-    if (n == 0 || n > (uint32_t)kSmallMax) return;   // empty, or sorted by k_tile_sort_big
+    if (n == 0 || n > (uint32_t)kSmallMax) return;
     const uint32_t start = a.ranges[t].x;
     if (n <= 32) warp_sort_tile<1>(a, (uint32_t)t, start, n, lane);
     else if (n <= 64) warp_sort_tile<2>(a, (uint32_t)t, start, n, lane);
@@ -280,11 +279,10 @@ __device__ void block_merge(const unsigned long long *src, uint32_t la, uint32_t
     }
 }
 
-__global__ void __launch_bounds__(kBigThreads) k_tile_sort_big(const TileSortArgs a)
+// One CTA pulls tiles of more than 256 instances from the big-tile list until it
+// is empty: sorted runs of kBigChunk in shared memory, merged in global memory.
+__device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned long long *s, uint32_t &s_idx)
 {
-    __shared__ unsigned long long s[kBigChunk];
-    __shared__ uint32_t s_idx;
-    if (live_instances(a.st, a.cap) == 0) return;
     const uint32_t n_big = a.st->work[1];
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[2], 1u);
@@ -333,6 +331,22 @@ __global__ void __launch_bounds__(kBigThreads) k_tile_sort_big(const TileSortArg
     }
 }
 
+// Both sorts in one launch, so that the few long big-tile CTAs overlap the many
+// short warp sorts: CTAs below n_big work through the big-tile list, the others
+// give each of their warps one tile.
+__global__ void __launch_bounds__(kBigThreads, 4) k_tile_sort(const TileSortArgs a, unsigned n_big)
+{
+    __shared__ unsigned long long s[kBigChunk];
+    __shared__ uint32_t s_idx;
+    if (live_instances(a.st, a.cap) == 0) return;
+    if (blockIdx.x < n_big) {
+        sort_big_tiles(a, s, s_idx);
+        return;
+    }
+    const int64_t t = (int64_t)(blockIdx.x - n_big) * (kBigThreads / 32) + (threadIdx.x >> 5);
+    sort_small_tile(a, t, threadIdx.x & 31);
+}
+
 cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *vals_in,
                              unsigned long long *bucket, unsigned long long *keys_out, uint32_t *vals_out,
                              const uint32_t *cnt, uint32_t *cursor, uint32_t *blocksum, uint32_t *big_list,
@@ -348,8 +362,9 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
     k_tile_blocksum<<<nb, kScanBlock, 0, s>>>(a);
     k_tile_scan<<<nb, kScanBlock, 0, s>>>(a);
     k_tile_scatter<<<n_sms * 8, 256, 0, s>>>(a);
-    k_tile_sort_small<<<(unsigned)((n_tiles + 3) / 4), 128, 0, s>>>(a);
-    k_tile_sort_big<<<n_sms * 2, kBigThreads, 0, s>>>(a);
+    const unsigned n_big = (unsigned)n_sms * 2u;
+    const int64_t per = kBigThreads / 32;
+    k_tile_sort<<<(unsigned)(n_big + (n_tiles + per - 1) / per), kBigThreads, 0, s>>>(a, n_big);
     return cudaGetLastError();
 }
 
