@@ -138,7 +138,9 @@ typedef struct {
     int64_t off_vals[2];       /* [max_instances] uint32 ping-pong record-index buffers */
     int64_t off_hist;          /* radix scratch */
     int64_t off_ranges;        /* [n_tiles] uint2 {start, end} into the sorted list; {0, 0} if empty */
-    int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1 */
+    int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1, written by
+                                  vrs_render_fwd for plans made with backward = 1 (the
+                                  reverse pass starts there); untouched otherwise */
     int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
     int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */
     int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] list of
@@ -223,7 +225,9 @@ vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
  *   rgb     [3][H][W] per view, view v at rgb + 3 * plan.view_pix_base[v]
  *   depth   [H][W] per view at depth + plan.view_pix_base[v]   (Eq. 1, not normalised)
  *   T_final [H][W] per view at T_final + plan.view_pix_base[v]
- * Colour is premultiplied with no background; composite with T_final. */
+ * Colour is premultiplied with no background; composite with T_final.
+ * For a plan made with backward = 1 it also writes each pixel's last blended
+ * list position at workspace + plan.off_ncontrib, where vrs_render_bwd starts. */
 vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, float *depth,
                           float *T_final, void *stream);
 

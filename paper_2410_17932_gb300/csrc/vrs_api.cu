@@ -297,7 +297,8 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         vt, at<float4>(workspace, plan->off_status + 256), at<float4>(workspace, plan->off_records),
         at<uint32_t>(workspace, plan->off_vals[sb]), at<uint2>(workspace, plan->off_ranges),
         at<DevStatus>(workspace, plan->off_status), rgb, depth, T_final,
-        at<uint32_t>(workspace, plan->off_ncontrib), order, order + plan->n_tiles, plan->n_tiles,
+        plan->backward ? at<uint32_t>(workspace, plan->off_ncontrib) : nullptr,   // only the reverse pass reads it
+        order, order + plan->n_tiles, plan->n_tiles,
         plan->n_records, (unsigned long long)plan->max_instances, plan->persistent, plan->count_pairs,
         plan->n_sms, static_cast<cudaStream_t>(stream));
     return cuda_status(e);

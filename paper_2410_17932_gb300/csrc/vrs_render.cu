@@ -49,9 +49,11 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // One splat at a thread's two pixels, front to back: skip below 1/255, stop
 // before T would drop under 1e-4, otherwise blend.  Written as selects (no
 // branches).  q holds the two pixels' quadratic forms; B = (l2, lo, lt,
-// depth), C = (r, g, b, list position).  COUNT also tracks the stop position
-// and the blend count for the work counters.
-template <bool COUNT>
+// depth), C = (r, g, b, list position).  LAST tracks each pixel's last
+// blended position, the reverse pass's starting point (plans made for the
+// backward); COUNT also tracks the stop position and the blend count for the
+// work counters.
+template <bool COUNT, bool LAST>
 __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &B, const float4 &C,
                                             uint32_t &n_blend)
 {
@@ -71,8 +73,10 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &
     P.D = __ffma2_rn(f2(B.w), wt, P.D);
     P.T = __fmul2_rn(P.T, __ffma2_rn(a, f2(-1.f), f2(1.f)));
     const uint32_t pos = (uint32_t)__float_as_int(C.w);
-    P.last0 = b0 ? pos : P.last0;
-    P.last1 = b1 ? pos : P.last1;
+    if (LAST) {
+        P.last0 = b0 ? pos : P.last0;
+        P.last1 = b1 ? pos : P.last1;
+    }
     P.done0 = P.done0 || s0;
     P.done1 = P.done1 || s1;
     if (COUNT) {
@@ -94,7 +98,7 @@ __device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc,
     return __ffma2_rn(t, t, f2(s2));
 }
 
-template <int TS, bool COUNT>
+template <int TS, bool COUNT, bool LAST>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCKS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
@@ -192,13 +196,13 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                     const float4 A1 = sR[j1][0], B1 = sR[j1][1], C1 = sR[j1][2];
                     const float2 q0 = pair_q2v(A0, B0.x, pxc, pyc);
                     const float2 q1 = pair_q2v(A1, B1.x, pxc, pyc);
-                    pix_update2<COUNT>(P, q0, B0, C0, n_blend);
-                    pix_update2<COUNT>(P, q1, B1, C1, n_blend);
+                    pix_update2<COUNT, LAST>(P, q0, B0, C0, n_blend);
+                    pix_update2<COUNT, LAST>(P, q1, B1, C1, n_blend);
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sR[j0][0], B0 = sR[j0][1], C0 = sR[j0][2];
-                    pix_update2<COUNT>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
+                    pix_update2<COUNT, LAST>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
                 }
             }
         }
@@ -217,14 +221,14 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
             *reinterpret_cast<float2 *>(rgb + 2 * HW + lp) = P.B;
             *reinterpret_cast<float2 *>(a.depth + pix) = P.D;
             *reinterpret_cast<float2 *>(a.Tf + pix) = P.T;
-            *reinterpret_cast<uint2 *>(a.ncontrib + pix) = make_uint2(P.last0, P.last1);
+            if (LAST) *reinterpret_cast<uint2 *>(a.ncontrib + pix) = make_uint2(P.last0, P.last1);
         } else if (in0) {
             rgb[lp] = P.R.x;
             rgb[HW + lp] = P.G.x;
             rgb[2 * HW + lp] = P.B.x;
             a.depth[pix] = P.D.x;
             a.Tf[pix] = P.T.x;
-            a.ncontrib[pix] = P.last0;
+            if (LAST) a.ncontrib[pix] = P.last0;
         }
         if (in1 && !pair) {
             rgb[lp + 1] = P.R.y;
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
             rgb[2 * HW + lp + 1] = P.B.y;
             a.depth[pix + 1] = P.D.y;
             a.Tf[pix + 1] = P.T.y;
-            a.ncontrib[pix + 1] = P.last1;
+            if (LAST) a.ncontrib[pix + 1] = P.last1;
         }
     }
     if (!COUNT) return;
@@ -292,8 +296,11 @@ __global__ void k_order_scatter(const uint2 *ranges, int64_t n_tiles, const uint
 template <int TS>
 static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
-    if (count) k_render_fwd<TS, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
-    else k_render_fwd<TS, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    // the last-blended-position plane is written only when the caller keeps it
+    if (count && a.ncontrib) k_render_fwd<TS, true, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    else if (count) k_render_fwd<TS, true, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    else if (a.ncontrib) k_render_fwd<TS, false, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    else k_render_fwd<TS, false, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
     return cudaGetLastError();
 }
 

@@ -225,6 +225,7 @@ class Rasterizer:
         return self.ws_view(int(p.off_records), 12 * int(p.n_records), torch.float32).view(-1, 12)
 
     def n_contrib(self) -> torch.Tensor:
+        """Each pixel's last blended list position + 1 (written for backward plans only)."""
         p = self.plan
         return self.ws_view(int(p.off_ncontrib), int(p.n_pixels), torch.int32)
 

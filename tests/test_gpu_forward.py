@@ -57,15 +57,18 @@ def test_plain_200_records_and_sort():
     assert np.abs(rec["rgb"][vis] - p["rgb"][vis]).max() < 2e-6
 
 
-def test_plain_200_image_parity():
+@pytest.mark.parametrize("backward", [False, True])
+def test_plain_200_image_parity(backward):
+    # a forward-only plan skips the last-position plane; a backward plan writes it
     scs, cams = I.plain_200()
-    ras = _run(scs, cams)
+    ras = _run(scs, cams, backward=backward)
     rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
     orc = oracle.render(scs[0], cams[0])
     worst = compare_images((rgb, depth, T), orc, "plain_200")
-    nc = ras.n_contrib().cpu().numpy().reshape(200, 200)
-    ok = orc["flags"] == 0
-    assert np.array_equal(nc[ok], orc["n_contrib"][ok])
+    if backward:
+        nc = ras.n_contrib().cpu().numpy().reshape(200, 200)
+        ok = orc["flags"] == 0
+        assert np.array_equal(nc[ok], orc["n_contrib"][ok])
     print("plain_200 worst", worst)
 
 
