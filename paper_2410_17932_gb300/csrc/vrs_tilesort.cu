@@ -2,7 +2,9 @@
 // by tile and each tile's bucket is sorted on its own (Sec. 1: tiling and
 // sorting all primitives).  vrs_preprocess already counted every tile's
 // instances while emitting them; here
-//   k_tile_blocksum, k_tile_scan   exclusive scan of the counts -> tile ranges
+//   k_tile_blocksum, k_tile_scan   exclusive scan of the counts -> tile ranges (up
+//                                  to 64 Ki tiles, k_tile_scan alone: each CTA
+//                                  sums the counts before its block itself)
 //   k_tile_scatter                 each instance into its tile's bucket as the
 //                                  composite (depth bits << 32 | record index)
 //   k_tile_sort                    one launch for both sizes: one warp per tile
@@ -70,15 +72,30 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_blocksum(const TileSortArgs
     if (threadIdx.x == 0) a.blocksum[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a)
+// direct = 1: each CTA sums the counts of all tiles before its block itself (one
+// launch; for grids of up to kDirectBlocks blocks), else it sums the block sums
+// k_tile_blocksum wrote.
+constexpr unsigned kDirectBlocks = 64;
+
+__global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, int direct)
 {
     __shared__ uint32_t sh[32];
     __shared__ uint32_t base_s;
     if (a.st->flags & ST_CAPACITY) return;    // every tile range is written, even with no instances
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // prefix of the block sums of the blocks before this one
+    // prefix of the counts of the blocks before this one
     uint32_t p = 0;
-    for (uint32_t b = threadIdx.x; b < blockIdx.x; b += kScanBlock) p += a.blocksum[b];
+    if (!direct) {
+        for (uint32_t b = threadIdx.x; b < blockIdx.x; b += kScanBlock) p += a.blocksum[b];
+    } else if ((reinterpret_cast<uintptr_t>(a.cnt) & 15u) == 0) {
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(a.cnt);
+        for (uint32_t i = threadIdx.x; i < blockIdx.x * (kScanBlock / 4); i += kScanBlock) {
+            const uint4 v = c4[i];
+            p += (v.x + v.y) + (v.z + v.w);
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < blockIdx.x * kScanBlock; i += kScanBlock) p += a.cnt[i];
+    }
     p = block_sum1024(p, sh);
     if (threadIdx.x == 0) base_s = p;
     __syncthreads();
@@ -359,8 +376,9 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
     cudaError_t e = cudaMemsetAsync(&st->work[1], 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((n_tiles + kScanBlock - 1) / kScanBlock);
-    k_tile_blocksum<<<nb, kScanBlock, 0, s>>>(a);
-    k_tile_scan<<<nb, kScanBlock, 0, s>>>(a);
+    const int direct = nb <= kDirectBlocks ? 1 : 0;
+    if (!direct) k_tile_blocksum<<<nb, kScanBlock, 0, s>>>(a);
+    k_tile_scan<<<nb, kScanBlock, 0, s>>>(a, direct);
     k_tile_scatter<<<n_sms * 8, 256, 0, s>>>(a);
     const unsigned n_big = (unsigned)n_sms * 2u;
     const int64_t per = kBigThreads / 32;

@@ -76,6 +76,22 @@ def test_periphery_stereo_05m_full_size():
     print("periphery_stereo_05m worst", worst)
 
 
+def test_periphery_stereo_05m_tile8_sort():
+    # 2 x 252 x 280 tiles: more than 64 Ki, so the tile-count scan takes its
+    # two-launch form (block sums, then the scan); tile 16 takes the one-launch form
+    torch = torch_cuda()
+    scenes, views = I.periphery_stereo_05m()
+    ras, _ = make_rasterizer(scenes, views, tile=8)
+    ras.forward()
+    torch.cuda.synchronize()
+    assert int(ras.plan.n_tiles) > 65536
+    keys, vals, ranges = ras.sorted_lists()
+    bs = oracle.bin_sort(scenes, views, 8)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), bs["keys"])
+    assert np.array_equal(vals.cpu().numpy().view(np.uint32), bs["vals"])
+    assert np.array_equal(ranges.cpu().numpy().astype(np.int64), bs["ranges"])
+
+
 def test_periphery_stereo_05m_persistent_identical():
     torch = torch_cuda()
     scenes, views = I.periphery_stereo_05m(n=200_000)
