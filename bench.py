@@ -635,13 +635,13 @@ def main():
     if rank == 0 and not args.no_extras:
         extra = run_extras(args)
 
-    # viewtab + (decide, pairs) per scene; the sort's kernels; the blend (+ the order kernels)
+    # (decide, pairs) per scene; the sort's kernels; the blend (+ the order kernels)
     if p.sort_mode == 0:
         # scan (+ block sums beyond 64 Ki tiles), scatter, tile sort
         sort_launches = 3 + (1 if (int(p.n_tiles) + 1023) // 1024 > 64 else 0)
-        launches_per_step = (1 + 2 * len(scenes)) + sort_launches + (3 if p.persistent else 1)
+        launches_per_step = 2 * len(scenes) + sort_launches + (3 if p.persistent else 1)
     else:
-        launches_per_step = (1 + 2 * len(scenes)) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
+        launches_per_step = 2 * len(scenes) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
     if rank == 0:
         line = {
             "metric": METRIC,

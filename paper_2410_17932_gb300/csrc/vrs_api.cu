@@ -7,8 +7,7 @@ namespace vrs {
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              int n_sms, cudaStream_t stream);
-cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream);
+                              float4 *viewtab, int n_sms, cudaStream_t stream);
 cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
                         uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
                         int64_t n_tiles, const DevStatus *st, unsigned long long cap, int passes, int G,
@@ -234,8 +233,6 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
     float4 *viewtab = at<float4>(workspace, plan->off_status + 256);
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
-    e = launch_write_viewtab(vt, viewtab, s);
-    if (e != cudaSuccess) return VRS_ERR_CUDA;
     uint32_t *tile_cnt = nullptr;
     if (plan->sort_mode == 0) {
         tile_cnt = at<uint32_t>(workspace, plan->off_tilesort);
@@ -251,7 +248,7 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
                               at<float4>(workspace, plan->off_records),
                               at<unsigned long long>(workspace, plan->off_keys[0]),
                               at<uint32_t>(workspace, plan->off_vals[0]), tile_cnt, st,
-                              (unsigned long long)plan->max_instances, plan->n_sms, s);
+                              (unsigned long long)plan->max_instances, viewtab, plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
         pair_base += (int64_t)plan->scene_n[sc] * nv;
     }

@@ -21,6 +21,7 @@ struct PreParams {
     uint32_t *tile_cnt;              // nullable: instances per tile (bucketed sort)
     DevStatus *st;
     unsigned long long cap;
+    float4 *viewtab;                 // [VRS_MAX_VIEWS] principal points, written by k_decide's first CTA
 };
 
 // The step runs as two kernels per scene.
@@ -45,6 +46,11 @@ constexpr int kPairThreads = 128;
 __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant__ ViewTable vt,
                                                            const __grid_constant__ PreParams p)
 {
+    // the views' principal points, read by the blend kernels to build each
+    // tile's local frame (the plan holds sizes only); every scene's launch
+    // writes the same values
+    if (blockIdx.x == 0 && threadIdx.x < vt.n_views)
+        p.viewtab[threadIdx.x] = make_float4(vt.v[threadIdx.x].cx, vt.v[threadIdx.x].cy, 0.f, 0.f);
     const unsigned FULL = 0xffffffffu;
     const int g = blockIdx.x * kDecideThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -277,26 +283,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
     if (nonfinite_sh) atomicOr(&p.st->flags, ST_NONFINITE);
 }
 
-// Principal points of the views, read by the blend kernels to build each
-// tile's local frame (the plan holds sizes only).
-__global__ void k_write_viewtab(const __grid_constant__ ViewTable vt, float4 *viewtab)
-{
-    const int v = threadIdx.x;
-    if (v < vt.n_views) viewtab[v] = make_float4(vt.v[v].cx, vt.v[v].cy, 0.f, 0.f);
-}
-
-cudaError_t launch_write_viewtab(const ViewTable &vt, float4 *viewtab, cudaStream_t stream)
-{
-    k_write_viewtab<<<1, VRS_MAX_VIEWS, 0, stream>>>(vt, viewtab);
-    return cudaGetLastError();
-}
-
 // Host launcher: two launches per scene (the SH degree is a template argument
 // of the pair kernel so that a row's coefficients stay in registers).
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              int n_sms, cudaStream_t stream)
+                              float4 *viewtab, int n_sms, cudaStream_t stream)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     PreParams p;
@@ -312,6 +304,7 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     p.tile_cnt = tile_cnt;
     p.st = st;
     p.cap = cap;
+    p.viewtab = viewtab;
     k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
