@@ -7,7 +7,7 @@ namespace vrs {
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              float4 *viewtab, int n_sms, cudaStream_t stream);
+                              float4 *viewtab, int64_t zero_tiles, int n_sms, cudaStream_t stream);
 cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
                         uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
                         int64_t n_tiles, const DevStatus *st, unsigned long long cap, int passes, int G,
@@ -233,11 +233,22 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
     float4 *viewtab = at<float4>(workspace, plan->off_status + 256);
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
+    // the per-tile counts of the bucketed sort are cleared by the first scene's
+    // decision kernel (before any pair kernel counts into them), or here when no
+    // scene has Gaussians
     uint32_t *tile_cnt = nullptr;
+    int first = -1;
     if (plan->sort_mode == 0) {
         tile_cnt = at<uint32_t>(workspace, plan->off_tilesort);
-        e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)plan->n_tiles, s);
-        if (e != cudaSuccess) return VRS_ERR_CUDA;
+        for (int sc = 0; sc < plan->n_scenes && first < 0; ++sc)
+            if (plan->scene_n[sc] > 0) {
+                int8_t vl[VRS_MAX_VIEWS];
+                if (views_of_scene(plan, sc, vl) > 0) first = sc;
+            }
+        if (first < 0) {
+            e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)plan->n_tiles, s);
+            if (e != cudaSuccess) return VRS_ERR_CUDA;
+        }
     }
     int64_t pair_base = 0;
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
@@ -248,7 +259,8 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
                               at<float4>(workspace, plan->off_records),
                               at<unsigned long long>(workspace, plan->off_keys[0]),
                               at<uint32_t>(workspace, plan->off_vals[0]), tile_cnt, st,
-                              (unsigned long long)plan->max_instances, viewtab, plan->n_sms, s);
+                              (unsigned long long)plan->max_instances, viewtab,
+                              sc == first ? plan->n_tiles : 0, plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
         pair_base += (int64_t)plan->scene_n[sc] * nv;
     }

@@ -22,6 +22,8 @@ struct PreParams {
     DevStatus *st;
     unsigned long long cap;
     float4 *viewtab;                 // [VRS_MAX_VIEWS] principal points, written by k_decide's first CTA
+    int64_t zero_tiles;              // > 0: k_decide clears tile_cnt[0, zero_tiles) (the frame's first
+                                     // scene, before any pair kernel counts into it)
 };
 
 // The step runs as two kernels per scene.
@@ -51,6 +53,9 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
     // writes the same values
     if (blockIdx.x == 0 && threadIdx.x < vt.n_views)
         p.viewtab[threadIdx.x] = make_float4(vt.v[threadIdx.x].cx, vt.v[threadIdx.x].cy, 0.f, 0.f);
+    for (int64_t t = (int64_t)blockIdx.x * kDecideThreads + threadIdx.x; t < p.zero_tiles;
+         t += (int64_t)gridDim.x * kDecideThreads)
+        p.tile_cnt[t] = 0u;
     const unsigned FULL = 0xffffffffu;
     const int g = blockIdx.x * kDecideThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              float4 *viewtab, int n_sms, cudaStream_t stream)
+                              float4 *viewtab, int64_t zero_tiles, int n_sms, cudaStream_t stream)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     PreParams p;
@@ -305,6 +310,7 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     p.st = st;
     p.cap = cap;
     p.viewtab = viewtab;
+    p.zero_tiles = tile_cnt ? zero_tiles : 0;
     k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
