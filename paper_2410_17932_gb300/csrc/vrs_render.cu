@@ -167,11 +167,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                 load_record(a.rec, rid, r0, r1, r2);
                 stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
                 C.w = __int_as_float((int)(j - range.x + 1));
-                const CullSplat cs = cull_setup(A.x, A.y, A.z, A.w, B.x, B.z);
-#pragma unroll
-                for (int ww = 0; ww < Cfg::WARPS; ++ww)
-                    if (cull_block(cs, (float)((ww % Cfg::WGX) * 8) + 0.5f, (float)((ww / Cfg::WGX) * 8) + 0.5f))
-                        mask |= 1u << ww;
+                mask = cull_blocks<Cfg::WGX, Cfg::WARPS / Cfg::WGX>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z));
                 sR[tid][0] = A;
                 sR[tid][1] = B;
                 sR[tid][2] = C;
