@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             float4 r0, r1, r2;
             load_record(a.rec, rid, r0, r1, r2);
             stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
-            hit = cull_block(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z), (float)bx + 0.5f, (float)by + 0.5f);
+            hit = cull_blocks<1, 1>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z), (float)bx + 0.5f, (float)by + 0.5f) != 0u;
         }
         const uint32_t bal = __ballot_sync(FULL, hit);
         if (hit) {

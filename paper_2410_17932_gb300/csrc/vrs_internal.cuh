@@ -513,34 +513,13 @@ __device__ __forceinline__ CullSplat cull_setup(float su, float sv, float l0, fl
     return c;
 }
 
-// Block of pixel centres [x0, x0 + 7] x [y0, y0 + 7] (tile-local).
-__device__ __forceinline__ bool cull_block(const CullSplat &c, float x0, float y0)
-{
-    if (c.thr <= 0.f) return false;
-    if (fabsf(c.su - (x0 + 3.5f)) > c.hx || fabsf(c.sv - (y0 + 3.5f)) > c.hy) return false;
-    const float u0 = c.su - (x0 + 7.0f), u1 = c.su - x0, v0 = c.sv - (y0 + 7.0f), v1 = c.sv - y0;
-    if (u0 <= 0.f && u1 >= 0.f && v0 <= 0.f && v1 >= 0.f) return true;
-    float best = 3.0e38f;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float v = e ? v1 : v0;                       // horizontal edges
-        const float u = fminf(fmaxf(-c.l1 * v * c.il0, u0), u1);
-        const float t = fmaf(c.l0, u, c.l1 * v), sy = c.l2 * v;
-        best = fminf(best, fmaf(t, t, sy * sy));
-        const float uu = e ? u1 : u0;                      // vertical edges
-        const float vv = fminf(fmaxf(-c.l0 * c.l1 * uu * c.ic, v0), v1);
-        const float t2 = fmaf(c.l0, uu, c.l1 * vv), sy2 = c.l2 * vv;
-        best = fminf(best, fmaf(t2, t2, sy2 * sy2));
-    }
-    return best <= c.thr;
-}
-
-// All WGX x WGY blocks of a tile at once (the forward's staging): the tests of
-// cull_block without branches, the minimiser along each edge line computed once
-// for the blocks that share the line.  Bit w of the result is block
-// (w % WGX, w / WGX), i.e. warp w.
+// WGX x WGY adjacent 8x8 blocks at once, the first one's pixel centres
+// [x0, x0 + 7] x [y0, y0 + 7] (tile-local).  A block is kept when it passes the
+// bounding-box screen and holds the minimiser or has an edge minimum within thr.
+// Branch-free; the minimiser along each edge line is computed once for the
+// blocks that share the line.  Bit w of the result is block (w % WGX, w / WGX).
 template <int WGX, int WGY>
-__device__ __forceinline__ uint32_t cull_blocks(const CullSplat &c)
+__device__ __forceinline__ uint32_t cull_blocks(const CullSplat &c, float x0 = 0.5f, float y0 = 0.5f)
 {
     const float ku = -c.l1 * c.il0;           // on a horizontal line v: u = ku v minimises q'
     const float kv = -c.l0 * c.l1 * c.ic;     // on a vertical line u: v = kv u
@@ -548,14 +527,14 @@ __device__ __forceinline__ uint32_t cull_blocks(const CullSplat &c)
     bool inx[WGX], iny[WGY], bbx[WGX], bby[WGY];
 #pragma unroll
     for (int b = 0; b < WGX; ++b) {
-        u1[b] = c.su - (8.0f * b + 0.5f);
+        u1[b] = c.su - (x0 + 8.0f * b);
         u0[b] = u1[b] - 7.0f;
         inx[b] = u0[b] <= 0.f && u1[b] >= 0.f;
         bbx[b] = fabsf(u1[b] - 3.5f) <= c.hx;
     }
 #pragma unroll
     for (int b = 0; b < WGY; ++b) {
-        v1[b] = c.sv - (8.0f * b + 0.5f);
+        v1[b] = c.sv - (y0 + 8.0f * b);
         v0[b] = v1[b] - 7.0f;
         iny[b] = v0[b] <= 0.f && v1[b] >= 0.f;
         bby[b] = fabsf(v1[b] - 3.5f) <= c.hy;
