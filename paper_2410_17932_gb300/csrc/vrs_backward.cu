@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const DevView &V = vt.v[vi];
     const float4 pp = a.viewtab[vi];
     const int64_t lt_ = t - V.tile_base;
-    const int tx = (int)(lt_ % V.gw), ty = (int)(lt_ / V.gw);
+    int tx, ty;
+    tile_xy(lt_, V.gw, tx, ty);
     const int px = tx * TS + bx + 2 * (lane & 3), py = ty * TS + by + (lane >> 2);
     const bool in0 = px < V.w && py < V.h, in1 = px + 1 < V.w && py < V.h;
     float oxh, oxl, oyh, oyl;

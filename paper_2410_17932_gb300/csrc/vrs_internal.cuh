@@ -86,6 +86,30 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return y;
 }
 
+// Column and row of tile lt in a view gw tiles wide.  Below 2^22 tiles: a
+// reciprocal estimate (relative error below 2^-21, so the quotient is off by
+// at most one for gw >= 2; exact for gw = 1) and one correction step, instead
+// of a 64-bit division.
+__device__ __forceinline__ void tile_xy(int64_t lt, int gw, int &tx, int &ty)
+{
+    if (lt < ((int64_t)1 << 22)) {
+        int q = (int)((float)(int)lt * rcp_approx((float)gw));
+        int r = (int)lt - q * gw;
+        if (r < 0) {
+            --q;
+            r += gw;
+        } else if (r >= gw) {
+            ++q;
+            r -= gw;
+        }
+        tx = r;
+        ty = q;
+    } else {
+        tx = (int)(lt % gw);
+        ty = (int)(lt / gw);
+    }
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
