@@ -98,7 +98,7 @@ __device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc,
     return __ffma2_rn(t, t, f2(s2));
 }
 
-template <int TS, bool COUNT, bool LAST>
+template <int TS, bool COUNT, bool LAST, bool PERSIST>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCKS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
 
     for (int64_t iter = 0; !skip_all; ++iter) {
         int64_t t;
-        if (a.persistent) {
+        if (PERSIST) {
             if (tid == 0) {
                 const uint32_t k = atomicAdd(&a.st->work[0], 1u);
                 s_tile = (int64_t)k < a.n_tiles ? (int64_t)a.order[k] : -1;
@@ -290,14 +290,24 @@ __global__ void k_order_scatter(const uint2 *ranges, int64_t n_tiles, const uint
     }
 }
 
+template <int TS, bool PERSIST>
+static void launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
+{
+    // the last-blended-position plane is written only when the caller keeps it
+    constexpr int T = BlendCfg<TS>::THREADS;
+    if (count && a.ncontrib) k_render_fwd<TS, true, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
+    else if (count) k_render_fwd<TS, true, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
+    else if (a.ncontrib) k_render_fwd<TS, false, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
+    else k_render_fwd<TS, false, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
+}
+
+// The persistent schedule is a separate instantiation, so that the per-tile
+// grid carries none of its work-queue code.
 template <int TS>
 static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
-    // the last-blended-position plane is written only when the caller keeps it
-    if (count && a.ncontrib) k_render_fwd<TS, true, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
-    else if (count) k_render_fwd<TS, true, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
-    else if (a.ncontrib) k_render_fwd<TS, false, true><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
-    else k_render_fwd<TS, false, false><<<grid, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
+    if (a.persistent) launch_fwd_tsp<TS, true>(vt, a, grid, count, s);
+    else launch_fwd_tsp<TS, false>(vt, a, grid, count, s);
     return cudaGetLastError();
 }
 
