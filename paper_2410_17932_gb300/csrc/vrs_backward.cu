@@ -38,43 +38,61 @@ struct BwdArgs {
 
 constexpr float kInvChol2 = 1.0f / (kCholScale * kCholScale);   // 2 / log2(e)
 
-struct PixState {
-    float T, SC0, SC1, SC2, SD, gC0, gC1, gC2, gD, gT, Tfin;
-    uint32_t last;
+// A lane's two pixels (x and x + 1 of one row) as packed pairs.
+struct PixState2 {
+    float2 T, SC0, SC1, SC2, SD, gC0, gC1, gC2, gD, gT, Tfin;
+    uint32_t last0, last1;
 };
 
-// One pixel's contribution to the 10 record gradients of a blended splat.
-__device__ __forceinline__ void pixel_adjoint(PixState &p, float q, float dx, float dy, const float4 A,
-                                              const float4 B, const float4 C, float *g)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// The two pixels' contributions to the 10 record gradients of a splat, as FP32x2
+// pairs (each component rounded as the scalar operation).  A pixel the splat does
+// not reach (c false) contributes zero and keeps its state: its weight and
+// dL/dalpha are multiplied by 0, its T is selected.  g[i].x + g[i].y is the
+// lane's value i.
+__device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 q, bool c0, bool c1, float2 dx, float dy,
+                                               const float4 A, const float4 B, const float4 C, float2 *g)
 {
-    const float e = ex2_approx(__fsub_rn(B.y, q));
-    const float al = fminf(e, 0.99f);
-    const float om = 1.0f - al;
-    const float rom = __frcp_rn(om);           // 1 / (1 - alpha)
-    const float Tb = p.T * rom;
-    const float w = al * Tb;
-    g[6] += p.gC0 * w;
-    g[7] += p.gC1 * w;
-    g[8] += p.gC2 * w;
-    g[9] += p.gD * w;
-    const float dLda = Tb * (p.gC0 * C.x + p.gC1 * C.y + p.gC2 * C.z + p.gD * B.w) -
-                       (p.gC0 * p.SC0 + p.gC1 * p.SC1 + p.gC2 * p.SC2 + p.gD * p.SD + p.gT * p.Tfin) * rom;
-    p.SC0 = fmaf(C.x, w, p.SC0);
-    p.SC1 = fmaf(C.y, w, p.SC1);
-    p.SC2 = fmaf(C.z, w, p.SC2);
-    p.SD = fmaf(B.w, w, p.SD);
-    p.T = Tb;
-    if (e < 0.99f) {
-        const float dLdp = dLda * al;              // d alpha / d power = alpha (natural units)
-        g[5] += dLda * ex2_approx(-q);             // d alpha / d opacity = 2^-q'
-        const float l0 = A.z, l1 = A.w, l2 = B.x;
-        const float t = l0 * dx + l1 * dy;
-        g[0] -= dLdp * (l0 * t) * kInvChol2;                    // -(a dx + b dy)
-        g[1] -= dLdp * (l1 * t + l2 * l2 * dy) * kInvChol2;     // -(c dy + b dx)
-        g[2] -= dLdp * 0.5f * dx * dx;
-        g[3] -= dLdp * dx * dy;
-        g[4] -= dLdp * 0.5f * dy * dy;
-    }
+    const float2 e = make_float2(ex2_approx(__fsub_rn(B.y, q.x)), ex2_approx(__fsub_rn(B.y, q.y)));
+    const float2 al = make_float2(fminf(e.x, 0.99f), fminf(e.y, 0.99f));
+    const float2 om = __ffma2_rn(al, f2(-1.f), f2(1.f));
+    const float2 rom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));   // 1 / (1 - alpha)
+    const float2 Tb = __fmul2_rn(p.T, rom);
+    const float2 m = make_float2(c0 ? 1.f : 0.f, c1 ? 1.f : 0.f);
+    const float2 w = __fmul2_rn(__fmul2_rn(al, Tb), m);
+    g[6] = __ffma2_rn(p.gC0, w, g[6]);
+    g[7] = __ffma2_rn(p.gC1, w, g[7]);
+    g[8] = __ffma2_rn(p.gC2, w, g[8]);
+    g[9] = __ffma2_rn(p.gD, w, g[9]);
+    float2 s1 = __fmul2_rn(p.gC0, f2(C.x));
+    s1 = __ffma2_rn(p.gC1, f2(C.y), s1);
+    s1 = __ffma2_rn(p.gC2, f2(C.z), s1);
+    s1 = __ffma2_rn(p.gD, f2(B.w), s1);
+    float2 s2 = __fmul2_rn(p.gC0, p.SC0);
+    s2 = __ffma2_rn(p.gC1, p.SC1, s2);
+    s2 = __ffma2_rn(p.gC2, p.SC2, s2);
+    s2 = __ffma2_rn(p.gD, p.SD, s2);
+    s2 = __ffma2_rn(p.gT, p.Tfin, s2);
+    // dL/dalpha, zero where the pixel is not reached or alpha was clamped
+    const float2 mc = make_float2(c0 && e.x < 0.99f ? 1.f : 0.f, c1 && e.y < 0.99f ? 1.f : 0.f);
+    const float2 dLda = __fmul2_rn(__ffma2_rn(Tb, s1, __fmul2_rn(s2, make_float2(-rom.x, -rom.y))), mc);
+    p.SC0 = __ffma2_rn(f2(C.x), w, p.SC0);
+    p.SC1 = __ffma2_rn(f2(C.y), w, p.SC1);
+    p.SC2 = __ffma2_rn(f2(C.z), w, p.SC2);
+    p.SD = __ffma2_rn(f2(B.w), w, p.SD);
+    p.T = make_float2(c0 ? Tb.x : p.T.x, c1 ? Tb.y : p.T.y);
+    const float2 dLdp = __fmul2_rn(dLda, al);                  // d alpha / d power = alpha (natural units)
+    g[5] = __ffma2_rn(dLda, make_float2(ex2_approx(-q.x), ex2_approx(-q.y)), g[5]);   // d alpha / d opacity = 2^-q'
+    const float l0 = A.z, l1 = A.w, l2 = B.x;
+    const float2 t = __ffma2_rn(f2(l0), dx, f2(l1 * dy));
+    const float2 ndp = __fmul2_rn(dLdp, f2(-kInvChol2));
+    g[0] = __ffma2_rn(ndp, __fmul2_rn(f2(l0), t), g[0]);                                   // -(a dx + b dy)
+    g[1] = __ffma2_rn(ndp, __ffma2_rn(f2(l1), t, f2(l2 * l2 * dy)), g[1]);                 // -(c dy + b dx)
+    const float2 hdp = __fmul2_rn(dLdp, f2(-0.5f));
+    g[2] = __ffma2_rn(hdp, __fmul2_rn(dx, dx), g[2]);
+    g[3] = __ffma2_rn(__fmul2_rn(dLdp, f2(-1.f)), __fmul2_rn(dx, f2(dy)), g[3]);
+    g[4] = __ffma2_rn(hdp, f2(dy * dy), g[4]);
 }
 
 constexpr int kGroup = 3;     // splats whose gradients are reduced together (3 x 10 rows <= 32 lanes)
@@ -136,33 +154,31 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const int64_t lp = (int64_t)py * V.w + px;
     const int64_t pix = V.pix_base + lp;
     const float *grgb = a.g_rgb + 3 * V.pix_base;
-    PixState P0, P1;
-    P0.SC0 = P0.SC1 = P0.SC2 = P0.SD = 0.f;
-    P1.SC0 = P1.SC1 = P1.SC2 = P1.SD = 0.f;
-    P0.last = P1.last = 0;
-    P0.T = P1.T = P0.Tfin = P1.Tfin = 1.f;
-    P0.gC0 = P0.gC1 = P0.gC2 = P0.gD = P0.gT = 0.f;
-    P1.gC0 = P1.gC1 = P1.gC2 = P1.gD = P1.gT = 0.f;
+    PixState2 P;
+    P.SC0 = P.SC1 = P.SC2 = P.SD = f2(0.f);
+    P.last0 = P.last1 = 0;
+    P.T = P.Tfin = f2(1.f);
+    P.gC0 = P.gC1 = P.gC2 = P.gD = P.gT = f2(0.f);
     if (in0) {
-        P0.last = a.ncontrib[pix];
-        P0.T = P0.Tfin = a.Tf[pix];
-        P0.gC0 = grgb[lp];
-        P0.gC1 = grgb[HW + lp];
-        P0.gC2 = grgb[2 * HW + lp];
-        P0.gD = a.g_depth[pix];
-        P0.gT = a.g_T ? a.g_T[pix] : 0.f;
+        P.last0 = a.ncontrib[pix];
+        P.T.x = P.Tfin.x = a.Tf[pix];
+        P.gC0.x = grgb[lp];
+        P.gC1.x = grgb[HW + lp];
+        P.gC2.x = grgb[2 * HW + lp];
+        P.gD.x = a.g_depth[pix];
+        P.gT.x = a.g_T ? a.g_T[pix] : 0.f;
     }
     if (in1) {
-        P1.last = a.ncontrib[pix + 1];
-        P1.T = P1.Tfin = a.Tf[pix + 1];
-        P1.gC0 = grgb[lp + 1];
-        P1.gC1 = grgb[HW + lp + 1];
-        P1.gC2 = grgb[2 * HW + lp + 1];
-        P1.gD = a.g_depth[pix + 1];
-        P1.gT = a.g_T ? a.g_T[pix + 1] : 0.f;
+        P.last1 = a.ncontrib[pix + 1];
+        P.T.y = P.Tfin.y = a.Tf[pix + 1];
+        P.gC0.y = grgb[lp + 1];
+        P.gC1.y = grgb[HW + lp + 1];
+        P.gC2.y = grgb[2 * HW + lp + 1];
+        P.gD.y = a.g_depth[pix + 1];
+        P.gT.y = a.g_T ? a.g_T[pix + 1] : 0.f;
     }
     // this warp's blended positions end at its largest last contributor
-    const uint32_t maxlast = __reduce_max_sync(FULL, max(P0.last, P1.last));
+    const uint32_t maxlast = __reduce_max_sync(FULL, max(P.last0, P.last1));
     if (maxlast == 0) return;
     const int nb = (int)((maxlast + 31) / 32);
 
@@ -195,15 +211,17 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const uint32_t pos = (uint32_t)bi * 32 + (uint32_t)__float_as_int(Ck.w) + 1;
             float q0, q1;
             pair_q2(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, pxc, pyc, q0, q1);
-            const bool c0 = pos <= P0.last && q0 <= Bk.z;
-            const bool c1 = pos <= P1.last && q1 <= Bk.z;
+            const bool c0 = pos <= P.last0 && q0 <= Bk.z;
+            const bool c1 = pos <= P.last1 && q1 <= Bk.z;
             if (!__any_sync(FULL, c0 || c1)) continue;
+            float2 g2[kGrad2D];
+#pragma unroll
+            for (int i = 0; i < kGrad2D; ++i) g2[i] = f2(0.f);
+            const float dx = Ak.x - pxc, dy = Ak.y - pyc;
+            pixel_adjoint2(P, make_float2(q0, q1), c0, c1, make_float2(dx, dx - 1.0f), dy, Ak, Bk, Ck, g2);
             float g[kGrad2D];
 #pragma unroll
-            for (int i = 0; i < kGrad2D; ++i) g[i] = 0.f;
-            const float dx = Ak.x - pxc, dy = Ak.y - pyc;
-            if (c0) pixel_adjoint(P0, q0, dx, dy, Ak, Bk, Ck, g);
-            if (c1) pixel_adjoint(P1, q1, dx - 1.0f, dy, Ak, Bk, Ck, g);
+            for (int i = 0; i < kGrad2D; ++i) g[i] = g2[i].x + g2[i].y;
             // the lane's contributions go to the group buffer; the group is reduced
             // when full: each lane sums whole 32-lane rows, one (splat, value) at a time
 #pragma unroll
