@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float4 Ck = wC[w][k];
             const uint32_t pos = (uint32_t)bi * 32 + (uint32_t)__float_as_int(Ck.w) + 1;
             float q0, q1;
-            pair_q2(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, pxc, pyc, q0, q1);
+            float K, L;
+            splat_KL(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, K, L);
+            pair_q2(K, L, Ak.z, Ak.w, Bk.x, pxc, pyc, q0, q1);
             const bool c0 = pos <= P.last0 && q0 <= Bk.z;
             const bool c1 = pos <= P.last1 && q1 <= Bk.z;
             if (!__any_sync(FULL, c0 || c1)) continue;

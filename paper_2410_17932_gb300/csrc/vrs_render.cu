@@ -86,14 +86,13 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &
     }
 }
 
-// The two pixels' quadratic forms of one splat (see pair_q2), the last step packed.
+// The two pixels' quadratic forms of a splat staged as A = (K, L, l0, l1) (see pair_q2),
+// the last step packed.
 __device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc, float pyc)
 {
-    const float dy = __fsub_rn(A.y, pyc);
-    const float m = __fmul_rn(A.w, dy);
-    const float s = __fmul_rn(l2, dy);
+    const float s = __fmaf_rn(-l2, pyc, A.y);
     const float s2 = __fmul_rn(s, s);
-    const float t0 = __fmaf_rn(A.z, __fsub_rn(A.x, pxc), m);
+    const float t0 = __fmaf_rn(-A.z, pxc, __fmaf_rn(-A.w, pyc, A.x));
     const float2 t = make_float2(t0, __fsub_rn(t0, A.z));
     return __ffma2_rn(t, t, f2(s2));
 }
@@ -169,7 +168,9 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                 stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
                 C.w = __int_as_float((int)(j - range.x + 1));
                 mask = cull_blocks<Cfg::WGX, Cfg::WARPS / Cfg::WGX>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z));
-                sR[tid][0] = A;
+                float K, L;
+                splat_KL(A.x, A.y, A.z, A.w, B.x, K, L);
+                sR[tid][0] = make_float4(K, L, A.z, A.w);   // the mean enters only through K and L
                 sR[tid][1] = B;
                 sR[tid][2] = C;
             }
