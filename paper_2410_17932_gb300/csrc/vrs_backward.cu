@@ -47,14 +47,15 @@ struct PixState2 {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // The two pixels' contributions to the 10 record gradients of a splat, as FP32x2
-// pairs (each component rounded as the scalar operation).  A pixel the splat does
+// pairs (each component rounded as the scalar operation); u = q' - lo per pixel
+// (pair_u2).  A pixel the splat does
 // not reach (c false) contributes zero and keeps its state: its weight and
 // dL/dalpha are multiplied by 0, its T is selected.  g[i].x + g[i].y is the
 // lane's value i.
-__device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 q, bool c0, bool c1, float2 dx, float dy,
+__device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 u, bool c0, bool c1, float2 dx, float dy,
                                                const float4 A, const float4 B, const float4 C, float2 *g)
 {
-    const float2 e = make_float2(ex2_approx(__fsub_rn(B.y, q.x)), ex2_approx(__fsub_rn(B.y, q.y)));
+    const float2 e = make_float2(ex2_approx(-u.x), ex2_approx(-u.y));
     const float2 al = make_float2(fminf(e.x, 0.99f), fminf(e.y, 0.99f));
     const float2 om = __ffma2_rn(al, f2(-1.f), f2(1.f));
     const float2 rom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));   // 1 / (1 - alpha)
@@ -83,7 +84,7 @@ __device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 q, bool c0, 
     p.SD = __ffma2_rn(f2(B.w), w, p.SD);
     p.T = make_float2(c0 ? Tb.x : p.T.x, c1 ? Tb.y : p.T.y);
     const float2 dLdp = __fmul2_rn(dLda, al);                  // d alpha / d power = alpha (natural units)
-    g[5] = __ffma2_rn(dLda, make_float2(ex2_approx(-q.x), ex2_approx(-q.y)), g[5]);   // d alpha / d opacity = 2^-q'
+    g[5] = __ffma2_rn(dLda, make_float2(ex2_approx(-(u.x + B.y)), ex2_approx(-(u.y + B.y))), g[5]);   // d alpha / d opacity = 2^-q'
     const float l0 = A.z, l1 = A.w, l2 = B.x;
     const float2 t = __ffma2_rn(f2(l0), dx, f2(l1 * dy));
     const float2 ndp = __fmul2_rn(dLdp, f2(-kInvChol2));
@@ -209,18 +210,17 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float4 Bk = wB[w][k];
             const float4 Ck = wC[w][k];
             const uint32_t pos = (uint32_t)bi * 32 + (uint32_t)__float_as_int(Ck.w) + 1;
-            float q0, q1;
-            float K, L;
+            float u0, u1, K, L;
             splat_KL(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, K, L);
-            pair_q2(K, L, Ak.z, Ak.w, Bk.x, pxc, pyc, q0, q1);
-            const bool c0 = pos <= P.last0 && q0 <= Bk.z;
-            const bool c1 = pos <= P.last1 && q1 <= Bk.z;
+            pair_u2(K, L, Ak.z, Ak.w, Bk.x, Bk.y, pxc, pyc, u0, u1);
+            const bool c0 = pos <= P.last0 && u0 <= kLog2_255;
+            const bool c1 = pos <= P.last1 && u1 <= kLog2_255;
             if (!__any_sync(FULL, c0 || c1)) continue;
             float2 g2[kGrad2D];
 #pragma unroll
             for (int i = 0; i < kGrad2D; ++i) g2[i] = f2(0.f);
             const float dx = Ak.x - pxc, dy = Ak.y - pyc;
-            pixel_adjoint2(P, make_float2(q0, q1), c0, c1, make_float2(dx, dx - 1.0f), dy, Ak, Bk, Ck, g2);
+            pixel_adjoint2(P, make_float2(u0, u1), c0, c1, make_float2(dx, dx - 1.0f), dy, Ak, Bk, Ck, g2);
             float g[kGrad2D];
 #pragma unroll
             for (int i = 0; i < kGrad2D; ++i) g[i] = g2[i].x + g2[i].y;

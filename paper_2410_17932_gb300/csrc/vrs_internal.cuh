@@ -460,25 +460,28 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int K, float
 //   q' = (l0 dx + l1 dy)^2 + (l2 dy)^2,  dx = su - pxc, dy = sv - pyc,
 // the quadratic form of the conic in the log2 domain; the splat contributes to
 // a pixel iff q' <= lt = lo + log2(255) (alpha >= 1/255), with
-// alpha = min(0.99, 2^(lo - q')).  Expanded, so that the per-pixel part is fused
-// multiply-adds: l0 dx + l1 dy = K - l0 pxc - l1 pyc with K = l0 su + l1 sv, and
-// l2 dy = L - l2 pyc with L = l2 sv (per splat, splat_KL).  In the tile-local frame
-// |K| stays below ~100, so its rounding moves q' by < 1e-4 where alpha >= 1/255.
+// alpha = min(0.99, 2^(lo - q')).  Evaluated as u = q' - lo, expanded so that
+// the per-pixel part is fused multiply-adds: l0 dx + l1 dy = K - l0 pxc - l1 pyc
+// with K = l0 su + l1 sv, and l2 dy = L - l2 pyc with L = l2 sv (per splat,
+// splat_KL); then u = t^2 + (s^2 - lo), alpha = min(0.99, 2^-u), and the splat
+// contributes iff u <= log2(255).  In the tile-local frame |K| stays below ~100,
+// so its rounding moves u by < 1e-4 where alpha >= 1/255.
 __device__ __forceinline__ void splat_KL(float su, float sv, float l0, float l1, float l2, float &K, float &L)
 {
     K = __fmaf_rn(l0, su, __fmul_rn(l1, sv));
     L = __fmul_rn(l2, sv);
 }
 
-__device__ __forceinline__ void pair_q2(float K, float L, float l0, float l1, float l2, float pxc, float pyc,
-                                        float &q0, float &q1)
+__device__ __forceinline__ void pair_u2(float K, float L, float l0, float l1, float l2, float lo, float pxc,
+                                        float pyc, float &u0, float &u1)
 {
     const float s = __fmaf_rn(-l2, pyc, L);
-    const float s2 = __fmul_rn(s, s);
-    const float t0 = __fmaf_rn(-l0, pxc, __fmaf_rn(-l1, pyc, K));
-    const float t1 = __fsub_rn(t0, l0);
-    q0 = __fmaf_rn(t0, t0, s2);
-    q1 = __fmaf_rn(t1, t1, s2);
+    const float w = __fmaf_rn(s, s, -lo);
+    const float r = __fmaf_rn(-l1, pyc, K);
+    const float t0 = __fmaf_rn(-l0, pxc, r);
+    const float t1 = __fmaf_rn(-l0, pxc + 1.0f, r);
+    u0 = __fmaf_rn(t0, t0, w);
+    u1 = __fmaf_rn(t1, t1, w);
 }
 
 __device__ __forceinline__ float pair_alpha(float lo, float q)

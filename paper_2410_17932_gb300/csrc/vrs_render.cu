@@ -48,18 +48,17 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // One splat at a thread's two pixels, front to back: skip below 1/255, stop
 // before T would drop under 1e-4, otherwise blend.  Written as selects (no
-// branches).  q holds the two pixels' quadratic forms; B = (l2, lo, lt,
+// branches).  u holds the two pixels' q' - lo (pair_u2); B = (-l2, lo, lt,
 // depth), C = (r, g, b, list position).  LAST tracks each pixel's last
 // blended position, the reverse pass's starting point (plans made for the
 // backward); COUNT also tracks the stop position and the blend count for the
 // work counters.
 template <bool COUNT, bool LAST>
-__device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &B, const float4 &C,
+__device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 u, const float4 &B, const float4 &C,
                                             uint32_t &n_blend)
 {
-    const bool h0 = !P.done0 && q.x <= B.z, h1 = !P.done1 && q.y <= B.z;
-    const float2 e = __ffma2_rn(q, f2(-1.f), f2(B.y));                     // lo - q
-    const float2 al = make_float2(fminf(ex2_approx(e.x), 0.99f), fminf(ex2_approx(e.y), 0.99f));
+    const bool h0 = !P.done0 && u.x <= kLog2_255, h1 = !P.done1 && u.y <= kLog2_255;
+    const float2 al = make_float2(fminf(ex2_approx(-u.x), 0.99f), fminf(ex2_approx(-u.y), 0.99f));
     const float2 Tn = __fmul2_rn(P.T, __ffma2_rn(al, f2(-1.f), f2(1.f)));  // T (1 - alpha)
     const bool s0 = h0 && Tn.x < 1e-4f, s1 = h1 && Tn.y < 1e-4f;
     const bool b0 = h0 && !s0, b1 = h1 && !s1;
@@ -86,15 +85,16 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 q, const float4 &
     }
 }
 
-// The two pixels' quadratic forms of a splat staged as A = (K, L, l0, l1) (see pair_q2),
-// the last step packed.
-__device__ __forceinline__ float2 pair_q2v(const float4 &A, float l2, float pxc, float pyc)
+// pair_u2 for a splat staged as A = (K, L, -l0, -l1), B.x = -l2, B.y = lo: the
+// same operations (negation is exact), the per-pixel ones packed; pxc2 =
+// (pxc, pxc + 1).
+__device__ __forceinline__ float2 pair_u2v(const float4 &A, const float4 &B, float2 pxc2, float pyc)
 {
-    const float s = __fmaf_rn(-l2, pyc, A.y);
-    const float s2 = __fmul_rn(s, s);
-    const float t0 = __fmaf_rn(-A.z, pxc, __fmaf_rn(-A.w, pyc, A.x));
-    const float2 t = make_float2(t0, __fsub_rn(t0, A.z));
-    return __ffma2_rn(t, t, f2(s2));
+    const float s = __fmaf_rn(B.x, pyc, A.y);
+    const float w = __fmaf_rn(s, s, -B.y);
+    const float r = __fmaf_rn(A.w, pyc, A.x);
+    const float2 t = __ffma2_rn(f2(A.z), pxc2, f2(r));
+    return __ffma2_rn(t, t, f2(w));
 }
 
 template <int TS, bool COUNT, bool LAST, bool PERSIST>
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
+    const float2 pxc2 = make_float2(pxc, pxc + 1.0f);
     const uint32_t lmask = lanemask_lt();
     if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0ull;
     __syncthreads();
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                 mask = cull_blocks<Cfg::WGX, Cfg::WARPS / Cfg::WGX>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z));
                 float K, L;
                 splat_KL(A.x, A.y, A.z, A.w, B.x, K, L);
-                sR[tid][0] = make_float4(K, L, A.z, A.w);   // the mean enters only through K and L
+                sR[tid][0] = make_float4(K, L, -A.z, -A.w);   // the mean enters only through K and L
+                B.x = -B.x;
                 sR[tid][1] = B;
                 sR[tid][2] = C;
             }
@@ -192,15 +194,15 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                     const int j0 = slist[w][k], j1 = slist[w][k + 1];
                     const float4 A0 = sR[j0][0], B0 = sR[j0][1], C0 = sR[j0][2];
                     const float4 A1 = sR[j1][0], B1 = sR[j1][1], C1 = sR[j1][2];
-                    const float2 q0 = pair_q2v(A0, B0.x, pxc, pyc);
-                    const float2 q1 = pair_q2v(A1, B1.x, pxc, pyc);
-                    pix_update2<COUNT, LAST>(P, q0, B0, C0, n_blend);
-                    pix_update2<COUNT, LAST>(P, q1, B1, C1, n_blend);
+                    const float2 u0 = pair_u2v(A0, B0, pxc2, pyc);
+                    const float2 u1 = pair_u2v(A1, B1, pxc2, pyc);
+                    pix_update2<COUNT, LAST>(P, u0, B0, C0, n_blend);
+                    pix_update2<COUNT, LAST>(P, u1, B1, C1, n_blend);
                 }
                 if (k < cnt) {
                     const int j0 = slist[w][k];
                     const float4 A0 = sR[j0][0], B0 = sR[j0][1], C0 = sR[j0][2];
-                    pix_update2<COUNT, LAST>(P, pair_q2v(A0, B0.x, pxc, pyc), B0, C0, n_blend);
+                    pix_update2<COUNT, LAST>(P, pair_u2v(A0, B0, pxc2, pyc), B0, C0, n_blend);
                 }
             }
         }
