@@ -59,18 +59,18 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 u, const float4 &
 {
     const bool h0 = !P.done0 && u.x <= kLog2_255, h1 = !P.done1 && u.y <= kLog2_255;
     const float2 al = make_float2(fminf(ex2_approx(-u.x), 0.99f), fminf(ex2_approx(-u.y), 0.99f));
-    const float2 Tn = __fmul2_rn(P.T, __ffma2_rn(al, f2(-1.f), f2(1.f)));  // T (1 - alpha)
+    const float2 m = __fmul2_rn(al, P.T);                       // alpha T, the weight if it blends
+    const float2 Tn = __ffma2_rn(m, f2(-1.f), P.T);             // T - alpha T = T (1 - alpha)
     const bool s0 = h0 && Tn.x < 1e-4f, s1 = h1 && Tn.y < 1e-4f;
     const bool b0 = h0 && !s0, b1 = h1 && !s1;
-    // alpha where the pixel blends, 0 elsewhere: then T (1 - a) is T' or T exactly,
-    // and a T is the weight or 0, without selects on T and the weight
-    const float2 a = make_float2(b0 ? al.x : 0.f, b1 ? al.y : 0.f);
-    const float2 wt = __fmul2_rn(a, P.T);
+    // the weight where the pixel blends, 0 elsewhere: then T - weight is T' or T
+    // exactly, without a select on T
+    const float2 wt = make_float2(b0 ? m.x : 0.f, b1 ? m.y : 0.f);
     P.R = __ffma2_rn(f2(C.x), wt, P.R);
     P.G = __ffma2_rn(f2(C.y), wt, P.G);
     P.B = __ffma2_rn(f2(C.z), wt, P.B);
     P.D = __ffma2_rn(f2(B.w), wt, P.D);
-    P.T = __fmul2_rn(P.T, __ffma2_rn(a, f2(-1.f), f2(1.f)));
+    P.T = __ffma2_rn(wt, f2(-1.f), P.T);
     const uint32_t pos = (uint32_t)__float_as_int(C.w);
     if (LAST) {
         P.last0 = b0 ? pos : P.last0;
