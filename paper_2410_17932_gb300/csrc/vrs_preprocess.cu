@@ -31,8 +31,7 @@ struct PreParams {
 // k_decide reads only the 44 bytes of geometry per Gaussian (mean, log-scales,
 // quaternion, opacity logit), takes the FP32 integer decisions for every view
 // of the scene and appends each visible (Gaussian, view) pair to a list with
-// the decision values the record needs (one warp-aggregated atomic per warp
-// and view).  Only about a quarter of the pairs of a VR view are visible, and
+// the decision values the record needs (one slot atomic per CTA and view).  Only about a quarter of the pairs of a VR view are visible, and
 // the visible ones cluster by Gaussian index (the scene's Gaussians come in
 // spatial clusters), so a fused kernel leaves most warps idle or most SMs
 // waiting on a few CTAs; the list makes the second kernel dense.
@@ -89,17 +88,32 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
     }
     if (in && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
     if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
-    if (!__any_sync(FULL, ok)) return;
+    // one slot atomic per CTA and view (all CTAs add to the same counter): the warps'
+    // counts meet in shared memory, double-buffered by view parity
+    __shared__ uint32_t s_cnt[2][kDecideThreads / 32];
+    __shared__ unsigned long long s_base[2][kDecideThreads / 32];
+    const int wp = threadIdx.x >> 5;
+    const bool wok = __any_sync(FULL, ok);
     for (int vi = 0; vi < p.n_views; ++vi) {
         const DevView &V = vt.v[p.views[vi]];
         Decision d;
         d.visible = false;
         if (ok) decide(V, pre, m[0], m[1], m[2], logit, vt.tile, d);
-        const uint32_t vb = __ballot_sync(FULL, d.visible);
-        if (vb == 0u) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.st->scene_pairs[p.scene], (unsigned long long)__popc(vb));
-        base = __shfl_sync(FULL, base, 0);
+        const uint32_t vb = wok ? __ballot_sync(FULL, d.visible) : 0u;
+        const int par = vi & 1;
+        if (lane == 0) s_cnt[par][wp] = __popc(vb);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long sum = 0;
+            for (int q = 0; q < kDecideThreads / 32; ++q) sum += s_cnt[par][q];
+            unsigned long long b = sum ? atomicAdd(&p.st->scene_pairs[p.scene], sum) : 0ull;
+            for (int q = 0; q < kDecideThreads / 32; ++q) {
+                s_base[par][q] = b;
+                b += s_cnt[par][q];
+            }
+        }
+        __syncthreads();
+        const unsigned long long base = s_base[par][wp];
         if (d.visible) {
             const unsigned long long slot = base + __popc(vb & lanemask_lt());
             if (slot < p.pair_cap) {
