@@ -509,18 +509,27 @@ __device__ __forceinline__ bool touched_warp(const ViewTable &vt, const ParamArg
 __global__ void __launch_bounds__(256) k_touched(const __grid_constant__ ViewTable vt,
                                                  const __grid_constant__ ParamArgs p)
 {
-    const int lane = threadIdx.x & 31;
+    // one list atomic per CTA: the warps' counts meet in shared memory
+    __shared__ uint32_t s_cnt[8], s_base[8];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) - lane;
-    if (p.st->flags & ST_CAPACITY) return;
-    if (g0 >= p.S.n) return;   // uniform over the warp
+    if (p.st->flags & ST_CAPACITY) return;     // uniform over the grid
     const int g = g0 + lane;
-    const bool t = touched_warp(vt, p, g0, lane) && g < p.S.n;
+    const bool t = g0 < p.S.n && touched_warp(vt, p, g0, lane) && g < p.S.n;
     const uint32_t b = __ballot_sync(0xffffffffu, t);
-    if (b == 0u) return;
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(p.list_count, (uint32_t)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (t) p.list[base + __popc(b & lanemask_lt())] = (uint32_t)g;
+    if (lane == 0) s_cnt[wp] = (uint32_t)__popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t sum = 0;
+        for (int q = 0; q < 8; ++q) sum += s_cnt[q];
+        uint32_t base = sum ? atomicAdd(p.list_count, sum) : 0u;
+        for (int q = 0; q < 8; ++q) {
+            s_base[q] = base;
+            base += s_cnt[q];
+        }
+    }
+    __syncthreads();
+    if (t) p.list[s_base[wp] + __popc(b & lanemask_lt())] = (uint32_t)g;
 }
 
 template <int K>
