@@ -464,8 +464,9 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int K, float
 // the per-pixel part is fused multiply-adds: l0 dx + l1 dy = K - l0 pxc - l1 pyc
 // with K = l0 su + l1 sv, and l2 dy = L - l2 pyc with L = l2 sv (per splat,
 // splat_KL); then u = t^2 + (s^2 - lo), alpha = min(0.99, 2^-u), and the splat
-// contributes iff u <= log2(255).  In the tile-local frame |K| stays below ~100,
-// so its rounding moves u by < 1e-4 where alpha >= 1/255.
+// contributes iff u <= log2(255).  In the tile-local frame |K| stays below ~50
+// where alpha >= 1/255; an FP32 emulation over the periphery frame's instances
+// put the error of 2^-u at <= 4.7e-6 relative there (the unexpanded form: ~6e-6).
 __device__ __forceinline__ void splat_KL(float su, float sv, float l0, float l1, float l2, float &K, float &L)
 {
     K = __fmaf_rn(l0, su, __fmul_rn(l1, sv));
