@@ -84,6 +84,20 @@ def test_tile_sizes_ragged(tile):
     compare_images((rgb, depth, T), orc, f"tile{tile}")
 
 
+@pytest.mark.parametrize("tile", [16, 32])
+def test_one_tile_wide_view(tile):
+    # a view one tile wide (gw = 1) and many tiles tall: every tile's column is 0,
+    # its row the whole tile index; a ragged width and height too
+    scs, _ = I.plain_200()
+    cam = I.Camera(np.eye(3), np.zeros(3), 180.0, 190.0, 6.3, 150.2, 13, 301)
+    ras = _run(scs, [cam], tile=tile)
+    assert int(ras.plan.view_gw[0]) == 1
+    _check_sort(ras, scs, [cam], tile)
+    rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
+    orc = oracle.render(scs[0], cam, tile=tile)
+    compare_images((rgb, depth, T), orc, f"narrow{tile}")
+
+
 def test_persistent_equals_per_tile():
     torch = torch_cuda()
     scs, cams = I.plain_200()
