@@ -334,27 +334,24 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     d.rad = rad;
     d.ub = FMUL(V.fx, d.txtz);
     d.vb = FMUL(V.fy, d.tytz);
-    float xlo = FSUB(d.ub, rad), xhi = FADD(d.ub, rad);
-    float ylo = FSUB(d.vb, rad), yhi = FADD(d.vb, rad);
-    // floor of the exact value of (edge + principal point) / tile
-    const float inv = 1.0f / (float)tile;    // a power of two: exact
-    int x0 = floor_sum_div(xlo, V.cx, inv), x1 = floor_sum_div(xhi, V.cx, inv) + 1;
-    int y0 = floor_sum_div(ylo, V.cy, inv), y1 = floor_sum_div(yhi, V.cy, inv) + 1;
-    // clipped to the bounding box of the ellipse where alpha >= 1/255:
-    // x^T Sigma'^-1 x <= thr = 2 ln(255 o), o = sigmoid(logit), half extents
-    // sqrt(thr Sigma'_xx) and sqrt(thr Sigma'_yy); thr carries a margin far above
-    // the rounding of any FP32 evaluation of alpha, so no tile that can hold a
-    // pixel with alpha >= 1/255 is dropped
+    // The 3-sigma rectangle clipped to the bounding box of the ellipse where
+    // alpha >= 1/255: x^T Sigma'^-1 x <= thr = 2 ln(255 o), o = sigmoid(logit),
+    // half extents sqrt(thr Sigma'_xx) and sqrt(thr Sigma'_yy); thr carries a
+    // margin far above the rounding of any FP32 evaluation of alpha, so no tile
+    // that can hold a pixel with alpha >= 1/255 is dropped.  Each bound is the
+    // floor of the exact value of (edge + principal point) / tile.  Rounding and
+    // that floor are monotone, so the tighter of the two rectangles' bounds is
+    // the bound of the nearer edge: max(floor(u - r), floor(u - h)) =
+    // floor(u - min(r, h)), one exact floor per side instead of two.
     const float eo = exp32_cw(-logit);
     const float op = FDIV(1.0f, FADD(1.0f, eo));
     float thr = FMUL(2.0f, log32_cw(FMUL(255.0f, op)));
     thr = FADD(FMUL(thr, 1.001f), 0.001f);
     if (!(thr > 0.0f)) return;
-    const float hx = __fsqrt_rn(FMUL(thr, a_)), hy = __fsqrt_rn(FMUL(thr, c_));
-    x0 = max(x0, floor_sum_div(FSUB(d.ub, hx), V.cx, inv));
-    x1 = min(x1, floor_sum_div(FADD(d.ub, hx), V.cx, inv) + 1);
-    y0 = max(y0, floor_sum_div(FSUB(d.vb, hy), V.cy, inv));
-    y1 = min(y1, floor_sum_div(FADD(d.vb, hy), V.cy, inv) + 1);
+    const float hx = fminf(rad, __fsqrt_rn(FMUL(thr, a_))), hy = fminf(rad, __fsqrt_rn(FMUL(thr, c_)));
+    const float inv = 1.0f / (float)tile;    // a power of two: exact
+    int x0 = floor_sum_div(FSUB(d.ub, hx), V.cx, inv), x1 = floor_sum_div(FADD(d.ub, hx), V.cx, inv) + 1;
+    int y0 = floor_sum_div(FSUB(d.vb, hy), V.cy, inv), y1 = floor_sum_div(FADD(d.vb, hy), V.cy, inv) + 1;
     x0 = min(max(x0, 0), V.gw);
     x1 = min(max(x1, 0), V.gw);
     y0 = min(max(y0, 0), V.gh);
