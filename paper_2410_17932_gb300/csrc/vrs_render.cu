@@ -63,9 +63,10 @@ __device__ __forceinline__ void pix_update2(PixAcc2 &P, float2 u, const float4 &
     const float2 Tn = __ffma2_rn(m, f2(-1.f), P.T);             // T - alpha T = T (1 - alpha)
     const bool s0 = h0 && Tn.x < 1e-4f, s1 = h1 && Tn.y < 1e-4f;
     const bool b0 = h0 && !s0, b1 = h1 && !s1;
-    // the weight where the pixel blends, 0 elsewhere: then T - weight is T' or T
-    // exactly, without a select on T
-    const float2 wt = make_float2(b0 ? m.x : 0.f, b1 ? m.y : 0.f);
+    // the weight where the pixel blends, 0 elsewhere (alpha T times a 0/1 factor, a
+    // multiply rather than a select): then T - weight is T' or T exactly, without a
+    // select on T
+    const float2 wt = __fmul2_rn(m, make_float2(b0 ? 1.f : 0.f, b1 ? 1.f : 0.f));
     P.R = __ffma2_rn(f2(C.x), wt, P.R);
     P.G = __ffma2_rn(f2(C.y), wt, P.G);
     P.B = __ffma2_rn(f2(C.z), wt, P.B);
