@@ -482,11 +482,6 @@ __device__ __forceinline__ void pair_u2(float K, float L, float l0, float l1, fl
     u1 = __fmaf_rn(t1, t1, w);
 }
 
-__device__ __forceinline__ float pair_alpha(float lo, float q)
-{
-    return fminf(ex2_approx(__fsub_rn(lo, q)), 0.99f);
-}
-
 // ---------------------------------------------------------------------------
 // Blend-kernel geometry and the staging of one instance into a tile's local
 // frame, shared by the forward and backward blend kernels.
@@ -632,55 +627,6 @@ __device__ __forceinline__ void stage_record(const float4 r0, const float4 r1, c
     A = make_float4(su, sv, r1.x, r1.y);
     B = make_float4(r1.z, r1.w, r1.w + kLog2_255, r2.w);
     C = make_float4(r2.x, r2.y, r2.z, 0.f);
-}
-
-// ---------------------------------------------------------------------------
-// mbarrier + bulk-copy (TMA, non-tensor) helpers.
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// 1D bulk copy global -> shared, completing `bytes` on the mbarrier.  Both
-// addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Bounded wait for phase `parity` of the mbarrier; returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_iters)
-{
-    for (uint32_t i = 0; i < max_iters; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 // A tile's [start, end) clamped to the live instance list, so that no range
