@@ -58,7 +58,10 @@ __device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 u, bool c0, 
     const float2 e = make_float2(ex2_approx(-u.x), ex2_approx(-u.y));
     const float2 al = make_float2(fminf(e.x, 0.99f), fminf(e.y, 0.99f));
     const float2 om = __ffma2_rn(al, f2(-1.f), f2(1.f));
-    const float2 rom = make_float2(__frcp_rn(om.x), __frcp_rn(om.y));   // 1 / (1 - alpha)
+    // 1 / (1 - alpha) by the hardware reciprocal (a few ulp, against the 0.5 ulp of the
+    // correctly rounded one, whose slow path cost 8 % of the training step's backward);
+    // 1 - alpha >= 0.01, and T recovered over hundreds of splats drifts by < 1e-4 relative
+    const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
     const float2 Tb = __fmul2_rn(p.T, rom);
     const float2 m = make_float2(c0 ? 1.f : 0.f, c1 ? 1.f : 0.f);
     const float2 w = __fmul2_rn(__fmul2_rn(al, Tb), m);
