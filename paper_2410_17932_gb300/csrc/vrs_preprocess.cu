@@ -275,10 +275,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             const uint32_t orid = __shfl_sync(FULL, rid, j);
             if (k < total) {
                 // (row, column) of the pair's local tile index: a reciprocal estimate
-                // (off by at most one below 2^23, and a rectangle holds at most 2^22
-                // tiles) and one correction step
+                // (the hardware reciprocal is within 1 ulp, so the quotient is off by
+                // at most 0.75 below 2^22, and a rectangle holds at most 2^22 tiles)
+                // and one correction step
                 const int local = (int)(k - oex);
-                int ty = (int)__fmul_rn((float)local, __frcp_rn((float)onx));
+                int ty = (int)__fmul_rn((float)local, rcp_approx((float)onx));
                 int tx = local - ty * onx;
                 if (tx < 0) {
                     --ty;
