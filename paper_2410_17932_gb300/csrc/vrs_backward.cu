@@ -509,11 +509,14 @@ __device__ __forceinline__ bool touched_warp(const ViewTable &vt, const ParamArg
 // Most Gaussians touch no pixel of any view: a light pass lists those that do
 // (one warp-aggregated atomic per warp), and the chain rule, heavy in registers,
 // then walks that list densely.
-__global__ void __launch_bounds__(256) k_touched(const __grid_constant__ ViewTable vt,
+constexpr int kTouchedThreads = 256;
+constexpr int kTouchedWarps = kTouchedThreads / 32;
+
+__global__ void __launch_bounds__(kTouchedThreads) k_touched(const __grid_constant__ ViewTable vt,
                                                  const __grid_constant__ ParamArgs p)
 {
     // one list atomic per CTA: the warps' counts meet in shared memory
-    __shared__ uint32_t s_cnt[8], s_base[8];
+    __shared__ uint32_t s_cnt[kTouchedWarps], s_base[kTouchedWarps];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) - lane;
     if (p.st->flags & ST_CAPACITY) return;     // uniform over the grid
@@ -524,9 +527,9 @@ __global__ void __launch_bounds__(256) k_touched(const __grid_constant__ ViewTab
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t sum = 0;
-        for (int q = 0; q < 8; ++q) sum += s_cnt[q];
+        for (int q = 0; q < kTouchedWarps; ++q) sum += s_cnt[q];
         uint32_t base = sum ? atomicAdd(p.list_count, sum) : 0u;
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < kTouchedWarps; ++q) {
             s_base[q] = base;
             base += s_cnt[q];
         }
@@ -574,7 +577,7 @@ cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const
     p.list_count = &st->work[4];
     cudaError_t e = cudaMemsetAsync(&st->work[4], 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_touched<<<grid_for(S.n, 256), 256, 0, s>>>(vt, p);
+    k_touched<<<grid_for(S.n, kTouchedThreads), kTouchedThreads, 0, s>>>(vt, p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (n_sms <= 0) n_sms = 152;
