@@ -257,13 +257,13 @@ vrs_status vrs_reset_status(const vrs_plan *plan, void *workspace, void *stream)
 #define VRS_NOALLOC_MAX_PAIRS (1 << 20)
 
 /* Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of
- * each key (8 bits per pass), the same sort vrs_bin_sort runs on the tile
- * instances, for callers that must not allocate device memory: code running
- * inside a CUDA stream capture (where cudaMalloc is not allowed), real-time
- * frame loops that must not risk the device-wide synchronisation an
- * allocation can cause, and plug-ins that live inside another application's
- * fixed memory budget.  The paper has no counterpart; this is a service of
- * the library.
+ * each key (8 bits per pass; a last pass that ends inside a byte sorts only the
+ * bits left, so bits above key_bits may hold anything), the same sort
+ * vrs_bin_sort runs on the tile instances, for callers that must not allocate
+ * device memory: real-time frame loops that must not risk the device-wide
+ * synchronisation an allocation can cause, and plug-ins that live inside
+ * another application's fixed memory budget.  The paper has no counterpart;
+ * this is a service of the library.
  *
  * It allocates nothing.  Its scratch is a static device array of about
  * 13.6 MB (VRS_NOALLOC_MAX_PAIRS pairs of ping-pong storage plus digit counts)

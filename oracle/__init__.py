@@ -89,7 +89,10 @@ def lib():
             L.orc_sh_basis_xyz.argtypes = [ctypes.c_double] * 3 + [P]
             L.orc_decide.restype = ctypes.c_int
             L.orc_decide.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
-                                     P, P, P, P, P, P]
+                                     P, P, P, P, P, P, P]
+            L.orc_decide64.restype = ctypes.c_int
+            L.orc_decide64.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
+                                       ctypes.c_int, P]
             L.orc_project.restype = None
             L.orc_project.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                       ctypes.POINTER(OrcCamera), P]
@@ -164,28 +167,98 @@ def sh_basis(x: float, y: float, z: float) -> np.ndarray:
     return out
 
 
-def decide(scene, cam, tile: int = 16) -> Dict[str, np.ndarray]:
-    """FP32 integer decisions for every Gaussian of `scene` in view `cam`."""
+def _nonfinite_rows(scene) -> np.ndarray:
+    # a Gaussian with any non-finite parameter is skipped (the C-ABI's NONFINITE rule)
+    n = scene.n
+    bad = ~np.isfinite(np.asarray(scene.opacity_logits, np.float32))
+    if n:
+        bad |= ~np.isfinite(np.asarray(scene.sh, np.float32)).reshape(n, -1).all(axis=1)
+    return bad
+
+
+def decide(scene, cam, tile: int = 16, pre: bool = False) -> Dict[str, np.ndarray]:
+    """FP32 integer decisions for every Gaussian of `scene` in view `cam`.
+
+    With pre=True also returns `pre` [n, 8]: the FP32 values just before each rounding
+    (tz, ubar, vbar, 3 sqrt(lambda), sqrt(thr a), sqrt(thr c), thr, det)."""
     n = scene.n
     means, ls, q = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)
     out = dict(visible=np.zeros(n, np.uint8), depth=np.zeros(n, np.float32),
                ubar=np.zeros(n, np.float32), vbar=np.zeros(n, np.float32),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32))
+    if pre:
+        out["pre"] = np.zeros((n, 8), np.float32)
     c = camera(cam)
     lg = _f32(scene.opacity_logits)
     st = lib().orc_decide(n, _p(means), _p(ls), _p(q), _p(lg), ctypes.byref(c), tile,
                           _p(out["visible"]), _p(out["depth"]), _p(out["ubar"]), _p(out["vbar"]),
-                          _p(out["radius"]), _p(out["rect"]))
-    # a Gaussian with any non-finite parameter is skipped (the C-ABI's NONFINITE rule)
-    bad = ~np.isfinite(np.asarray(scene.opacity_logits, np.float32))
-    if n:
-        bad |= ~np.isfinite(np.asarray(scene.sh, np.float32)).reshape(n, -1).all(axis=1)
+                          _p(out["radius"]), _p(out["rect"]), _p(out["pre"]) if pre else None)
+    bad = _nonfinite_rows(scene)
     if bad.any():
         out["visible"][bad] = 0
         out["rect"][bad] = 0
         st |= 2
     out["status"] = int(st)
     return out
+
+
+DEC64_DTYPE = np.dtype([("visible", "i4"), ("vis_amb", "i4"), ("radius", "i4"), ("r_lo", "i4"),
+                        ("r_hi", "i4"), ("rect", "i4", 4), ("rect_lo", "i4", 4), ("rect_hi", "i4", 4),
+                        ("tz", "f8"), ("e_tz", "f8"), ("ubar", "f8"), ("e_u", "f8"), ("vbar", "f8"),
+                        ("e_v", "f8"), ("rho", "f8"), ("e_rho", "f8"), ("hx", "f8"), ("e_hx", "f8"),
+                        ("hy", "f8"), ("e_hy", "f8"), ("thr", "f8"), ("e_thr", "f8"), ("det", "f8"),
+                        ("e_det", "f8")], align=True)
+KNIFE = 2.0      # decision windows are this many times the first-order FP32 error bound
+
+
+def decide64(scene, cam, tile: int = 16, clip: bool = True) -> np.ndarray:
+    """FP64 decisions from the plain definition (DEC64_DTYPE per Gaussian).
+
+    `visible`, `radius`, `rect` are the FP64 decisions; `vis_amb`, `r_lo..r_hi` and
+    `rect_lo..rect_hi` say which values an FP32 evaluation may legitimately reach
+    (knife edges); the value/bound pairs (tz, e_tz), (ubar, e_u), ... are the
+    pre-rounding values and first-order FP32 error bounds.  clip=False gives the
+    plain 3-sigma rectangle without the alpha >= 1/255 clip."""
+    n = scene.n
+    out = np.zeros(n, DEC64_DTYPE)
+    c = camera(cam)
+    st = lib().orc_decide64(n, _p(_f32(scene.means)), _p(_f32(scene.log_scales)), _p(_f32(scene.quats)),
+                            _p(_f32(scene.opacity_logits)), ctypes.byref(c), tile, int(bool(clip)),
+                            _p(out))
+    bad = _nonfinite_rows(scene)
+    if bad.any():
+        out["visible"][bad] = 0
+        out["vis_amb"][bad] = 0
+        out["rect"][bad] = 0
+    return out
+
+
+def dec64_as_decisions(d64: np.ndarray, scene, cam) -> Dict[str, np.ndarray]:
+    """The FP64 decisions in the form render()/bin_sort() take (depth key = FP32 of the FP64 z)."""
+    vis = d64["visible"].astype(np.uint8)
+    return dict(visible=vis, depth=np.where(vis > 0, d64["tz"], 0).astype(np.float32),
+                ubar=d64["ubar"].astype(np.float32), vbar=d64["vbar"].astype(np.float32),
+                radius=d64["radius"].astype(np.int32), rect=np.ascontiguousarray(d64["rect"], np.int32),
+                status=0)
+
+
+def decision_mismatches(d64: np.ndarray, visible, rect) -> Dict[str, np.ndarray]:
+    """Compares another evaluation's visibility and rectangles [n, 4] with the FP64 ones.
+
+    Returns boolean arrays: `differs` (any difference from the FP64 decision) and
+    `outside` (a difference that no FP32 rounding of the defined steps can explain)."""
+    vis = np.asarray(visible).astype(bool)
+    rect = np.asarray(rect).reshape(-1, 4)
+    v64 = d64["visible"].astype(bool)
+    amb = d64["vis_amb"].astype(bool)
+    both = vis & v64
+    rdiff = np.zeros(len(vis), bool)
+    rout = np.zeros(len(vis), bool)
+    rdiff[both] = np.any(rect[both] != d64["rect"][both], axis=1)
+    rout[both] = np.any((rect[both] < d64["rect_lo"][both]) | (rect[both] > d64["rect_hi"][both]), axis=1)
+    differs = (vis != v64) | rdiff
+    outside = ((vis != v64) & ~amb) | rout
+    return dict(differs=differs, outside=outside)
 
 
 def project(scene, cam) -> np.ndarray:

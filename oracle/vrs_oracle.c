@@ -204,10 +204,14 @@ static int floor_sum_div(float a, float b, int tile)
  * Returns per Gaussian: visible (0/1), the FP32 depth key, the FP32 screen
  * offsets (ubar, vbar), the radius, and the tile rectangle [x0,x1) x [y0,y1).
  * status bit 1: a quaternion had zero norm; bit 2: a non-finite parameter.
+ * `pre` (nullable, 8 floats per Gaussian) receives the values just before each
+ * rounding to an integer, for comparison with the FP64 decisions below:
+ * (tz, ubar, vbar, 3 sqrt(lambda), sqrt(thr a), sqrt(thr c), thr, det); NaN
+ * where the sequence stopped earlier.  They take no part in the decisions.
  */
 int orc_decide(int n, const float *means, const float *log_scales, const float *quats,
                const float *logits, const orc_camera *cam, int tile, uint8_t *visible, float *depth,
-               float *ubar, float *vbar, int32_t *radius, int32_t *rect)
+               float *ubar, float *vbar, int32_t *radius, int32_t *rect, float *pre)
 {
     int status = 0;
     const float *W = cam->R;
@@ -218,6 +222,8 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
     for (int g = 0; g < n; ++g) {
         visible[g] = 0; depth[g] = 0.f; ubar[g] = 0.f; vbar[g] = 0.f; radius[g] = 0;
         rect[4 * g + 0] = rect[4 * g + 1] = rect[4 * g + 2] = rect[4 * g + 3] = 0;
+        float *pv = pre ? pre + 8 * (size_t)g : NULL;
+        if (pv) for (int k = 0; k < 8; ++k) pv[k] = NAN;
         const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
         const float *ls = log_scales + 3 * g;
         const float *q = quats + 4 * g;
@@ -254,6 +260,7 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
             tc[r] = a + cam->t[r];
         }
         const float tx = tc[0], ty = tc[1], tz = tc[2];
+        if (pv) pv[0] = tz;
         if (!(tz > cam->znear)) continue;
         /* clamped projection Jacobian, rows of T = J W */
         float iz = 1.0f / tz;
@@ -294,12 +301,14 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         float dvv = g0 * g0; dvv = dvv + g1 * g1; dvv = dvv + g2 * g2;
         float a_ = n0 + 0.3f, c_ = n1 + 0.3f;
         float det = (dvv + 0.3f * (n0 + n1)) + 0.09f;
+        if (pv) pv[7] = det;
         if (!(det > 0.0f)) continue;
         float mid = 0.5f * (a_ + c_);
         float disc = fmaxf(0.1f, mid * mid - det);
         float lam = mid + sqrtf(disc);
         float rad = ceilf(3.0f * sqrtf(lam));
         float ub = cam->fx * txtz, vb = cam->fy * tytz;
+        if (pv) { pv[1] = ub; pv[2] = vb; pv[3] = 3.0f * sqrtf(lam); }
         float xlo = ub - rad, xhi = ub + rad, ylo = vb - rad, yhi = vb + rad;
         /* tile rectangle: floor of the exact value of (edge + principal point) / tile */
         int x0 = floor_sum_div(xlo, cam->cx, tile);
@@ -315,8 +324,10 @@ int orc_decide(int n, const float *means, const float *log_scales, const float *
         float thr = 2.0f * orc_log32(255.0f * op);
         thr = thr * 1.001f;
         thr = thr + 0.001f;
+        if (pv) pv[6] = thr;
         if (!(thr > 0.0f)) continue;
         float hx = sqrtf(thr * a_), hy = sqrtf(thr * c_);
+        if (pv) { pv[4] = hx; pv[5] = hy; }
         int bx0 = floor_sum_div(ub - hx, cam->cx, tile);
         int bx1 = floor_sum_div(ub + hx, cam->cx, tile) + 1;
         int by0 = floor_sum_div(vb - hy, cam->cy, tile);
@@ -437,6 +448,263 @@ void orc_project(int n, const float *means, const float *log_scales, const float
     for (int g = 0; g < n; ++g)
         project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
                     sh + (size_t)3 * K * g, K, cam, out + g);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The integer decisions from their plain definition, in FP64, written
+ * independently of the FP32 sequence of orc_decide (Sec. 3.1: splats with a
+ * covariance built from scale and rotation, projected to screen; the 3-sigma
+ * radius and tile rectangle of the 3DGS rasterizer the paper builds on):
+ *   Sigma  = R S S^T R^T with S = diag(exp(log_s)), R from the normalised quaternion
+ *   t      = W mu + t_c; not visible when t_z <= znear
+ *   J      = [[fx/z, 0, -fx x'/z^2], [0, fy/z, -fy y'/z^2]], x' and y' clamped to
+ *            +-1.3 tan(half-FOV) z
+ *   Sigma' = J W Sigma W^T J^T + 0.3 I = [[a, b], [b, c]]; det = a c - b^2
+ *   lambda = mid + sqrt(max(0.1, mid^2 - det)), mid = (a + c) / 2
+ *   r      = ceil(3 sqrt(lambda))
+ *   x0 = floor((ubar - r + cx) / T), x1 = floor((ubar + r + cx) / T) + 1 (same in y),
+ *   and, when `clip` is set, clipped to the bounding box of the ellipse where
+ *   alpha >= 1/255: thr = 2 ln(255 o) 1.001 + 0.001 with o = sigmoid(logit) (not
+ *   visible when thr <= 0), half extents hx = sqrt(thr a), hy = sqrt(thr c),
+ *   x0 = max(x0, floor((ubar - hx + cx) / T)), x1 = min(x1, floor((ubar + hx + cx) / T) + 1);
+ *   clamped to the tile grid; an empty rectangle is not visible.
+ *
+ * Knife edges.  Beside each value that is rounded to an integer or compared
+ * with a threshold, a first-order bound e on how far an FP32 evaluation of
+ * these steps can land from the exact value (Wilkinson's running error
+ * analysis: every operation carries its operands' bounds forward and adds half
+ * an ulp of its own FP32 result; the FP32 exp and log add their ulp bounds;
+ * FP32 constants such as 0.3f carry their own rounding).  An integer output is
+ * returned with the range of values that value +- ORC_KNIFE e can round to, and
+ * vis_amb says whether visibility itself lies within such a window.  A
+ * different FP32 decision outside these ranges is an error, not rounding. */
+
+#define ORC_U32 5.9604644775390625e-08      /* 2^-24: unit roundoff of FP32 */
+#define ORC_KNIFE 2.0                       /* windows are twice the first-order bound */
+
+typedef struct { double v, e; } rb_t;
+
+static rb_t rb_exact(double v) { rb_t r = {v, 0.0}; return r; }
+static rb_t rb_const32(double v) { rb_t r = {v, ORC_U32 * fabs(v)}; return r; }
+static rb_t rb_round(double v, double e) { rb_t r = {v, e + ORC_U32 * fabs(v)}; return r; }
+static rb_t rb_add(rb_t a, rb_t b) { return rb_round(a.v + b.v, a.e + b.e); }
+static rb_t rb_sub(rb_t a, rb_t b) { return rb_round(a.v - b.v, a.e + b.e); }
+static rb_t rb_neg(rb_t a) { rb_t r = {-a.v, a.e}; return r; }
+static rb_t rb_mul(rb_t a, rb_t b)
+{
+    return rb_round(a.v * b.v, fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e);
+}
+static rb_t rb_div(rb_t a, rb_t b)
+{
+    double q = a.v / b.v, den = fabs(b.v) - b.e;
+    return rb_round(q, den > 0.0 ? (a.e + fabs(q) * b.e) / den : INFINITY);
+}
+static rb_t rb_sqrt(rb_t a)
+{
+    double r = a.v > 0.0 ? sqrt(a.v) : 0.0;
+    double lo = a.v - a.e > 0.0 ? sqrt(a.v - a.e) : 0.0;
+    return rb_round(r, r - lo);          /* concave: the downward step is the larger */
+}
+static rb_t rb_maxc(rb_t a, double c)
+{
+    if (a.v - a.e >= c) return a;
+    rb_t r = {a.v > c ? a.v : c, a.v + a.e <= c ? 0.0 : a.e};
+    return r;
+}
+static rb_t rb_clamp(rb_t a, double lim)
+{
+    rb_t r = a;
+    if (a.v > lim) r.v = lim;
+    if (a.v < -lim) r.v = -lim;
+    if (fabs(a.v) - a.e > lim) r.e = 0.0;
+    return r;
+}
+/* exp and log of the decision path: within 2 and 4 ulp of the exact result */
+static rb_t rb_exp(rb_t a)
+{
+    double v = exp(a.v);
+    rb_t r = {v, v * expm1(a.e) + 4.0 * ORC_U32 * v};
+    return r;
+}
+static rb_t rb_log(rb_t a)
+{
+    double v = log(a.v), den = a.v - a.e;
+    rb_t r = {v, (den > 0.0 ? -log1p(-a.e / a.v) : INFINITY) + 8.0 * ORC_U32 * fabs(v) + 1e-12};
+    return r;
+}
+
+typedef struct {
+    int32_t visible, vis_amb;                 /* FP64 decision; 1 = visibility is a knife edge */
+    int32_t radius, r_lo, r_hi;               /* ceil(3 sqrt(lambda)) and its reachable range */
+    int32_t rect[4], rect_lo[4], rect_hi[4];  /* [x0, x1, y0, y1], clamped; reachable ranges */
+    double tz, e_tz, ubar, e_u, vbar, e_v, rho, e_rho, hx, e_hx, hy, e_hy, thr, e_thr, det, e_det;
+} orc_dec64;
+
+static int clampi(double v, int hi) { return v < 0.0 ? 0 : (v > hi ? hi : (int)v); }
+
+static void decide64_one(const float *m, const float *ls, const float *qf, float logit,
+                         const orc_camera *cam, int tile, int clip, orc_dec64 *o, int *status)
+{
+    memset(o, 0, sizeof(*o));
+    int finite = f_isfinite(m[0]) & f_isfinite(m[1]) & f_isfinite(m[2]) & f_isfinite(ls[0]) &
+                 f_isfinite(ls[1]) & f_isfinite(ls[2]) & f_isfinite(qf[0]) & f_isfinite(qf[1]) &
+                 f_isfinite(qf[2]) & f_isfinite(qf[3]) & f_isfinite(logit);
+    if (!finite) { *status |= 2; return; }
+    const int gw = (cam->width + tile - 1) / tile, gh = (cam->height + tile - 1) / tile;
+    /* 3D covariance */
+    rb_t s[3];
+    for (int j = 0; j < 3; ++j) s[j] = rb_exp(rb_exact(ls[j]));
+    rb_t qq = rb_mul(rb_exact(qf[0]), rb_exact(qf[0]));
+    for (int i = 1; i < 4; ++i) qq = rb_add(qq, rb_mul(rb_exact(qf[i]), rb_exact(qf[i])));
+    if (!(qq.v > 0.0)) { *status |= 1; return; }
+    rb_t iq = rb_div(rb_exact(1.0), rb_sqrt(qq));
+    rb_t w = rb_mul(rb_exact(qf[0]), iq), x = rb_mul(rb_exact(qf[1]), iq);
+    rb_t y = rb_mul(rb_exact(qf[2]), iq), z = rb_mul(rb_exact(qf[3]), iq);
+    rb_t one = rb_exact(1.0), two = rb_exact(2.0);
+    rb_t R[9];
+    R[0] = rb_sub(one, rb_mul(two, rb_add(rb_mul(y, y), rb_mul(z, z))));
+    R[1] = rb_mul(two, rb_sub(rb_mul(x, y), rb_mul(w, z)));
+    R[2] = rb_mul(two, rb_add(rb_mul(x, z), rb_mul(w, y)));
+    R[3] = rb_mul(two, rb_add(rb_mul(x, y), rb_mul(w, z)));
+    R[4] = rb_sub(one, rb_mul(two, rb_add(rb_mul(x, x), rb_mul(z, z))));
+    R[5] = rb_mul(two, rb_sub(rb_mul(y, z), rb_mul(w, x)));
+    R[6] = rb_mul(two, rb_sub(rb_mul(x, z), rb_mul(w, y)));
+    R[7] = rb_mul(two, rb_add(rb_mul(y, z), rb_mul(w, x)));
+    R[8] = rb_sub(one, rb_mul(two, rb_add(rb_mul(x, x), rb_mul(y, y))));
+    rb_t M[9], Sig[9];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) M[3 * i + k] = rb_mul(R[3 * i + k], s[k]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            rb_t a = rb_mul(M[3 * i], M[3 * j]);
+            for (int k = 1; k < 3; ++k) a = rb_add(a, rb_mul(M[3 * i + k], M[3 * j + k]));
+            Sig[3 * i + j] = a;
+        }
+    /* camera-space mean */
+    rb_t tc[3];
+    for (int r = 0; r < 3; ++r) {
+        rb_t a = rb_mul(rb_exact(cam->R[3 * r]), rb_exact(m[0]));
+        a = rb_add(a, rb_mul(rb_exact(cam->R[3 * r + 1]), rb_exact(m[1])));
+        a = rb_add(a, rb_mul(rb_exact(cam->R[3 * r + 2]), rb_exact(m[2])));
+        tc[r] = rb_add(a, rb_exact(cam->t[r]));
+    }
+    o->tz = tc[2].v;
+    o->e_tz = tc[2].e;
+    const double zn = cam->znear, wz = ORC_KNIFE * tc[2].e;
+    if (tc[2].v + wz <= zn) return;                         /* certainly behind the near plane */
+    int amb = !(tc[2].v - wz > zn);
+    int vis = tc[2].v > zn;
+    /* Jacobian with the 1.3 x half-FOV guard, T = J W */
+    rb_t iz = rb_div(one, tc[2]);
+    rb_t rx = rb_mul(tc[0], iz), ry = rb_mul(tc[1], iz);
+    rb_t limx = rb_mul(rb_exact(1.3f), rb_exact(cam->tan_fovx));
+    rb_t limy = rb_mul(rb_exact(1.3f), rb_exact(cam->tan_fovy));
+    rb_t cx_ = rb_clamp(rx, limx.v), cy_ = rb_clamp(ry, limy.v);
+    rb_t j00 = rb_mul(rb_exact(cam->fx), iz), j11 = rb_mul(rb_exact(cam->fy), iz);
+    rb_t j02 = rb_neg(rb_mul(j00, cx_)), j12 = rb_neg(rb_mul(j11, cy_));
+    rb_t T[6];
+    for (int k = 0; k < 3; ++k) {
+        T[k] = rb_add(rb_mul(j00, rb_exact(cam->R[k])), rb_mul(j02, rb_exact(cam->R[6 + k])));
+        T[3 + k] = rb_add(rb_mul(j11, rb_exact(cam->R[3 + k])), rb_mul(j12, rb_exact(cam->R[6 + k])));
+    }
+    /* Sigma' = T Sigma T^T + 0.3 I */
+    rb_t TS[6], S2[4];
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 3; ++j) {
+            rb_t v = rb_mul(T[3 * a], Sig[j]);
+            for (int i = 1; i < 3; ++i) v = rb_add(v, rb_mul(T[3 * a + i], Sig[3 * i + j]));
+            TS[3 * a + j] = v;
+        }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            rb_t v = rb_mul(TS[3 * a], T[3 * b]);
+            for (int j = 1; j < 3; ++j) v = rb_add(v, rb_mul(TS[3 * a + j], T[3 * b + j]));
+            S2[2 * a + b] = v;
+        }
+    rb_t dil = rb_const32(0.3);
+    rb_t A = rb_add(S2[0], dil), B = S2[1], C = rb_add(S2[3], dil);
+    rb_t det = rb_sub(rb_mul(A, C), rb_mul(B, B));
+    o->det = det.v;
+    o->e_det = det.e;
+    if (det.v + ORC_KNIFE * det.e <= 0.0) return;
+    amb |= !(det.v - ORC_KNIFE * det.e > 0.0);
+    vis &= det.v > 0.0;
+    rb_t mid = rb_mul(rb_exact(0.5), rb_add(A, C));
+    rb_t disc = rb_maxc(rb_sub(rb_mul(mid, mid), det), 0.1);
+    disc.e += ORC_U32 * 0.1;
+    rb_t lam = rb_add(mid, rb_sqrt(disc));
+    rb_t rho = rb_mul(rb_exact(3.0), rb_sqrt(lam));
+    o->rho = rho.v;
+    o->e_rho = rho.e;
+    const double wr = ORC_KNIFE * rho.e;
+    const double r = ceil(rho.v), r_lo = ceil(rho.v - wr), r_hi = ceil(rho.v + wr);
+    o->radius = (int32_t)r;
+    o->r_lo = (int32_t)r_lo;
+    o->r_hi = (int32_t)r_hi;
+    rb_t ub = rb_mul(rb_exact(cam->fx), rx), vb = rb_mul(rb_exact(cam->fy), ry);
+    o->ubar = ub.v; o->e_u = ub.e;
+    o->vbar = vb.v; o->e_v = vb.e;
+    /* half extents: the 3-sigma radius, or the alpha >= 1/255 box when it is nearer */
+    double hx = INFINITY, hy = INFINITY, whx = 0.0, why = 0.0;
+    if (clip) {
+        rb_t eo = rb_exp(rb_exact(-(double)logit));
+        rb_t op = rb_div(one, rb_add(one, eo));
+        rb_t thr = rb_mul(two, rb_log(rb_mul(rb_exact(255.0), op)));
+        thr = rb_add(rb_mul(thr, rb_const32(1.001)), rb_const32(0.001));
+        o->thr = thr.v;
+        o->e_thr = thr.e;
+        if (thr.v + ORC_KNIFE * thr.e <= 0.0) return;
+        amb |= !(thr.v - ORC_KNIFE * thr.e > 0.0);
+        vis &= thr.v > 0.0;
+        rb_t bx = rb_sqrt(rb_mul(rb_maxc(thr, 0.0), A)), by = rb_sqrt(rb_mul(rb_maxc(thr, 0.0), C));
+        hx = bx.v; whx = ORC_KNIFE * bx.e;
+        hy = by.v; why = ORC_KNIFE * by.e;
+        o->hx = hx; o->e_hx = bx.e;
+        o->hy = hy; o->e_hy = by.e;
+    }
+    /* each bound: floor((centre -+ min(r, h) + principal point) / T); the FP32 edge
+     * is one more rounded subtraction, then an exact floor */
+    const double ctr[2] = {ub.v, vb.v}, wc[2] = {ORC_KNIFE * ub.e, ORC_KNIFE * vb.e};
+    const double h[2] = {hx, hy}, wh[2] = {whx, why}, pp[2] = {cam->cx, cam->cy};
+    const int gsz[2] = {gw, gh};
+    for (int ax = 0; ax < 2; ++ax) {
+        const double e0 = h[ax] < r ? h[ax] : r;                                 /* point */
+        const double e_lo = fmin(r_lo, h[ax] - wh[ax]), e_hi = fmin(r_hi, h[ax] + wh[ax]);
+        const double wround = ORC_KNIFE * ORC_U32 * (fabs(ctr[ax]) + e_hi);
+        const double lo_lo = ctr[ax] - wc[ax] - e_hi - wround, lo_hi = ctr[ax] + wc[ax] - e_lo + wround;
+        const double hi_lo = ctr[ax] - wc[ax] + e_lo - wround, hi_hi = ctr[ax] + wc[ax] + e_hi + wround;
+        const int g = gsz[ax];
+        o->rect[2 * ax] = clampi(floor((ctr[ax] - e0 + pp[ax]) / tile), g);
+        o->rect[2 * ax + 1] = clampi(floor((ctr[ax] + e0 + pp[ax]) / tile) + 1.0, g);
+        o->rect_lo[2 * ax] = clampi(floor((lo_lo + pp[ax]) / tile), g);
+        o->rect_hi[2 * ax] = clampi(floor((lo_hi + pp[ax]) / tile), g);
+        o->rect_lo[2 * ax + 1] = clampi(floor((hi_lo + pp[ax]) / tile) + 1.0, g);
+        o->rect_hi[2 * ax + 1] = clampi(floor((hi_hi + pp[ax]) / tile) + 1.0, g);
+    }
+    const int *rc = o->rect, *lo = o->rect_lo, *hi = o->rect_hi;
+    const int nonempty = rc[1] > rc[0] && rc[3] > rc[2];
+    const int surely = lo[1] > hi[0] && lo[3] > hi[2];
+    const int surely_not = hi[1] <= lo[0] || hi[3] <= lo[2];
+    if (surely_not) vis = 0, amb = 0;
+    else amb |= !surely;
+    vis &= nonempty;
+    if (!vis) memset(o->rect, 0, sizeof(o->rect));
+    o->visible = vis;
+    o->vis_amb = amb;
+}
+
+int orc_decide64(int n, const float *means, const float *log_scales, const float *quats,
+                 const float *logits, const orc_camera *cam, int tile, int clip, orc_dec64 *out)
+{
+    int status = 0;
+#pragma omp parallel for schedule(static) reduction(| : status)
+    for (int g = 0; g < n; ++g) {
+        int st = 0;
+        decide64_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], cam, tile, clip,
+                     out + g, &st);
+        status |= st;
+    }
+    return status;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -96,8 +96,12 @@ extern "C" vrs_status vrs_sort_pairs_noalloc(const uint64_t *keys_in, const uint
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         unsigned long long *dst_k = to_out ? reinterpret_cast<unsigned long long *>(keys_out) : S->keys;
         uint32_t *dst_v = to_out ? vals_out : S->vals;
+        // the last pass sorts only the bits left below key_bits, so that bits above it
+        // (which the caller may leave nonzero) do not reorder pairs with equal sort bits
+        const int left = key_bits - 8 * p;
+        const uint32_t mask = left >= 8 ? 255u : ((1u << left) - 1u);
         SortArgs a{src_k, src_v, dst_k, dst_v, S->counts, S->totals, &S->st,
-                   (unsigned long long)n, 8 * p, G};
+                   (unsigned long long)n, 8 * p, G, mask};
         k_upsweep<<<G, kSortThreads, 0, s>>>(a);
         k_scan_digits<<<kRadix, scan_threads, 0, s>>>(a);
         k_downsweep<<<G, kSortThreads, sizeof(DownSmem), s>>>(a);

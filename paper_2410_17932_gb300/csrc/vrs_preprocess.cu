@@ -77,7 +77,13 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
             for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
         }
         logit = __ldg(p.S.logits + g);
-        const float chk = m[0] + m[1] + m[2] + ls[0] + ls[1] + ls[2] + q[0] + q[1] + q[2] + q[3] + logit;
+        // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so the sum of
+        // those products is finite exactly when every parameter is (a plain sum of the
+        // values could overflow on large finite ones)
+        const float vals[11] = {m[0], m[1], m[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
+        float chk = 0.f;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) chk = __fmaf_rn(vals[i], 0.f, chk);
         if (!isfinite(chk)) ok = false;
     }
     GaussPre pre;
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
                     const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        shs += vv[e];
+                        shs = __fmaf_rn(vv[e], 0.f, shs);     // NaN iff some value is not finite
                         col[(4 * c + e) % 3] += Y[(4 * c + e) / 3] * vv[e];
                     }
                 }
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
                         const float v = __ldg(src + 3 * k + ch);
-                        shs += v;
+                        shs = __fmaf_rn(v, 0.f, shs);
                         col[ch] += Y[k] * v;
                     }
             }

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(const SortArgs a)
     chunk_of(M, blockIdx.x, a.G, b, e);
     const int w = threadIdx.x >> 5;
     for (uint32_t i = b + threadIdx.x; i < e; i += kSortThreads) {
-        const uint32_t d = (uint32_t)(a.keys_in[i] >> a.shift) & 255u;
+        const uint32_t d = (uint32_t)(a.keys_in[i] >> a.shift) & a.digit_mask;
         atomicAdd(&h[w][d], 1u);
     }
     __syncthreads();
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const SortArgs a)
             const bool valid = idx < n;
             kk[i] = valid ? a.keys_in[ts + idx] : 0ull;
             vv[i] = valid ? a.vals_in[ts + idx] : 0u;
-            dg[i] = valid ? ((uint32_t)(kk[i] >> a.shift) & 255u) : (uint32_t)kRadix;
+            dg[i] = valid ? ((uint32_t)(kk[i] >> a.shift) & a.digit_mask) : (uint32_t)kRadix;
         }
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const SortArgs a)
         __syncthreads();
         for (uint32_t j = t; j < n; j += kSortThreads) {
             const unsigned long long key = S.keys[j];
-            const uint32_t d = (uint32_t)(key >> a.shift) & 255u;
+            const uint32_t d = (uint32_t)(key >> a.shift) & a.digit_mask;
             const uint32_t dst = S.gbase[d] + (j - S.dstart[d]);
             a.keys_out[dst] = key;
             a.vals_out[dst] = S.vals[j];
@@ -229,7 +229,7 @@ cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned lon
     uint32_t *vin = vals0, *vout = vals1;
     const int scan_threads = ((G + 31) / 32) * 32;
     for (int p = 0; p < passes; ++p) {
-        SortArgs a{kin, vin, kout, vout, counts, totals, st, cap, 8 * p, G};
+        SortArgs a{kin, vin, kout, vout, counts, totals, st, cap, 8 * p, G, 255u};
         k_upsweep<<<G, kSortThreads, 0, stream>>>(a);
         k_scan_digits<<<kRadix, scan_threads, 0, stream>>>(a);
         k_downsweep<<<G, kSortThreads, sizeof(DownSmem), stream>>>(a);

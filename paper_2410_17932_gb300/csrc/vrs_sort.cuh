@@ -22,6 +22,7 @@ struct SortArgs {
     unsigned long long cap;
     int shift;
     int G;
+    uint32_t digit_mask;  // 255, or fewer bits on a last pass that ends inside a byte
 };
 
 struct DownSmem {

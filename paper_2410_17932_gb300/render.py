@@ -94,10 +94,12 @@ class Rasterizer:
         self.persistent = bool(persistent)
         self.backward = bool(backward)
         self.sort = int(sort)
+        self.generation = 0          # forward passes and re-plans; the autograd glue checks it
         self._make_plan(max_instances)
 
     # -- planning ------------------------------------------------------------------------
     def _make_plan(self, max_instances: int):
+        self.generation = getattr(self, "generation", 0) + 1     # a new workspace: old state is gone
         n_s, n_v = len(self.scenes), len(self.views)
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
@@ -140,6 +142,7 @@ class Rasterizer:
 
     def forward_async(self, stream=None):
         """The whole forward path, stream ordered, no host synchronisation."""
+        self.generation += 1
         self.preprocess(stream)
         self.bin_sort(stream)
         self.render_fwd(stream=stream)
@@ -220,6 +223,35 @@ class Rasterizer:
         ranges = self.ws_view(int(p.off_ranges), 2 * int(p.n_tiles), torch.int32).view(-1, 2)
         return keys, vals, ranges
 
+    def decisions(self, v: int):
+        """The preprocess's integer decisions for view v, read back from the visible-pair
+        list (valid after preprocess, until a backward reuses the list): a uint8 visibility
+        flag per Gaussian of the view's scene and the tile rectangles [n, 4] as
+        (x0, x1, y0, y1), zero where not visible."""
+        p = self.plan
+        sc = int(p.view_scene[v])
+        n = int(p.scene_n[sc])
+        base = 0
+        for s in range(sc):
+            base += int(p.scene_n[s]) * sum(1 for w in range(int(p.n_views)) if int(p.view_scene[w]) == s)
+        vlist = [w for w in range(int(p.n_views)) if int(p.view_scene[w]) == sc]
+        info = L.vrs_run_info()
+        L._check(L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(None)),
+                 "decisions")
+        cnt = min(int(info.visible_pairs[sc]), n * len(vlist))
+        e = self.ws_view(int(p.off_pairs) + 32 * base, 8 * cnt, torch.int32).view(-1, 8)[:, :4]
+        e = e.cpu().numpy().view(np.uint32)
+        sel = e[:, 1] == vlist.index(v)
+        g = e[sel, 0].astype(np.int64)
+        vis = np.zeros(n, np.uint8)
+        rect = np.zeros((n, 4), np.int32)
+        vis[g] = 1
+        rect[g, 0] = e[sel, 2] & 0xffff
+        rect[g, 1] = e[sel, 2] >> 16
+        rect[g, 2] = e[sel, 3] & 0xffff
+        rect[g, 3] = e[sel, 3] >> 16
+        return vis, rect
+
     def records(self) -> torch.Tensor:
         p = self.plan
         return self.ws_view(int(p.off_records), 12 * int(p.n_records), torch.float32).view(-1, 12)
@@ -235,17 +267,28 @@ class VrsRenderFunction(torch.autograd.Function):
 
     forward(ras, *params) -> (rgb, depth, T) packed over views; params are the
     scenes' [means, log_scales, quats, opacity_logits, sh] in scene order.
+
+    The backward reads the rasterizer's workspace (records, sorted lists, last
+    blended positions) and its T, which the next forward overwrites; so one
+    forward per backward: a backward whose rasterizer has run another forward
+    (or was re-planned) since raises instead of returning wrong gradients.
     """
 
     @staticmethod
     def forward(ctx, ras: Rasterizer, *params):
         ras.forward()
         ctx.ras = ras
+        ctx.generation = ras.generation
         return ras.rgb.clone(), ras.depth.clone(), ras.T.clone()
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_T):
         ras = ctx.ras
+        if ras.generation != ctx.generation:
+            raise RuntimeError("the Rasterizer ran another forward pass (or was re-planned) after the one "
+                               "being differentiated; its workspace no longer holds that pass's state. "
+                               "Call backward before the next render(ras), or use one Rasterizer per "
+                               "graph")
         g_rgb = torch.zeros_like(ras.rgb) if g_rgb is None else g_rgb.contiguous()
         g_depth = torch.zeros_like(ras.depth) if g_depth is None else g_depth.contiguous()
         g_T = None if g_T is None else g_T.contiguous()

@@ -10,6 +10,7 @@ T_TOL = 2e-4            # max abs of the final transmittance
 DEPTH_REL = 1e-4        # relative tolerance of the Eq. 1 depth
 DEPTH_ABS = 1e-6        # absolute floor for uncovered pixels
 FLAG_FRAC = 5e-4        # at most 0.05 % knife-edge pixels excluded
+DECISION_FRAC = 1e-4    # at most 0.01 % of Gaussian-views whose decisions differ from FP64 (knife edges)
 
 
 def torch_cuda():

@@ -1,8 +1,13 @@
 """GPU parity of the hand-written backward pass against the CPU oracle's FP64 reverse pass.
 
 The oracle's reverse pass is itself pinned to FP64 central finite differences
-(tests/test_oracle_pins.py).  Bar: per parameter group, the GPU gradient is
-within 1e-3 relative (norm-wise) of the oracle's.
+(tests/test_oracle_pins.py).  Bars, per parameter array: the GPU gradient is
+within 1e-3 relative of the oracle's norm-wise, and element by element
+|g_gpu - g_orc| <= 1e-3 max|g_orc| + 1e-6.  Besides the 64x64 / 200-Gaussian
+subsets, the full training view (1 M SH-3 Gaussians, 1264x832, upstream
+gradients N(0, 1)) is compared whole; the upstream gradient is zeroed on the
+pixels the oracle flags as knife edges (an alpha at 1/255 or a T at the stop
+threshold, where FP32 and FP64 may blend different sets), on both sides.
 """
 import numpy as np
 import pytest
@@ -53,15 +58,31 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+ELEM_REL, ELEM_ABS = 1e-3, 1e-6
+
+
+def _elem(a, b):
+    """Largest element error in units of the element-wise bar (<= 1 passes)."""
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    if b.size == 0:
+        return 0.0
+    return float((np.abs(a - b) / (ELEM_REL * np.abs(b).max() + ELEM_ABS)).max())
+
+
+def _check(got, ref, label):
+    errs = {k: (_rel(got[k], ref[k]), _elem(got[k], ref[k])) for k in NAMES}
+    print(label, "norm-wise / element-wise errors", errs)
+    for k in NAMES:
+        assert errs[k][0] < REL and errs[k][1] <= 1.0, (label, k, errs[k])
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_backward_matches_oracle_reverse(seed):
     sc, cam, gC, gD, gT = _training_subset(seed)
     ras, g = _gpu_grads([sc], [cam], [gC], [gD], [gT])
     ref = oracle.grads(sc, cam, gC, gD, gT)
-    errs = {k: _rel(g[0][k], ref[k]) for k in NAMES}
-    print("rel errors", errs)
-    for k in NAMES:
-        assert errs[k] < REL, (k, errs)
+    _check(g[0], ref, f"subset seed {seed}")
 
 
 def test_backward_record_gradients():
@@ -73,6 +94,7 @@ def test_backward_record_gradients():
     ref = oracle.render_bwd(sc, cam, gC, gD, gT)
     for c in range(10):
         assert _rel(g2[:, c].astype(np.float64), ref[:, c]) < REL, c
+        assert _elem(g2[:, c], ref[:, c]) <= 1.0, c
 
 
 def test_backward_accumulates_over_views_and_no_upstream_T():
@@ -82,16 +104,14 @@ def test_backward_accumulates_over_views_and_no_upstream_T():
     ras, g = _gpu_grads([sc], [cam, cam2], [gC, g2[0]], [gD, g2[1]])
     r1 = oracle.grads(sc, cam, gC, gD, None)
     r2 = oracle.grads(sc, cam2, g2[0], g2[1], None)
-    for k in NAMES:
-        assert _rel(g[0][k], r1[k] + r2[k]) < REL, k
+    _check(g[0], {k: r1[k] + r2[k] for k in NAMES}, "two views")
 
 
 def test_backward_tile_sizes_agree():
     sc, cam, gC, gD, gT = _training_subset(4)
     ref = oracle.grads(sc, cam, gC, gD, gT, tile=8)
     _, g8 = _gpu_grads([sc], [cam], [gC], [gD], [gT], tile=8)
-    for k in NAMES:
-        assert _rel(g8[0][k], ref[k]) < REL, k
+    _check(g8[0], ref, "tile 8")
 
 
 def test_autograd_function():
@@ -105,5 +125,36 @@ def test_autograd_function():
         (depth * torch.as_tensor(gD.reshape(-1), device="cuda")).sum()
     loss.backward()
     ref = oracle.grads(sc, cam, gC, gD, None)
-    for k in NAMES:
-        assert _rel(getattr(st, k).grad.cpu().numpy().astype(np.float64), ref[k]) < REL, k
+    _check({k: getattr(st, k).grad.cpu().numpy() for k in NAMES}, ref, "autograd")
+
+
+def test_training_view_1m_full_size():
+    """The whole 1264x832 training view of 1 M SH-3 Gaussians, in the bench's launch
+    configuration, against the oracle's FP64 reverse pass and chain rule."""
+    scs, cams = I.training_view_1m()
+    sc, cam = scs[0], cams[0]
+    gC, gD = I.upstream_grads([cam], 41)[0]
+    orc = oracle.render(sc, cam)
+    knife = orc["flags"] > 0
+    assert knife.mean() <= 5e-4
+    gC = np.where(knife[None], 0.0, gC).astype(np.float32)
+    gD = np.where(knife, 0.0, gD).astype(np.float32)
+    ras, g = _gpu_grads([sc], [cam], [gC], [gD])
+    ref = oracle.grads(sc, cam, gC, gD, None)
+    _check(g[0], ref, "training_view_1m")
+
+
+def test_autograd_rejects_a_stale_rasterizer():
+    """A second forward through the same Rasterizer before the first graph's backward
+    overwrites the state that backward reads: it must raise, not return wrong grads."""
+    torch = torch_cuda()
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors, render
+    sc, cam, gC, gD, _ = _training_subset(6)
+    st = SceneTensors.from_scene(sc, requires_grad=True)
+    ras = Rasterizer([st], [cam], backward=True)
+    rgb1, _, _ = render(ras)
+    rgb2, _, _ = render(ras)
+    with pytest.raises(RuntimeError, match="another forward"):
+        rgb1.sum().backward()
+    rgb2.sum().backward()                      # the latest pass is still differentiable
+    assert st.means.grad is not None

@@ -160,6 +160,21 @@ def test_device_status_zero_quat_and_nonfinite():
     compare_images((rgb, depth, T), orc, "skipped")
 
 
+def test_large_finite_parameters_are_not_flagged():
+    # a Gaussian whose parameters are all finite is rendered even when a sum of them
+    # would overflow FP32: the check is per value, as the oracle's
+    scs, cams = I.plain_200()
+    sc = scs[0].subset(np.arange(300))
+    sc.quats[5] = [3e38, 3e38, 0.0, 0.0]          # |q|^2 overflows on both sides alike
+    sc.sh[11, 0, :] = 1.5e38                      # a colour row whose sum overflows
+    ras = _run([sc], cams)
+    _, flags, _ = ras.last_status
+    assert flags & 2 == 0
+    d = oracle.decide(sc, cams[0])
+    assert d["status"] & 2 == 0 and d["visible"][11] == 1
+    _check_sort(ras, [sc], cams)
+
+
 def test_capacity_overflow_reported_then_regrown():
     from paper_2410_17932_gb300 import _lib as L
     torch = torch_cuda()

@@ -1,52 +1,58 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times.
 
 The whole sorted instance list and every visible record are compared with the
-oracle; images are compared on sampled tiles (random ones plus the heaviest),
-which the oracle composites one by one.
+oracle, every pixel of every view is compared with the oracle's compositing,
+and the GPU's integer decisions (visibility and tile rectangle of every
+Gaussian-view) are compared with the FP64 decisions taken from the plain
+definition: every difference must be a counted knife edge, at most 0.01 % of
+the Gaussian-views.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2410_17932_gb300 import inputs as I
-from tests.gpu_util import FLAG_FRAC, compare_images, decode_records, make_rasterizer, torch_cuda
+from tests.gpu_util import (DECISION_FRAC, compare_images, decode_records, make_rasterizer,
+                            torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
 
-def _sampled_image_parity(ras, scenes, views, n_random=48, n_heavy=16, seed=0, tile=16):
-    rng = np.random.default_rng(seed)
-    _, _, ranges = ras.sorted_lists()
-    r = ranges.cpu().numpy().astype(np.int64)
-    counts = r[:, 1] - r[:, 0]
+def _whole_frame_parity(ras, scenes, views, label, tile=16, which=None):
+    """Every pixel of each view against the oracle (bucketed traversal, same result as
+    the brute force); returns the worst errors and prints the flagged fraction per view."""
     worst = {}
-    flagged = total = 0
     for v, cam in enumerate(views):
-        sc = scenes[cam.scene]
-        p = ras.plan
-        base = int(p.view_tile_base[v])
-        gw, gh = int(p.view_gw[v]), int(p.view_gh[v])
-        nt = gw * gh
-        c = counts[base:base + nt]
-        pick = set(rng.choice(nt, min(n_random, nt), replace=False).tolist())
-        pick |= set(np.argsort(-c)[:n_heavy].tolist())
-        mask = np.zeros(nt, np.uint8)
-        mask[list(pick)] = 1
-        orc = oracle.render(sc, cam, tile, tile_mask=mask)
+        if which is not None and v not in which:
+            continue
+        orc = oracle.render(scenes[cam.scene], cam, tile)
         rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(v)]
-        pixmask = np.kron(mask.reshape(gh, gw), np.ones((tile, tile), np.uint8))[:cam.height, :cam.width]
-        sel = pixmask.astype(bool)
-        sub = dict(rgb=orc["rgb"][:, sel], depth=orc["depth"][sel], T=orc["T"][sel], flags=orc["flags"][sel])
-        w = compare_images((rgb[:, sel], depth[sel], T[sel]), sub, f"view{v}")
-        flagged += int((sub["flags"] > 0).sum())
-        total += int(sel.sum())
+        w = compare_images((rgb, depth, T), orc, f"{label} view{v}")
+        print(f"{label} view{v} {cam.width}x{cam.height}: flagged {w['flagged']:.2e}, worst {w}")
         for k, val in w.items():
             worst[k] = max(worst.get(k, 0.0), val)
-    assert flagged <= FLAG_FRAC * total
     return worst
 
 
-def _full_checks(scenes, views, **kw):
+def _fp64_decisions(ras, scenes, views, label, which=None):
+    """GPU visibility and tile rectangles against the FP64 decisions of every Gaussian-view."""
+    differs = total = 0
+    for v, cam in enumerate(views):
+        if which is not None and v not in which:
+            continue
+        sc = scenes[cam.scene]
+        vis, rect = ras.decisions(v)
+        d64 = oracle.decide64(sc, cam, ras.tile)
+        mm = oracle.decision_mismatches(d64, vis, rect)
+        bad = np.nonzero(mm["outside"])[0]
+        assert len(bad) == 0, (label, v, bad[:10], rect[bad[:3]], d64[bad[:3]])
+        differs += int(mm["differs"].sum())
+        total += sc.n
+    print(f"{label}: {differs} knife-edge decisions of {total} Gaussian-views differ from FP64")
+    assert differs <= DECISION_FRAC * total
+
+
+def _full_checks(scenes, views, label="full", **kw):
     torch = torch_cuda()
     ras, _ = make_rasterizer(scenes, views, **kw)
     ras.forward()
@@ -55,6 +61,7 @@ def _full_checks(scenes, views, **kw):
     bs = oracle.bin_sort(scenes, views, ras.tile)
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), bs["keys"])
     assert np.array_equal(vals.cpu().numpy().view(np.uint32), bs["vals"])
+    _fp64_decisions(ras, scenes, views, label)
     rec = decode_records(ras.records().cpu().numpy())
     for v, cam in enumerate(views):
         sc = scenes[cam.scene]
@@ -71,8 +78,8 @@ def _full_checks(scenes, views, **kw):
 
 def test_periphery_stereo_05m_full_size():
     scenes, views = I.periphery_stereo_05m()
-    ras = _full_checks(scenes, views)
-    worst = _sampled_image_parity(ras, scenes, views)
+    ras = _full_checks(scenes, views, "periphery_stereo_05m")
+    worst = _whole_frame_parity(ras, scenes, views, "periphery_stereo_05m")
     print("periphery_stereo_05m worst", worst)
 
 
@@ -106,8 +113,8 @@ def test_periphery_stereo_05m_persistent_identical():
 def test_dense_stereo_3m_with_crops():
     torch = torch_cuda()
     scenes, views = I.dense_stereo_3m()
-    ras = _full_checks(scenes, views)
-    worst = _sampled_image_parity(ras, scenes, views, n_random=24, n_heavy=8)
+    ras = _full_checks(scenes, views, "dense_stereo_3m")
+    worst = _whole_frame_parity(ras, scenes, views, "dense_stereo_3m")
     print("dense_stereo_3m worst", worst)
     # each aligned foveal crop equals its window of the eye it was cut from
     for c in (2, 3):
@@ -119,3 +126,15 @@ def test_dense_stereo_3m_with_crops():
         c_rgb, c_d, c_T = ras.outputs(c)
         assert torch.equal(c_rgb, f_rgb[:, y0:y0 + 512, x0:x0 + 512])
         assert torch.equal(c_d, f_d[y0:y0 + 512, x0:x0 + 512])
+
+
+@pytest.mark.slow
+def test_dense_stereo_3m_unaligned_crops():
+    """Crops whose origins are not tile-aligned: a different tile grid over the same
+    pixels; every pixel against the oracle at the crop's own grid."""
+    torch_cuda()
+    scenes, views = I.dense_stereo_3m(aligned=False)
+    ras, _ = make_rasterizer(scenes, views)
+    ras.forward()
+    _fp64_decisions(ras, scenes, views, "dense_stereo_3m crops", which=(2, 3))
+    _whole_frame_parity(ras, scenes, views, "dense_stereo_3m unaligned", which=(2, 3))

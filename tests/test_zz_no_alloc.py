@@ -1,11 +1,12 @@
 """vrs_sort_pairs_noalloc: the radix sort for callers that cannot allocate device memory.
 
-Code inside a CUDA stream capture cannot call cudaMalloc, a real-time frame
-loop must not risk the synchronisation an allocation can cause, and a plug-in
-may live inside a host application's fixed memory budget; this entry point
-sorts with a static device array instead.  The test compares it with the
-library's regular sort (vrs_bin_sort) on the same instance lists, for two
-calls in a row of different sizes, bit for bit as every sort test here does.
+A real-time frame loop must not risk the device-wide synchronisation an
+allocation can cause, and a plug-in may live inside a host application's fixed
+memory budget; this entry point sorts with a static device array instead.  The
+test compares it with the library's regular sort (vrs_bin_sort) on the same
+instance lists, for two calls in a row of different sizes, bit for bit as every
+sort test here does; then with a stable host sort at exactly the size limit and
+with a key width that ends inside a byte while the bits above it are nonzero.
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
@@ -85,3 +86,38 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
         == L.VRS_ERR_INVALID
     assert L.vrs_sort_pairs_noalloc(k.data_ptr(), v.data_ptr(), k2.data_ptr(), v2.data_ptr(), 0, 40, s) \
         == L.VRS_OK
+
+
+def _noalloc_vs_stable_host_sort(n, key_bits, seed):
+    from paper_2410_17932_gb300 import _lib as L
+    torch = torch_cuda()
+    rng = np.random.default_rng(seed)
+    keys = rng.integers(0, np.iinfo(np.int64).max, n, dtype=np.int64)     # high bits set too
+    keys[: n // 4] = keys[n // 4: n // 2]                                  # runs of equal sort bits
+    vals = rng.integers(0, 2**31 - 1, n, dtype=np.int64).astype(np.int32)
+    k_in = torch.as_tensor(keys, device="cuda")
+    v_in = torch.as_tensor(vals, device="cuda")
+    k_out = torch.full_like(k_in, -1)
+    v_out = torch.full_like(v_in, -1)
+    stream = torch.cuda.current_stream().cuda_stream
+    code = L.vrs_sort_pairs_noalloc(k_in.data_ptr(), v_in.data_ptr(), k_out.data_ptr(), v_out.data_ptr(), n,
+                                    key_bits, stream)
+    assert code == L.VRS_OK, L.status_string(code)
+    torch.cuda.synchronize()
+    ku = keys.view(np.uint64)
+    sort_bits = ku & np.uint64((1 << key_bits) - 1) if key_bits < 64 else ku
+    order = np.argsort(sort_bits, kind="stable")
+    assert np.array_equal(k_out.cpu().numpy(), keys[order])
+    assert np.array_equal(v_out.cpu().numpy(), vals[order])
+
+
+def test_noalloc_key_width_inside_a_byte():
+    """key_bits = 12: the second pass sorts 4 bits; bits 12..63 are nonzero and must not
+    reorder pairs whose low 12 bits are equal."""
+    _noalloc_vs_stable_host_sort(200_000, 12, 5)
+    _noalloc_vs_stable_host_sort(70_001, 37, 6)
+
+
+def test_noalloc_at_the_size_limit():
+    from paper_2410_17932_gb300 import _lib as L
+    _noalloc_vs_stable_host_sort(L.VRS_NOALLOC_MAX_PAIRS, 40, 7)
