@@ -884,6 +884,158 @@ void orc_render_bucketed(int n, const uint8_t *visible, const float *depth_key, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Per-pixel depth order: the popping fix of Sec. 3.2, which sorts the Gaussian
+ * contributions per pixel instead of per primitive.  A pixel's candidates are
+ * the same as above (visible, tile rectangle holding the pixel's tile, alpha >=
+ * 1/255 at the pixel); they are ordered by the depth of each Gaussian's 3D
+ * density maximum along the pixel's viewing ray, ties by index, and composited
+ * front to back with the same skip, clamp and stop rules.  With the camera-space
+ * ray r = ((px - cx)/fx, (py - cy)/fy, 1) through the pixel centre, the camera-
+ * space mean mu and covariance Sigma_c = W R S S^T R^T W^T, the density along
+ * the ray, exp(-1/2 (t r - mu)^T Sigma_c^-1 (t r - mu)), is largest at
+ *   t* = r^T Sigma_c^-1 mu / r^T Sigma_c^-1 r,
+ * the camera-space z of that point (r has unit z).  Eq. 1 then accumulates
+ * these per-pixel depths: d_i = t*_i at the pixel.
+ * flags bit 4: two neighbours in the pixel's order (up to the stopping
+ * candidate) whose t* are within tie_win relative of each other. */
+
+typedef struct { double P[6]; double Pm[3]; } orc_raydepth;   /* Sigma_c^-1 (xx xy xz yy yz zz), Sigma_c^-1 mu */
+
+void orc_raydepth_setup(int n, const float *means, const float *log_scales, const float *quats,
+                        const orc_camera *cam, orc_raydepth *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < n; ++g) {
+        const float *m = means + 3 * g, *ls = log_scales + 3 * g, *qf = quats + 4 * g;
+        double q[4] = {qf[0], qf[1], qf[2], qf[3]};
+        double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        orc_raydepth *o = out + g;
+        memset(o, 0, sizeof(*o));
+        if (!(qn > 0.0)) continue;
+        for (int i = 0; i < 4; ++i) q[i] /= qn;
+        double Rq[9];
+        quat_to_rot(q, Rq);
+        double W[9];
+        for (int i = 0; i < 9; ++i) W[i] = cam->R[i];
+        /* camera-space axes e_k = W R_k; Sigma_c^-1 = sum_k e_k e_k^T / s_k^2 */
+        double Pm[9] = {0};
+        for (int k = 0; k < 3; ++k) {
+            double e[3];
+            for (int i = 0; i < 3; ++i) e[i] = W[3 * i] * Rq[k] + W[3 * i + 1] * Rq[3 + k] + W[3 * i + 2] * Rq[6 + k];
+            double is2 = exp(-2.0 * (double)ls[k]);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Pm[3 * i + j] += e[i] * e[j] * is2;
+        }
+        double mu[3];
+        for (int r = 0; r < 3; ++r)
+            mu[r] = W[3 * r] * m[0] + W[3 * r + 1] * m[1] + W[3 * r + 2] * m[2] + cam->t[r];
+        o->P[0] = Pm[0]; o->P[1] = Pm[1]; o->P[2] = Pm[2]; o->P[3] = Pm[4]; o->P[4] = Pm[5]; o->P[5] = Pm[8];
+        for (int i = 0; i < 3; ++i) o->Pm[i] = Pm[3 * i] * mu[0] + Pm[3 * i + 1] * mu[1] + Pm[3 * i + 2] * mu[2];
+    }
+}
+
+static double ray_depth(const orc_raydepth *g, double rx, double ry)
+{
+    const double *P = g->P;
+    double num = rx * g->Pm[0] + ry * g->Pm[1] + g->Pm[2];
+    double den = P[0] * rx * rx + 2.0 * P[1] * rx * ry + 2.0 * P[2] * rx + P[3] * ry * ry + 2.0 * P[4] * ry + P[5];
+    return num / den;
+}
+
+typedef struct { double t; int32_t idx; double alpha; } pix_cand_t;
+
+static int pix_cand_cmp(const void *pa, const void *pb)
+{
+    const pix_cand_t *a = (const pix_cand_t *)pa, *b = (const pix_cand_t *)pb;
+    if (a->t != b->t) return a->t < b->t ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+static void composite_pixel_resort(const cand_t *cands, int nc, const orc_proj *P, const orc_raydepth *RD,
+                                   double pxc, double pyc, double rx, double ry, const orc_flag_opts *fo,
+                                   double tie_win, pix_cand_t *buf, double *rgb, double *dep, double *Tout,
+                                   uint8_t *flag_out, int32_t *nblend_out)
+{
+    uint8_t flag = 0;
+    int m = 0;
+    for (int p = 0; p < nc; ++p) {
+        const int gi = cands[p].idx;
+        const orc_proj *g = P + gi;
+        double dx = g->ubar - pxc, dy = g->vbar - pyc;
+        double power = -0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) - g->conic[1] * dx * dy;
+        if (power > 0.0) continue;
+        double raw = g->opacity * exp(power);
+        if (fabs(raw * 255.0 - 1.0) < fo->alpha_win) flag |= 1;
+        double alpha = raw < 0.99 ? raw : 0.99;
+        if (alpha < 1.0 / 255.0) continue;
+        buf[m].t = ray_depth(RD + gi, rx, ry);
+        buf[m].idx = gi;
+        buf[m].alpha = alpha;
+        ++m;
+    }
+    qsort(buf, m, sizeof(pix_cand_t), pix_cand_cmp);
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
+    int nb = 0;
+    for (int k = 0; k < m; ++k) {
+        if (k > 0 && fabs(buf[k].t - buf[k - 1].t) <= tie_win * fmax(fabs(buf[k].t), fabs(buf[k - 1].t)))
+            flag |= 4;
+        const orc_proj *g = P + buf[k].idx;
+        double alpha = buf[k].alpha;
+        double Tn = T * (1.0 - alpha);
+        if (fabs(Tn * 1e4 - 1.0) < fo->t_win) flag |= 2;
+        if (Tn < 1e-4) break;
+        double w = alpha * T;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * w;
+        D += buf[k].t * w;
+        T = Tn;
+        ++nb;
+    }
+    rgb[0] = C[0]; rgb[1] = C[1]; rgb[2] = C[2];
+    *dep = D;
+    *Tout = T;
+    *flag_out = flag;
+    *nblend_out = nb;
+}
+
+void orc_render_resort(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
+                       const orc_proj *P, const orc_raydepth *RD, const orc_camera *cam, int tile,
+                       const orc_flag_opts *fo, double tie_win, const uint8_t *tile_mask, double *rgb,
+                       double *depth, double *Tfin, uint8_t *flags, int32_t *nblend)
+{
+    const int W = cam->width, H = cam->height;
+    const size_t HW = (size_t)W * H;
+    const int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
+    tile_lists L;
+    build_tile_lists(n, visible, depth_key, rect, gw, gh, &L);
+    int maxc = 1;
+    for (int t = 0; t < gw * gh; ++t) if (L.count[t] > maxc) maxc = L.count[t];
+#pragma omp parallel
+    {
+        pix_cand_t *buf = (pix_cand_t *)malloc(sizeof(pix_cand_t) * (size_t)maxc);
+#pragma omp for schedule(dynamic, 1)
+        for (int t = 0; t < gw * gh; ++t) {
+            if (tile_mask && !tile_mask[t]) continue;
+            int tx = t % gw, ty = t / gw;
+            for (int j = ty * tile; j < (ty + 1) * tile && j < H; ++j)
+                for (int i = tx * tile; i < (tx + 1) * tile && i < W; ++i) {
+                    double c3[3], d, T;
+                    uint8_t fl;
+                    int32_t nb;
+                    const double pxc = i + 0.5 - cam->cx, pyc = j + 0.5 - cam->cy;
+                    composite_pixel_resort(L.items + L.start[t], L.count[t], P, RD, pxc, pyc,
+                                           pxc / cam->fx, pyc / cam->fy, fo, tie_win, buf, c3, &d, &T,
+                                           &fl, &nb);
+                    size_t pix = (size_t)j * W + i;
+                    rgb[pix] = c3[0]; rgb[HW + pix] = c3[1]; rgb[2 * HW + pix] = c3[2];
+                    depth[pix] = d; Tfin[pix] = T; flags[pix] = fl; nblend[pix] = nb;
+                }
+        }
+        free(buf);
+    }
+    free_tile_lists(&L);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Reverse pass.  For each pixel the forward list is recomputed; with
  * w_i = alpha_i T_i, T_i = prod_{m<i} (1 - alpha_m) (a prefix product, no
  * division), and the explicit suffix sums S_C,i = sum_{j>i} rgb_j w_j,

@@ -90,13 +90,18 @@ __device__ __forceinline__ void pixel_adjoint2(PixState2 &p, float2 u, bool c0, 
     g[5] = __ffma2_rn(dLda, make_float2(ex2_approx(-(u.x + B.y)), ex2_approx(-(u.y + B.y))), g[5]);   // d alpha / d opacity = 2^-q'
     const float l0 = A.z, l1 = A.w, l2 = B.x;
     const float2 t = __ffma2_rn(f2(l0), dx, f2(l1 * dy));
+    // w = Sigma'^-1 d = (l0 t, l1 t + l2^2 dy) / kCholScale^2, the conic applied to the offset
+    const float2 wx = __fmul2_rn(f2(l0), t), wy = __ffma2_rn(f2(l1), t, f2(l2 * l2 * dy));
     const float2 ndp = __fmul2_rn(dLdp, f2(-kInvChol2));
-    g[0] = __ffma2_rn(ndp, __fmul2_rn(f2(l0), t), g[0]);                                   // -(a dx + b dy)
-    g[1] = __ffma2_rn(ndp, __ffma2_rn(f2(l1), t, f2(l2 * l2 * dy)), g[1]);                 // -(c dy + b dx)
-    const float2 hdp = __fmul2_rn(dLdp, f2(-0.5f));
-    g[2] = __ffma2_rn(hdp, __fmul2_rn(dx, dx), g[2]);
-    g[3] = __ffma2_rn(__fmul2_rn(dLdp, f2(-1.f)), __fmul2_rn(dx, f2(dy)), g[3]);
-    g[4] = __ffma2_rn(hdp, f2(dy * dy), g[4]);
+    g[0] = __ffma2_rn(ndp, wx, g[0]);                                   // -(a dx + b dy)
+    g[1] = __ffma2_rn(ndp, wy, g[1]);                                   // -(c dy + b dx)
+    // d power / d Sigma' = w w^T / 2: the gradient of the 2D covariance [[A, B], [B, C]]
+    // itself (B one variable), a sum of bounded terms; the gradient of the conic would
+    // cancel by orders of magnitude on the way back to Sigma' for elongated splats
+    const float2 hdp = __fmul2_rn(dLdp, f2(0.5f * kInvChol2 * kInvChol2));
+    g[2] = __ffma2_rn(hdp, __fmul2_rn(wx, wx), g[2]);
+    g[3] = __ffma2_rn(__fmul2_rn(hdp, f2(2.f)), __fmul2_rn(wx, wy), g[3]);
+    g[4] = __ffma2_rn(hdp, __fmul2_rn(wy, wy), g[4]);
 }
 
 constexpr int kGroup = 3;     // splats whose gradients are reduced together (3 x 10 rows <= 32 lanes)
@@ -397,13 +402,9 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
         float dtx = G[0] * V.fx * iz;
         float dty = G[1] * V.fy * iz;
         float dtz = G[9] - (G[0] * V.fx * tx + G[1] * V.fy * ty) * iz2;
-        // conic = adj(Sigma') / det with Sigma' = [[A, B], [B, C]] = V V^T + 0.3 I
-        const float A = d.n0 + 0.3f, Bc = d.b, C = d.n1 + 0.3f, det = d.det;
-        const float idet2 = 1.0f / (det * det);
-        const float gA = (-C * C * G[2] + Bc * C * G[3] - Bc * Bc * G[4]) * idet2;
-        const float gB = (2.f * Bc * C * G[2] - (A * C + Bc * Bc) * G[3] + 2.f * A * Bc * G[4]) * idet2;
-        const float gC = (-Bc * Bc * G[2] + A * Bc * G[3] - A * A * G[4]) * idet2;
+        // the record holds dL/d of Sigma' = [[A, B], [B, C]] = V V^T + 0.3 I directly:
         // A = v0.v0 + .3, B = v0.v1, C = v1.v1 + .3 with V = T M
+        const float gA = G[2], gB = G[3], gC = G[4];
         float gV0[3], gV1[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {

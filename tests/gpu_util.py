@@ -54,3 +54,21 @@ def compare_images(gpu, orc, label=""):
     assert e_T.max(initial=0) <= T_TOL, (label, worst)
     assert np.all(e_d <= tol_d), (label, worst)
     return worst
+
+
+def record_grads_wrt_sigma(g2: np.ndarray, conic: np.ndarray) -> np.ndarray:
+    """The oracle's 2D gradients [n, 10] with columns 2..4 taken from the conic (a, b, c)
+    to the 2D covariance Sigma' = [[A, B], [B, C]] (B one variable), the form the GPU
+    records hold: dL/dSigma' = -C G C with C the conic and G = [[g_a, g_b/2], [g_b/2, g_c]]
+    (in FP64)."""
+    out = np.array(g2, np.float64, copy=True)
+    a, b, c = conic[:, 0], conic[:, 1], conic[:, 2]
+    ga, gb, gc = g2[:, 2], 0.5 * g2[:, 3], g2[:, 4]
+    # H = -C G C, C = [[a, b], [b, c]]
+    cg00, cg01 = a * ga + b * gb, a * gb + b * gc
+    cg10, cg11 = b * ga + c * gb, b * gb + c * gc
+    h00 = -(cg00 * a + cg01 * b)
+    h01 = -(cg00 * b + cg01 * c)
+    h11 = -(cg10 * b + cg11 * c)
+    out[:, 2], out[:, 3], out[:, 4] = h00, 2.0 * h01, h11
+    return out

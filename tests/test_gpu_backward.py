@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from paper_2410_17932_gb300 import inputs as I
-from tests.gpu_util import make_rasterizer, torch_cuda
+from tests.gpu_util import make_rasterizer, record_grads_wrt_sigma, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +91,7 @@ def test_backward_record_gradients():
     ras, _ = _gpu_grads([sc], [cam], [gC], [gD], [gT])
     p = ras.plan
     g2 = ras.ws_view(int(p.off_grad2d), 10 * int(p.n_records), torch.float32).view(-1, 10).cpu().numpy()
-    ref = oracle.render_bwd(sc, cam, gC, gD, gT)
+    ref = record_grads_wrt_sigma(oracle.render_bwd(sc, cam, gC, gD, gT), oracle.project(sc, cam)["conic"])
     for c in range(10):
         assert _rel(g2[:, c].astype(np.float64), ref[:, c]) < REL, c
         assert _elem(g2[:, c], ref[:, c]) <= 1.0, c
