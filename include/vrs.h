@@ -115,7 +115,10 @@ typedef struct {
     int64_t max_instances; /* capacity of the (tile, Gaussian) instance list; 0 = 4 x records + 65536 */
     int32_t count_pairs;   /* 1 = vrs_render_fwd also counts the Gaussian-pixel pairs it evaluated
                               and blended into the status block (a slower, measuring variant) */
-    int32_t reserved;
+    int32_t resort;        /* 0 = every pixel blends its tile's list in the list's depth order;
+                              4, 8 or 16 = per-pixel depth order (the popping fix of Sec. 3.2)
+                              through a sorting window of that many splats per pixel (see
+                              vrs_render_fwd); forward only (backward must be 0) */
 } vrs_plan_opts;
 
 /* Sizes and workspace layout, filled by vrs_plan_batch.  Treat as read-only. */
@@ -163,6 +166,12 @@ typedef struct {
     int64_t view_rec_base[VRS_MAX_VIEWS];   /* record index of (view v, Gaussian g) = view_rec_base[v] + g */
     int64_t view_tile_base[VRS_MAX_VIEWS];  /* global tile id = view_tile_base[v] + ty * gw + tx */
     int64_t view_pix_base[VRS_MAX_VIEWS];   /* view v's pixels start at element view_pix_base[v] */
+    int32_t resort;            /* vrs_plan_opts.resort */
+    int32_t reserved;
+    int64_t off_raydepth;      /* resort plans: [n_records][3] float4, per record the terms of the
+                                  per-pixel depth (see vrs_render_fwd); 0 otherwise */
+    int64_t off_resort_flags;  /* resort plans: [n_pixels] uint8, 1 where the pixel's sorting
+                                  window could not restore the per-pixel order; 0 otherwise */
 } vrs_plan;
 
 /* Device status block, copied to the host by vrs_query_status. */
@@ -182,6 +191,8 @@ typedef struct {
                                   Gaussian-pixel evaluations) */
     uint64_t visible_pairs[VRS_MAX_SCENES]; /* (Gaussian, view) pairs of each scene that the last
                                   vrs_preprocess found visible (one 48-byte record each) */
+    uint64_t resort_flagged;   /* resort plans: pixels whose sorting window overflowed in the last
+                                  vrs_render_fwd (their flag is set in the resort flag plane) */
 } vrs_run_info;
 
 /* Sizes a batch of n_views views over n_scenes scenes and lays out the
@@ -221,6 +232,24 @@ vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
  * front to back over its tile's sorted list: alpha = min(0.99, o exp(power)),
  * skipped below 1/255; the pixel stops before a splat that would bring T under
  * 1e-4; otherwise C += rgb alpha T, D += z alpha T, T *= 1 - alpha.
+ *
+ * Per-pixel order (plans with resort = K; the popping fix of Sec. 3.2, which
+ * sorts Gaussian contributions per pixel instead of per primitive).  Each pixel
+ * orders the splats it blends by the depth of each 3D Gaussian's density
+ * maximum along the pixel's ray, t* = r^T Sigma_c^-1 mu / r^T Sigma_c^-1 r with
+ * r = ((x - cx)/fx, (y - cy)/fy, 1) (ties by record index), and Eq. 1 takes
+ * d_i = t* at the pixel.  In these plans vrs_preprocess keys each instance by
+ * t* at its tile's centre (moved into the splat's alpha >= 1/255 box where the
+ * centre lies outside it) instead of by the mean's depth, so the tile list
+ * arrives in an order close to every pixel's own; every pixel
+ * keeps the K nearest splats it has not blended yet in a window in shared
+ * memory and blends the nearest one whenever the window is full.  A splat that
+ * arrives nearer than one the pixel has already blended (or than the one it
+ * stopped at) breaks the per-pixel order: the pixel's byte in the resort flag
+ * plane (workspace + plan.off_resort_flags) is set to 1 and
+ * vrs_run_info.resort_flagged counts it.  Unflagged pixels are blended exactly
+ * in per-pixel order.  The per-tile early exit is not taken in this mode, so
+ * that every splat is checked.
  * Outputs (device, float32, written for every pixel of every view):
  *   rgb     [3][H][W] per view, view v at rgb + 3 * plan.view_pix_base[v]
  *   depth   [H][W] per view at depth + plan.view_pix_base[v]   (Eq. 1, not normalised)

@@ -108,7 +108,7 @@ def lib():
             L.orc_raydepth_setup.argtypes = [ctypes.c_int, P, P, P, ctypes.POINTER(OrcCamera), P]
             L.orc_render_resort.restype = None
             L.orc_render_resort.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(OrcCamera), ctypes.c_int,
-                                            ctypes.POINTER(OrcFlagOpts), ctypes.c_double, P, P, P, P, P, P]
+                                            ctypes.POINTER(OrcFlagOpts), ctypes.c_double, P, P, P, P, P, P, P]
             L.orc_render_bwd.restype = None
             L.orc_render_bwd.argtypes = [ctypes.c_int, P, P, P, P, ctypes.POINTER(OrcCamera),
                                          ctypes.c_int, P, P, P, P]
@@ -303,7 +303,7 @@ def render(scene, cam, tile: int = 16, mode: str = "bucketed", dec=None, proj=No
     return out
 
 
-TIE_WIN = 2e-5       # relative window of two per-pixel depths that marks a near tie
+TIE_WIN = 4e-6       # relative window of two per-pixel depths that marks a near tie
 
 
 RAYDEPTH_DTYPE = np.dtype([("P", "f8", 6), ("Pm", "f8", 3)])
@@ -322,21 +322,23 @@ def raydepth(scene, cam) -> np.ndarray:
 def render_resort(scene, cam, tile: int = 16, dec=None, proj=None, tile_mask: Optional[np.ndarray] = None,
                   alpha_win: float = ALPHA_WIN, t_win: float = T_WIN, tie_win: float = TIE_WIN):
     """Per-pixel depth order (Sec. 3.2 popping fix): RGB [3,H,W], Eq. 1 depth of the per-pixel
-    depths [H,W], final T [H,W], knife-edge flags (bit 1 alpha, bit 2 T, bit 4 near-tied depths)
-    and the number of blended splats per pixel."""
+    depths [H,W], final T [H,W], knife-edge flags (bit 1 alpha, bit 2 T, bit 4 a run of near-tied
+    depths, bit 8 such a run at the stopping candidate), the number of blended splats per pixel
+    and `tie_bound` [H,W], the most any order of the near-tied runs can move a colour channel."""
     dec = decide(scene, cam, tile) if dec is None else dec
     proj = project(scene, cam) if proj is None else proj
     rd = raydepth(scene, cam)
     H, W = cam.height, cam.width
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), T=np.ones((H, W)),
-               flags=np.zeros((H, W), np.uint8), n_blend=np.zeros((H, W), np.int32))
+               flags=np.zeros((H, W), np.uint8), n_blend=np.zeros((H, W), np.int32),
+               tie_bound=np.zeros((H, W)))
     c = camera(cam)
     fo = OrcFlagOpts(alpha_win, t_win)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     lib().orc_render_resort(scene.n, _p(dec["visible"]), _p(dec["depth"]), _p(dec["rect"]), _p(proj), _p(rd),
                             ctypes.byref(c), tile, ctypes.byref(fo), float(tie_win),
                             None if tm is None else _p(tm), _p(out["rgb"]), _p(out["depth"]), _p(out["T"]),
-                            _p(out["flags"]), _p(out["n_blend"]))
+                            _p(out["flags"]), _p(out["n_blend"]), _p(out["tie_bound"]))
     return out
 
 

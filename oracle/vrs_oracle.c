@@ -896,8 +896,14 @@ void orc_render_bucketed(int n, const uint8_t *visible, const float *depth_key, 
  *   t* = r^T Sigma_c^-1 mu / r^T Sigma_c^-1 r,
  * the camera-space z of that point (r has unit z).  Eq. 1 then accumulates
  * these per-pixel depths: d_i = t*_i at the pixel.
- * flags bit 4: two neighbours in the pixel's order (up to the stopping
- * candidate) whose t* are within tie_win relative of each other. */
+ * Near ties.  Neighbours in the order whose t* lie within tie_win relative of
+ * each other form a run; an evaluation of t* in lower precision may order a
+ * run differently.  Reordering a run does not change its total weight
+ * T_start (1 - prod (1 - alpha)), so the colour can move by at most that
+ * weight times the run's colour range (and the depth by the weight times its
+ * t* range): tie_bound sums the colour bound over the runs.  flags bit 4: the
+ * pixel has such a run; bit 8: a run reaches the candidate at which the pixel
+ * stops, where another order may stop elsewhere. */
 
 typedef struct { double P[6]; double Pm[3]; } orc_raydepth;   /* Sigma_c^-1 (xx xy xz yy yz zz), Sigma_c^-1 mu */
 
@@ -954,7 +960,7 @@ static int pix_cand_cmp(const void *pa, const void *pb)
 static void composite_pixel_resort(const cand_t *cands, int nc, const orc_proj *P, const orc_raydepth *RD,
                                    double pxc, double pyc, double rx, double ry, const orc_flag_opts *fo,
                                    double tie_win, pix_cand_t *buf, double *rgb, double *dep, double *Tout,
-                                   uint8_t *flag_out, int32_t *nblend_out)
+                                   uint8_t *flag_out, int32_t *nblend_out, double *tie_out)
 {
     uint8_t flag = 0;
     int m = 0;
@@ -975,32 +981,59 @@ static void composite_pixel_resort(const cand_t *cands, int nc, const orc_proj *
     }
     qsort(buf, m, sizeof(pix_cand_t), pix_cand_cmp);
     double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
-    int nb = 0;
+    int nb = 0, stop = -1;
     for (int k = 0; k < m; ++k) {
-        if (k > 0 && fabs(buf[k].t - buf[k - 1].t) <= tie_win * fmax(fabs(buf[k].t), fabs(buf[k - 1].t)))
-            flag |= 4;
         const orc_proj *g = P + buf[k].idx;
         double alpha = buf[k].alpha;
         double Tn = T * (1.0 - alpha);
         if (fabs(Tn * 1e4 - 1.0) < fo->t_win) flag |= 2;
-        if (Tn < 1e-4) break;
+        if (Tn < 1e-4) { stop = k; break; }
         double w = alpha * T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * w;
         D += buf[k].t * w;
         T = Tn;
         ++nb;
     }
+    /* runs of near-tied neighbours among the blended candidates and the stopping one */
+    const int last = stop >= 0 ? stop : nb - 1;
+    double tie = 0.0, Tr = 1.0;
+    int k = 0;
+    while (k <= last) {
+        int e = k;
+        while (e < last && fabs(buf[e + 1].t - buf[e].t) <= tie_win * fmax(fabs(buf[e + 1].t), fabs(buf[e].t)))
+            ++e;
+        double keep = 1.0, lo[3], hi[3];
+        for (int ch = 0; ch < 3; ++ch) lo[ch] = hi[ch] = P[buf[k].idx].rgb[ch];
+        for (int j = k; j <= e; ++j) {
+            if (j < nb) keep *= 1.0 - buf[j].alpha;
+            for (int ch = 0; ch < 3; ++ch) {
+                double c = P[buf[j].idx].rgb[ch];
+                lo[ch] = c < lo[ch] ? c : lo[ch];
+                hi[ch] = c > hi[ch] ? c : hi[ch];
+            }
+        }
+        if (e > k) {
+            flag |= 4;
+            if (e == stop) flag |= 8;
+            double range = 0.0;
+            for (int ch = 0; ch < 3; ++ch) range = hi[ch] - lo[ch] > range ? hi[ch] - lo[ch] : range;
+            tie += Tr * (1.0 - keep) * range;
+        }
+        Tr *= keep;
+        k = e + 1;
+    }
     rgb[0] = C[0]; rgb[1] = C[1]; rgb[2] = C[2];
     *dep = D;
     *Tout = T;
     *flag_out = flag;
     *nblend_out = nb;
+    *tie_out = tie;
 }
 
 void orc_render_resort(int n, const uint8_t *visible, const float *depth_key, const int32_t *rect,
                        const orc_proj *P, const orc_raydepth *RD, const orc_camera *cam, int tile,
                        const orc_flag_opts *fo, double tie_win, const uint8_t *tile_mask, double *rgb,
-                       double *depth, double *Tfin, uint8_t *flags, int32_t *nblend)
+                       double *depth, double *Tfin, uint8_t *flags, int32_t *nblend, double *tie_bound)
 {
     const int W = cam->width, H = cam->height;
     const size_t HW = (size_t)W * H;
@@ -1021,13 +1054,14 @@ void orc_render_resort(int n, const uint8_t *visible, const float *depth_key, co
                     double c3[3], d, T;
                     uint8_t fl;
                     int32_t nb;
+                    double tb;
                     const double pxc = i + 0.5 - cam->cx, pyc = j + 0.5 - cam->cy;
                     composite_pixel_resort(L.items + L.start[t], L.count[t], P, RD, pxc, pyc,
                                            pxc / cam->fx, pyc / cam->fy, fo, tie_win, buf, c3, &d, &T,
-                                           &fl, &nb);
+                                           &fl, &nb, &tb);
                     size_t pix = (size_t)j * W + i;
                     rgb[pix] = c3[0]; rgb[HW + pix] = c3[1]; rgb[2 * HW + pix] = c3[2];
-                    depth[pix] = d; Tfin[pix] = T; flags[pix] = fl; nblend[pix] = nb;
+                    depth[pix] = d; Tfin[pix] = T; flags[pix] = fl; nblend[pix] = nb; tie_bound[pix] = tb;
                 }
         }
         free(buf);

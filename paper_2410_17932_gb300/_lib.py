@@ -38,7 +38,7 @@ class vrs_camera(ctypes.Structure):
 
 class vrs_plan_opts(ctypes.Structure):
     _fields_ = [("tile", _i32), ("persistent", _i32), ("backward", _i32), ("sort", _i32),
-                ("max_instances", _i64), ("count_pairs", _i32), ("reserved", _i32)]
+                ("max_instances", _i64), ("count_pairs", _i32), ("resort", _i32)]
 
 
 class vrs_plan(ctypes.Structure):
@@ -55,12 +55,14 @@ class vrs_plan(ctypes.Structure):
                 ("view_scene", _i32 * VRS_MAX_VIEWS), ("view_w", _i32 * VRS_MAX_VIEWS),
                 ("view_h", _i32 * VRS_MAX_VIEWS), ("view_gw", _i32 * VRS_MAX_VIEWS),
                 ("view_gh", _i32 * VRS_MAX_VIEWS), ("view_rec_base", _i64 * VRS_MAX_VIEWS),
-                ("view_tile_base", _i64 * VRS_MAX_VIEWS), ("view_pix_base", _i64 * VRS_MAX_VIEWS)]
+                ("view_tile_base", _i64 * VRS_MAX_VIEWS), ("view_pix_base", _i64 * VRS_MAX_VIEWS),
+                ("resort", _i32), ("reserved", _i32), ("off_raydepth", _i64), ("off_resort_flags", _i64)]
 
 
 class vrs_run_info(ctypes.Structure):
     _fields_ = [("flags", _u32), ("reserved", _u32), ("instances", _u64), ("pair_evals", _u64),
-                ("pair_blends", _u64), ("block_evals", _u64), ("visible_pairs", _u64 * VRS_MAX_SCENES)]
+                ("pair_blends", _u64), ("block_evals", _u64), ("visible_pairs", _u64 * VRS_MAX_SCENES),
+                ("resort_flagged", _u64)]
 
 
 class vrs_combine_opts(ctypes.Structure):

@@ -7,7 +7,8 @@ namespace vrs {
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              float4 *viewtab, int64_t zero_tiles, int n_sms, cudaStream_t stream);
+                              float4 *viewtab, int64_t zero_tiles, float4 *raydepth, int n_sms,
+                              cudaStream_t stream);
 cudaError_t launch_sort(unsigned long long *keys0, uint32_t *vals0, unsigned long long *keys1,
                         uint32_t *vals1, uint32_t *counts, uint32_t *totals, uint2 *ranges,
                         int64_t n_tiles, const DevStatus *st, unsigned long long cap, int passes, int G,
@@ -23,6 +24,11 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
                               unsigned long long cap, int persistent, int count, int n_sms,
                               cudaStream_t s);
+cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
+                                 const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
+                                 DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
+                                 int64_t n_tiles, int64_t n_records, unsigned long long cap, int window,
+                                 cudaStream_t s);
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
@@ -143,6 +149,8 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     if (tile != 8 && tile != 16 && tile != 32) return VRS_ERR_INVALID;
     if (o.max_instances < 0) return VRS_ERR_INVALID;
     if (o.sort != 0 && o.sort != 1) return VRS_ERR_INVALID;
+    if (o.resort != 0 && o.resort != 4 && o.resort != 8 && o.resort != 16) return VRS_ERR_INVALID;
+    if (o.resort && (o.backward || (tile == 32 && o.resort > 8))) return VRS_ERR_INVALID;
     vrs_plan P;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
@@ -152,6 +160,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.backward = o.backward ? 1 : 0;
     P.sort_mode = o.sort;
     P.count_pairs = o.count_pairs ? 1 : 0;
+    P.resort = o.resort;
     for (int s = 0; s < n_scenes; ++s) {
         if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
         P.scene_n[s] = scenes[s].n;
@@ -212,6 +221,8 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.off_grad2d = P.backward ? take(rec * kGrad2D * 4) : 0;
     P.off_tilesort = take((3 * tiles + (tiles + 1023) / 1024) * 4);
     P.off_pairs = take(rec * 32);
+    P.off_raydepth = P.resort ? take(rec * 3 * 16) : 0;
+    P.off_resort_flags = P.resort ? take(pix) : 0;
     P.workspace_bytes = off;
     *plan = P;
     return VRS_OK;
@@ -260,7 +271,8 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
                               at<unsigned long long>(workspace, plan->off_keys[0]),
                               at<uint32_t>(workspace, plan->off_vals[0]), tile_cnt, st,
                               (unsigned long long)plan->max_instances, viewtab,
-                              sc == first ? plan->n_tiles : 0, plan->n_sms, s);
+                              sc == first ? plan->n_tiles : 0,
+                              plan->resort ? at<float4>(workspace, plan->off_raydepth) : nullptr, plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
         pair_base += (int64_t)plan->scene_n[sc] * nv;
     }
@@ -301,6 +313,14 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
     ViewTable vt;
     fill_sizes(plan, vt);
     const int sb = plan->sorted_buf;
+    if (plan->resort) {
+        return cuda_status(launch_render_resort(
+            vt, at<float4>(workspace, plan->off_status + 256), at<float4>(workspace, plan->off_records),
+            at<float4>(workspace, plan->off_raydepth), at<uint32_t>(workspace, plan->off_vals[sb]),
+            at<uint2>(workspace, plan->off_ranges), at<DevStatus>(workspace, plan->off_status), rgb, depth,
+            T_final, at<uint8_t>(workspace, plan->off_resort_flags), plan->n_tiles, plan->n_records,
+            (unsigned long long)plan->max_instances, plan->resort, static_cast<cudaStream_t>(stream)));
+    }
     uint32_t *order = at<uint32_t>(workspace, plan->off_order);
     cudaError_t e = launch_render_fwd(
         vt, at<float4>(workspace, plan->off_status + 256), at<float4>(workspace, plan->off_records),

@@ -39,6 +39,7 @@ struct DevStatus {
     unsigned long long pair_blends;
     unsigned long long block_evals;
     unsigned long long scene_pairs[VRS_MAX_SCENES];   // visible (Gaussian, view) pairs per scene
+    unsigned long long resort_flagged;                  // per-pixel order: pixels whose window overflowed
     uint32_t work[8];          // counters: [0] persistent blend, [1..2] tile sort, [4] backward list
 };
 static_assert(sizeof(DevStatus) <= 256, "the status block is 256 bytes");

@@ -24,6 +24,7 @@ struct PreParams {
     float4 *viewtab;                 // [VRS_MAX_VIEWS] principal points, written by k_decide's first CTA
     int64_t zero_tiles;              // > 0: k_decide clears tile_cnt[0, zero_tiles) (the frame's first
                                      // scene, before any pair kernel counts into it)
+    float4 *raydepth;                // nullable (per-pixel order plans): 3 float4 per record
 };
 
 // The step runs as two kernels per scene.
@@ -145,6 +146,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
     bool nonfinite_sh = false;
     __shared__ uint32_t s_wtot[kPairThreads / 32];
     __shared__ unsigned long long s_wbase[kPairThreads / 32];
+    // per-pixel-order plans: each lane's terms of t* in tile units and its 2D mean in tile
+    // units, for the keys (see below)
+    __shared__ float4 s_rd[kPairThreads / 32][32][3];
+    __shared__ float4 s_rdm[kPairThreads / 32][32];
     const int wp = threadIdx.x >> 5;
     const unsigned long long stride = (unsigned long long)gridDim.x * kPairThreads;
     for (unsigned long long c0 = (unsigned long long)blockIdx.x * kPairThreads; c0 < n_pairs; c0 += stride) {
@@ -228,6 +233,42 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             r[0] = make_float4(uh, vh, ul, vl);
             r[1] = make_float4(l0, l1, l2, lo);
             r[2] = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), __uint_as_float(e1.w));
+            if (p.raydepth) {
+                // terms of the per-pixel depth t* = sum_k a_k b_k / sum_k a_k^2 (the depth of
+                // the density maximum along the pixel's ray): with the camera-space axes
+                // e_k = W R_k of the Gaussian and u, v the pixel centre minus the principal
+                // point, a_k = (e_k . (u/fx, v/fy, 1)) / s_k and b_k = (e_k . mu_cam) / s_k;
+                // the record holds (e_kx / (fx s_k), e_ky / (fy s_k), e_kz / s_k, b_k)
+                float q[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
+                const float iq = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
+                const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                                     2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                                     2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+                const float mc0 = xh + xl, mc1 = yh + yl, mc2 = zh + zl;
+                float4 *rdp = p.raydepth + (size_t)(V.rec_base + g) * 3;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float is = __expf(-__ldg(p.S.log_scales + 3 * g + k));
+                    const float e0 = V.R[0] * Rq[k] + V.R[1] * Rq[3 + k] + V.R[2] * Rq[6 + k];
+                    const float e1_ = V.R[3] * Rq[k] + V.R[4] * Rq[3 + k] + V.R[5] * Rq[6 + k];
+                    const float e2 = V.R[6] * Rq[k] + V.R[7] * Rq[3 + k] + V.R[8] * Rq[6 + k];
+                    const float4 c = make_float4(e0 * is / V.fx, e1_ * is / V.fy, e2 * is,
+                                                 (e0 * mc0 + e1_ * mc1 + e2 * mc2) * is);
+                    rdp[k] = c;
+                    // the same terms over tile coordinates
+                    const float ts = (float)vt.tile;
+                    s_rd[wp][lane][k] = make_float4(c.x * ts, c.y * ts, c.z - c.x * V.cx - c.y * V.cy, c.w);
+                }
+                // the 2D mean and the half extents of the alpha >= 1/255 box, sqrt(thr Sigma'_xx)
+                // and sqrt(thr c) with thr = 2 ln(255 o) and Sigma'_xx = (det + b^2) / c, in tile units
+                const float thr = fmaxf(2.0f * 0.69314718f * (lo + kLog2_255), 0.f);
+                const float its = 1.0f / (float)vt.tile;
+                s_rdm[wp][lane] = make_float4((uh + ul + V.cx) * its, (vh + vl + V.cy) * its,
+                                              sqrtf(thr * (det + bb * bb) / c) * its, sqrtf(thr * c) * its);
+            }
         }
         // warp-cooperative emission: one atomic per warp, coalesced key writes
         const int x0 = (int)(e0.z & 0xffffu), x1 = (int)(e0.z >> 16);
@@ -277,8 +318,13 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             const long long ofirst = __shfl_sync(FULL, first, j);
             const int onx = __shfl_sync(FULL, nx, j);
             const int ogw = __shfl_sync(FULL, gw, j);
-            const uint32_t odb = __shfl_sync(FULL, dbits, j);
+            uint32_t odb = __shfl_sync(FULL, dbits, j);
             const uint32_t orid = __shfl_sync(FULL, rid, j);
+            int ox0 = 0, oy0 = 0;
+            if (p.raydepth) {
+                ox0 = __shfl_sync(FULL, x0, j);
+                oy0 = __shfl_sync(FULL, y0, j);
+            }
             if (k < total) {
                 // (row, column) of the pair's local tile index: a reciprocal estimate
                 // (the hardware reciprocal is within 1 ulp, so the quotient is off by
@@ -293,6 +339,24 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
                 } else if (tx >= onx) {
                     ++ty;
                     tx -= onx;
+                }
+                if (p.raydepth) {
+                    // per-pixel-order plans sort each tile's list by t* at the tile's centre, moved
+                    // into the splat's alpha >= 1/255 box where it lies outside (t* stays where the
+                    // splat is seen): for splats on a common surface their order there is the order
+                    // at most of the tile's pixels (non-negative, so its bits sort as its value)
+                    const float4 mt = s_rdm[wp][j];
+                    const float cx_ = fminf(fmaxf((float)(ox0 + tx) + 0.5f, mt.x - mt.z), mt.x + mt.z);
+                    const float cy_ = fminf(fmaxf((float)(oy0 + ty) + 0.5f, mt.y - mt.w), mt.y + mt.w);
+                    float num = 0.f, den = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const float4 c = s_rd[wp][j][q];
+                        const float a_ = fmaf(c.x, cx_, fmaf(c.y, cy_, c.z));
+                        num = fmaf(a_, c.w, num);
+                        den = fmaf(a_, a_, den);
+                    }
+                    odb = __float_as_uint(fmaxf(__fdividef(num, den), 0.f));
                 }
                 const unsigned long long tid64 = (unsigned long long)(ofirst + (long long)ty * ogw + tx);
                 const unsigned long long pos = base + k;
@@ -314,10 +378,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
                               int n_views, uint4 *pairs, float4 *rec, unsigned long long *keys,
                               uint32_t *vals, uint32_t *tile_cnt, DevStatus *st, unsigned long long cap,
-                              float4 *viewtab, int64_t zero_tiles, int n_sms, cudaStream_t stream)
+                              float4 *viewtab, int64_t zero_tiles, float4 *raydepth, int n_sms,
+                              cudaStream_t stream)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     PreParams p;
+    p.raydepth = raydepth;
     p.S = S;
     p.scene = scene;
     p.n_views = n_views;

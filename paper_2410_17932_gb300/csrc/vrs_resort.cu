@@ -1,0 +1,332 @@
+// Step 3 with the per-pixel depth order: the popping fix of Sec. 3.2, which
+// sorts the Gaussian contributions per pixel instead of per primitive.
+//
+// Each pixel orders the splats it blends by t*, the camera-space depth of the
+// 3D Gaussian's density maximum along the pixel's ray, and accumulates Eq. 1
+// with d_i = t*.  The tile's list arrives sorted by mean depth, which is close
+// to each pixel's order; the pixel holds the K nearest splats it has not
+// blended yet in a window in shared memory (a sorted ring of (t*, record)
+// keys and alphas) and blends the nearest one whenever a new splat would
+// overfill it.  A splat that arrives nearer than one the pixel has already
+// blended, or than the one it stopped at, cannot be put back in order: the
+// pixel is flagged.  An unflagged pixel has blended exactly the prefix of its
+// per-pixel order that the stop rule admits.  Pixels keep checking arrivals
+// after they stop, so the per-tile early exit is not taken.
+//
+// CTA and warp layout, staging and block culling are the per-tile blend's: one
+// CTA per tile, each warp an 8x8 block, each lane two horizontally adjacent
+// pixels; staged splats also carry the four terms per axis of t*.
+#include "vrs_internal.cuh"
+
+namespace vrs {
+
+struct ResortArgs {
+    const float4 *viewtab;
+    const float4 *rec;
+    const float4 *raydepth;     // 3 float4 per record: (e_kx/(fx s_k), e_ky/(fy s_k), e_kz/s_k, b_k)
+    const uint32_t *vals;
+    const uint2 *ranges;
+    DevStatus *st;
+    float *rgb;
+    float *depth;
+    float *Tf;
+    uint8_t *flags;
+    int64_t n_records;
+    unsigned long long cap;
+};
+
+// Order-preserving map of a float to an unsigned integer, and back.
+__device__ __forceinline__ uint32_t fkey(float t)
+{
+    const uint32_t b = __float_as_uint(t);
+    return b ^ ((b & 0x80000000u) ? 0xffffffffu : 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k)
+{
+    return __uint_as_float(k ^ ((k & 0x80000000u) ? 0x80000000u : 0xffffffffu));
+}
+
+// One pixel's compositing state and its window's ring (head slot, count).
+struct RsPix {
+    float T, R, G, B, D;
+    unsigned long long last;   // key of the last blended splat, or of the one the pixel stopped at
+    int head, n;
+    bool done, flag;
+};
+
+template <int K>
+struct RsWin {
+    unsigned long long *key;   // [K][STRIDE]: (fkey(t*) << 32) | record index
+    float *al;                 // [K][STRIDE]
+    int stride;
+};
+
+__device__ __forceinline__ void rs_blend(RsPix &P, unsigned long long key, float a, const float4 *rec)
+{
+    const float Tn = P.T * (1.0f - a);
+    P.last = key;
+    if (Tn < 1e-4f) {
+        P.done = true;
+        return;
+    }
+    const float w = a * P.T;
+    const float4 c = __ldg(rec + (size_t)(uint32_t)key * kRecF4 + 2);
+    P.R = fmaf(c.x, w, P.R);
+    P.G = fmaf(c.y, w, P.G);
+    P.B = fmaf(c.z, w, P.B);
+    P.D = fmaf(fkey_inv((uint32_t)(key >> 32)), w, P.D);
+    P.T = Tn;
+}
+
+// A splat reaches the pixel with alpha >= 1/255: order check, then window.
+template <int K>
+__device__ __forceinline__ void rs_push(RsPix &P, const RsWin<K> &W, int col, unsigned long long key, float a,
+                                        const float4 *rec)
+{
+    if (key < P.last) P.flag = true;
+    if (P.done) return;
+    if (P.n == K) {
+        const int h = P.head * W.stride + col;
+        const unsigned long long k0 = W.key[h];
+        if (key < k0) {                 // nearer than everything held: it goes first
+            rs_blend(P, key, a, rec);
+            return;
+        }
+        rs_blend(P, k0, W.al[h], rec);
+        P.head = (P.head + 1) & (K - 1);
+        P.n = K - 1;
+        if (P.done) return;
+    }
+    // insertion into the sorted ring from its far end
+    int i = P.n;
+    while (i > 0) {
+        const int src = ((P.head + i - 1) & (K - 1)) * W.stride + col;
+        const unsigned long long kp = W.key[src];
+        if (kp <= key) break;
+        const int dst = ((P.head + i) & (K - 1)) * W.stride + col;
+        W.key[dst] = kp;
+        W.al[dst] = W.al[src];
+        --i;
+    }
+    const int dst = ((P.head + i) & (K - 1)) * W.stride + col;
+    W.key[dst] = key;
+    W.al[dst] = a;
+    ++P.n;
+}
+
+template <int K>
+__device__ __forceinline__ void rs_drain(RsPix &P, const RsWin<K> &W, int col, const float4 *rec)
+{
+    while (P.n > 0 && !P.done) {
+        const int h = P.head * W.stride + col;
+        rs_blend(P, W.key[h], W.al[h], rec);
+        P.head = (P.head + 1) & (K - 1);
+        --P.n;
+    }
+}
+
+template <int TS, int K>
+__global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
+    k_render_resort(const __grid_constant__ ViewTable vt, const ResortArgs a)
+{
+    using Cfg = BlendCfg<TS>;
+    constexpr int STRIDE = 2 * Cfg::THREADS;
+    __shared__ float4 sR[Cfg::BATCH][3];   // staged splats: A, B, C as in the per-tile blend
+    __shared__ float4 sD[Cfg::BATCH][3];   // per axis: (c0, c1, c2 in the tile frame, b)
+    __shared__ uint32_t sRid[Cfg::BATCH];
+    __shared__ uint32_t smask[Cfg::BATCH];
+    __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
+    __shared__ unsigned long long s_flagged;
+    extern __shared__ __align__(16) unsigned char s_win[];
+
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
+    const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
+    const uint32_t lmask = lanemask_lt();
+    RsWin<K> Wn;
+    Wn.key = reinterpret_cast<unsigned long long *>(s_win);
+    Wn.al = reinterpret_cast<float *>(s_win + sizeof(unsigned long long) * K * STRIDE);
+    Wn.stride = STRIDE;
+    if (tid == 0) s_flagged = 0ull;
+    if (a.st->flags & ST_CAPACITY) return;
+
+    const int64_t t = blockIdx.x;
+    const int vi = view_of_tile(vt, t);
+    const DevView &V = vt.v[vi];
+    const float4 pp = a.viewtab[vi];
+    int tx, ty;
+    tile_xy(t - V.tile_base, V.gw, tx, ty);
+    const int px = tx * TS + bx + 2 * (lane & 3), py = ty * TS + by + (lane >> 2);
+    const bool in0 = px < V.w && py < V.h, in1 = px + 1 < V.w && py < V.h;
+    float oxh, oxl, oyh, oyl;
+    tile_origin((float)(tx * TS), pp.x, oxh, oxl);
+    tile_origin((float)(ty * TS), pp.y, oyh, oyl);
+    const float ox = oxh + oxl, oy = oyh + oyl;     // tile origin minus the principal point
+    const uint2 range = live_range(a.ranges, t, a.st, a.cap);
+
+    RsPix P0, P1;
+    P0.T = P1.T = 1.f;
+    P0.R = P0.G = P0.B = P0.D = P1.R = P1.G = P1.B = P1.D = 0.f;
+    P0.last = P1.last = 0ull;
+    P0.head = P0.n = P1.head = P1.n = 0;
+    P0.done = !in0;
+    P1.done = !in1;
+    P0.flag = P1.flag = false;
+
+    for (uint32_t bs = range.x; bs < range.y; bs += Cfg::BATCH) {
+        if (bs != range.x) __syncthreads();            // the previous batch is no longer read
+        const uint32_t j = bs + tid;
+        const uint32_t rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
+        uint32_t mask = 0u;
+        if ((int64_t)rid < a.n_records) {
+            float4 r0, r1, r2, A, B, C;
+            load_record(a.rec, rid, r0, r1, r2);
+            stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
+            mask = cull_blocks<Cfg::WGX, Cfg::WARPS / Cfg::WGX>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z));
+            float Kc, Lc;
+            splat_KL(A.x, A.y, A.z, A.w, B.x, Kc, Lc);
+            sR[tid][0] = make_float4(Kc, Lc, -A.z, -A.w);
+            B.x = -B.x;
+            sR[tid][1] = B;
+            sR[tid][2] = C;
+            const float4 *rd = a.raydepth + (size_t)rid * 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 c = __ldg(rd + k);
+                sD[tid][k] = make_float4(c.x, c.y, fmaf(c.x, ox, fmaf(c.y, oy, c.z)), c.w);
+            }
+            sRid[tid] = rid;
+        }
+        smask[tid] = mask;
+        __syncthreads();
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < Cfg::BATCH / 32; ++c) {
+            const uint32_t bit = (smask[c * 32 + lane] >> w) & 1u;
+            const uint32_t bal = __ballot_sync(FULL, bit);
+            if (bit) slist[w][cnt + __popc(bal & lmask)] = (uint16_t)(c * 32 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int k = 0; k < cnt; ++k) {
+            const int js = slist[w][k];
+            const float4 A = sR[js][0], B = sR[js][1];
+            // q' - lo at the two pixels, as the per-tile blend evaluates it
+            const float s = __fmaf_rn(B.x, pyc, A.y);
+            const float ww = __fmaf_rn(s, s, -B.y);
+            const float r = __fmaf_rn(A.w, pyc, A.x);
+            const float t0 = __fmaf_rn(A.z, pxc, r), t1 = __fmaf_rn(A.z, pxc + 1.0f, r);
+            const float u0 = __fmaf_rn(t0, t0, ww), u1 = __fmaf_rn(t1, t1, ww);
+            const bool h0 = in0 && u0 <= kLog2_255, h1 = in1 && u1 <= kLog2_255;
+            if (!(h0 || h1)) continue;
+            // t* at both pixels: a_k = c0 x + c1 y + c2, t* = sum a_k b_k / sum a_k^2
+            float n0 = 0.f, d0 = 0.f, n1 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 c = sD[js][q];
+                const float ay = fmaf(c.y, pyc, c.z);
+                const float a0 = fmaf(c.x, pxc, ay), a1 = a0 + c.x;
+                n0 = fmaf(a0, c.w, n0);
+                d0 = fmaf(a0, a0, d0);
+                n1 = fmaf(a1, c.w, n1);
+                d1 = fmaf(a1, a1, d1);
+            }
+            const unsigned long long rkey = sRid[js];
+            if (h0) {
+                const float al = fminf(ex2_approx(-u0), 0.99f);
+                const unsigned long long key = ((unsigned long long)fkey(__fdividef(n0, d0)) << 32) | rkey;
+                rs_push<K>(P0, Wn, tid, key, al, a.rec);
+            }
+            if (h1) {
+                const float al = fminf(ex2_approx(-u1), 0.99f);
+                const unsigned long long key = ((unsigned long long)fkey(__fdividef(n1, d1)) << 32) | rkey;
+                rs_push<K>(P1, Wn, Cfg::THREADS + tid, key, al, a.rec);
+            }
+        }
+    }
+    rs_drain<K>(P0, Wn, tid, a.rec);
+    rs_drain<K>(P1, Wn, Cfg::THREADS + tid, a.rec);
+
+    const int64_t HW = (int64_t)V.w * V.h;
+    const int64_t lp = (int64_t)py * V.w + px;
+    const int64_t pix = V.pix_base + lp;
+    float *rgb = a.rgb + 3 * V.pix_base;
+    if (in0) {
+        rgb[lp] = P0.R;
+        rgb[HW + lp] = P0.G;
+        rgb[2 * HW + lp] = P0.B;
+        a.depth[pix] = P0.D;
+        a.Tf[pix] = P0.T;
+        a.flags[pix] = P0.flag ? 1 : 0;
+    }
+    if (in1) {
+        rgb[lp + 1] = P1.R;
+        rgb[HW + lp + 1] = P1.G;
+        rgb[2 * HW + lp + 1] = P1.B;
+        a.depth[pix + 1] = P1.D;
+        a.Tf[pix + 1] = P1.T;
+        a.flags[pix + 1] = P1.flag ? 1 : 0;
+    }
+    const uint32_t nf = __reduce_add_sync(FULL, (in0 && P0.flag ? 1u : 0u) + (in1 && P1.flag ? 1u : 0u));
+    if (lane == 0 && nf) atomicAdd(&s_flagged, (unsigned long long)nf);
+    __syncthreads();
+    if (tid == 0 && s_flagged) atomicAdd(&a.st->resort_flagged, s_flagged);
+}
+
+template <int TS, int K>
+static cudaError_t launch_resort_tk(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, cudaStream_t s)
+{
+    constexpr int T = BlendCfg<TS>::THREADS;
+    const size_t smem = (size_t)K * 2 * T * (sizeof(unsigned long long) + sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_render_resort<TS, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_render_resort<TS, K><<<(unsigned)n_tiles, T, smem, s>>>(vt, a);
+    return cudaGetLastError();
+}
+
+template <int TS>
+static cudaError_t launch_resort_t(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, int window,
+                                   cudaStream_t s)
+{
+    switch (window) {
+        case 4: return launch_resort_tk<TS, 4>(vt, a, n_tiles, s);
+        case 8: return launch_resort_tk<TS, 8>(vt, a, n_tiles, s);
+        case 16:
+            if (TS == 32) return cudaErrorInvalidValue;
+            return launch_resort_tk<TS, (TS == 32 ? 8 : 16)>(vt, a, n_tiles, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
+                                 const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
+                                 DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
+                                 int64_t n_tiles, int64_t n_records, unsigned long long cap, int window,
+                                 cudaStream_t s)
+{
+    ResortArgs a;
+    a.viewtab = viewtab;
+    a.rec = rec;
+    a.raydepth = raydepth;
+    a.vals = vals;
+    a.ranges = ranges;
+    a.st = st;
+    a.rgb = rgb;
+    a.depth = depth;
+    a.Tf = Tf;
+    a.flags = flags;
+    a.n_records = n_records;
+    a.cap = cap;
+    cudaError_t e = cudaMemsetAsync(&st->resort_flagged, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n_tiles <= 0) return e;
+    switch (vt.tile) {
+        case 8: return launch_resort_t<8>(vt, a, n_tiles, window, s);
+        case 16: return launch_resort_t<16>(vt, a, n_tiles, window, s);
+        case 32: return launch_resort_t<32>(vt, a, n_tiles, window, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vrs

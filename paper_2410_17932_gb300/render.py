@@ -86,7 +86,7 @@ class Rasterizer:
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
                  persistent: bool = False, backward: bool = False, max_instances: int = 0,
-                 sort: int = 0, device="cuda"):
+                 sort: int = 0, resort: int = 0, device="cuda"):
         self.scenes = list(scenes)
         self.views = list(views)
         self.device = torch.device(device)
@@ -94,6 +94,7 @@ class Rasterizer:
         self.persistent = bool(persistent)
         self.backward = bool(backward)
         self.sort = int(sort)
+        self.resort = int(resort)    # 0: list order; 4/8/16: per-pixel order through a window of that size
         self.generation = 0          # forward passes and re-plans; the autograd glue checks it
         self._make_plan(max_instances)
 
@@ -104,7 +105,7 @@ class Rasterizer:
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
         opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), self.sort,
-                               int(max_instances), 0, 0)
+                               int(max_instances), 0, self.resort)
         plan = L.vrs_plan()
         L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
         self.plan = plan
@@ -255,6 +256,19 @@ class Rasterizer:
     def records(self) -> torch.Tensor:
         p = self.plan
         return self.ws_view(int(p.off_records), 12 * int(p.n_records), torch.float32).view(-1, 12)
+
+    def resort_flags(self) -> torch.Tensor:
+        """Per-pixel order plans: 1 where a pixel's sorting window could not restore its order."""
+        p = self.plan
+        if not int(p.resort):
+            raise ValueError("not a per-pixel order plan")
+        return self.ws_view(int(p.off_resort_flags), int(p.n_pixels), torch.uint8)
+
+    def resort_flagged(self, stream=None) -> int:
+        info = L.vrs_run_info()
+        L._check(L.vrs_query_status(self.plan, self.workspace.data_ptr(), info, _stream_handle(stream)),
+                 "resort_flagged")
+        return int(info.resort_flagged)
 
     def n_contrib(self) -> torch.Tensor:
         """Each pixel's last blended list position + 1 (written for backward plans only)."""

@@ -53,7 +53,8 @@ int main(void) {
   P(vrs_camera, fx) P(vrs_camera, width) P(vrs_camera, scene) P(vrs_scene, n)
   P(vrs_run_info, instances) P(vrs_run_info, pair_blends) P(vrs_run_info, block_evals)
   P(vrs_plan_opts, max_instances) P(vrs_plan, off_pairs) P(vrs_cull_opts, abs_margin)
-  P(vrs_run_info, visible_pairs)
+  P(vrs_run_info, visible_pairs) P(vrs_run_info, resort_flagged) P(vrs_plan, resort)
+  P(vrs_plan, off_raydepth) P(vrs_plan, off_resort_flags) P(vrs_plan_opts, resort)
   return 0;
 }
 """
