@@ -303,7 +303,7 @@ def _time_loop(fn, flush, iters):
     return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
 
 
-EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m")
+EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m", "per_pixel_order")
 
 
 def run_extras(args):
@@ -348,7 +348,50 @@ def run_extras(args):
         out["batched_32_views"] = _batched_32(args, flush)
     if "foveal_points_5m" in want:
         out["foveal_points_5m"] = _foveal_points(args, flush)
+    if "per_pixel_order" in want:
+        out["periphery_stereo_05m_per_pixel_order"] = _per_pixel_order(args, flush)
     return out
+
+
+def _stage_times(ras, flush, iters):
+    """Preprocess, bin/sort and blend of one frame, in order, an event between stages."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(iters)]
+    for e in evs:
+        flush.zero_()
+        e[0].record()
+        ras.preprocess()
+        e[1].record()
+        ras.bin_sort()
+        e[2].record()
+        ras.render_fwd()
+        e[3].record()
+    torch.cuda.synchronize()
+    names = ("preprocess", "bin_sort", "render_fwd")
+    return {n: round(statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs), 4) for i, n in enumerate(names)}
+
+
+def _per_pixel_order(args, flush):
+    """The bench frame with the popping fix of Sec. 3.2 (per-pixel depth order) at sorting
+    windows of 8 and 16 splats per pixel: frame time (graph replay), blend time, flagged pixels."""
+    from paper_2410_17932_gb300 import autotune
+    from paper_2410_17932_gb300 import inputs as I
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+    scenes, views = I.periphery_stereo_05m()
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    res = {}
+    for K in (8, 16):
+        ras = Rasterizer(sts, views, resort=K)
+        runner = autotune.GraphRunner(ras)
+        for _ in range(3):
+            runner.replay()
+        ms = _time_loop(runner.replay, flush, args.extra_steps)
+        flagged = ras.resort_flagged() / int(ras.plan.n_pixels)
+        stages = _stage_times(ras, flush, args.extra_steps)
+        res[f"window_{K}"] = {"ms_per_frame": round(ms, 4), "stages_ms": stages,
+                              "flagged_pixel_frac": round(flagged, 6)}
+        del runner, ras
+    return res
 
 
 def _batched_32(args, flush):

@@ -237,7 +237,7 @@ vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
  * sorts Gaussian contributions per pixel instead of per primitive).  Each pixel
  * orders the splats it blends by the depth of each 3D Gaussian's density
  * maximum along the pixel's ray, t* = r^T Sigma_c^-1 mu / r^T Sigma_c^-1 r with
- * r = ((x - cx)/fx, (y - cy)/fy, 1) (ties by record index), and Eq. 1 takes
+ * r = ((x - cx)/fx, (y - cy)/fy, 1) (exact ties in list order), and Eq. 1 takes
  * d_i = t* at the pixel.  In these plans vrs_preprocess keys each instance by
  * t* at its tile's centre (moved into the splat's alpha >= 1/255 box where the
  * centre lies outside it) instead of by the mean's depth, so the tile list

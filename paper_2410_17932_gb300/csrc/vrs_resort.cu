@@ -3,13 +3,13 @@
 //
 // Each pixel orders the splats it blends by t*, the camera-space depth of the
 // 3D Gaussian's density maximum along the pixel's ray, and accumulates Eq. 1
-// with d_i = t*.  The tile's list arrives sorted by mean depth, which is close
-// to each pixel's order; the pixel holds the K nearest splats it has not
-// blended yet in a window in shared memory (a sorted ring of (t*, record)
-// keys and alphas) and blends the nearest one whenever a new splat would
-// overfill it.  A splat that arrives nearer than one the pixel has already
-// blended, or than the one it stopped at, cannot be put back in order: the
-// pixel is flagged.  An unflagged pixel has blended exactly the prefix of its
+// with d_i = t*.  The tile's list arrives sorted by t* at the tile's centre
+// (clamped into each splat's footprint), which is close to each pixel's order;
+// the pixel holds the K nearest splats it has not blended yet in a window in
+// shared memory (a sorted ring of t* keys with premultiplied colours) and
+// blends the nearest one whenever a new splat would overfill it.  A splat that
+// arrives nearer than one the pixel has already blended, or than the one it
+// stopped at, cannot be put back in order: the pixel is flagged.  An unflagged pixel has blended exactly the prefix of its
 // per-pixel order that the stop rule admits.  Pixels keep checking arrivals
 // after they stop, so the per-tile early exit is not taken.
 //
@@ -46,84 +46,98 @@ __device__ __forceinline__ float fkey_inv(uint32_t k)
     return __uint_as_float(k ^ ((k & 0x80000000u) ? 0x80000000u : 0xffffffffu));
 }
 
-// One pixel's compositing state and its window's ring (head slot, count).
+// One pixel's compositing state and its window, a sorted ring in shared memory
+// of (key, premultiplied colour and alpha) entries: key = fkey(t*), the colour
+// alpha (r, g, b) and alpha.  The head (nearest) and tail (farthest) keys are
+// kept in registers, so that an arrival in order touches shared memory only to
+// store itself and to read the entry it pushes out.  Exact ties of t* keep
+// their arrival order.
 struct RsPix {
     float T, R, G, B, D;
-    unsigned long long last;   // key of the last blended splat, or of the one the pixel stopped at
+    uint32_t last;             // key of the last blended splat, or of the one the pixel stopped at
+    uint32_t hk, tk;           // keys at the head and the tail of the ring
     int head, n;
     bool done, flag;
 };
 
 template <int K>
 struct RsWin {
-    unsigned long long *key;   // [K][STRIDE]: (fkey(t*) << 32) | record index
-    float *al;                 // [K][STRIDE]
+    uint32_t *key;             // [K][stride]
+    float4 *col;               // [K][stride]: (alpha r, alpha g, alpha b, alpha)
     int stride;
 };
 
-__device__ __forceinline__ void rs_blend(RsPix &P, unsigned long long key, float a, const float4 *rec)
+__device__ __forceinline__ void rs_blend(RsPix &P, uint32_t key, float4 c)
 {
-    const float Tn = P.T * (1.0f - a);
+    const float Tn = P.T * (1.0f - c.w);
     P.last = key;
     if (Tn < 1e-4f) {
         P.done = true;
         return;
     }
-    const float w = a * P.T;
-    const float4 c = __ldg(rec + (size_t)(uint32_t)key * kRecF4 + 2);
-    P.R = fmaf(c.x, w, P.R);
-    P.G = fmaf(c.y, w, P.G);
-    P.B = fmaf(c.z, w, P.B);
-    P.D = fmaf(fkey_inv((uint32_t)(key >> 32)), w, P.D);
+    P.R = fmaf(c.x, P.T, P.R);
+    P.G = fmaf(c.y, P.T, P.G);
+    P.B = fmaf(c.z, P.T, P.B);
+    P.D = fmaf(fkey_inv(key) * c.w, P.T, P.D);
     P.T = Tn;
 }
 
 // A splat reaches the pixel with alpha >= 1/255: order check, then window.
 template <int K>
-__device__ __forceinline__ void rs_push(RsPix &P, const RsWin<K> &W, int col, unsigned long long key, float a,
-                                        const float4 *rec)
+__device__ __forceinline__ void rs_push(RsPix &P, const RsWin<K> &W, int col, uint32_t key, float4 c)
 {
     if (key < P.last) P.flag = true;
     if (P.done) return;
     if (P.n == K) {
-        const int h = P.head * W.stride + col;
-        const unsigned long long k0 = W.key[h];
-        if (key < k0) {                 // nearer than everything held: it goes first
-            rs_blend(P, key, a, rec);
+        if (key < P.hk) {               // nearer than everything held: it goes first
+            rs_blend(P, key, c);
             return;
         }
-        rs_blend(P, k0, W.al[h], rec);
+        rs_blend(P, P.hk, W.col[P.head * W.stride + col]);
         P.head = (P.head + 1) & (K - 1);
         P.n = K - 1;
         if (P.done) return;
+        P.hk = W.key[P.head * W.stride + col];
     }
-    // insertion into the sorted ring from its far end
+    if (P.n == 0 || key >= P.tk) {      // in order: append at the tail
+        const int dst = ((P.head + P.n) & (K - 1)) * W.stride + col;
+        W.key[dst] = key;
+        W.col[dst] = c;
+        if (P.n == 0) P.hk = key;
+        P.tk = key;
+        ++P.n;
+        return;
+    }
+    // insertion from the far end of the ring
     int i = P.n;
     while (i > 0) {
         const int src = ((P.head + i - 1) & (K - 1)) * W.stride + col;
-        const unsigned long long kp = W.key[src];
+        const uint32_t kp = W.key[src];
         if (kp <= key) break;
         const int dst = ((P.head + i) & (K - 1)) * W.stride + col;
         W.key[dst] = kp;
-        W.al[dst] = W.al[src];
+        W.col[dst] = W.col[src];
         --i;
     }
     const int dst = ((P.head + i) & (K - 1)) * W.stride + col;
     W.key[dst] = key;
-    W.al[dst] = a;
+    W.col[dst] = c;
+    if (i == 0) P.hk = key;
     ++P.n;
 }
 
 template <int K>
-__device__ __forceinline__ void rs_drain(RsPix &P, const RsWin<K> &W, int col, const float4 *rec)
+__device__ __forceinline__ void rs_drain(RsPix &P, const RsWin<K> &W, int col)
 {
     while (P.n > 0 && !P.done) {
         const int h = P.head * W.stride + col;
-        rs_blend(P, W.key[h], W.al[h], rec);
+        rs_blend(P, W.key[h], W.col[h]);
         P.head = (P.head + 1) & (K - 1);
         --P.n;
     }
 }
+
+__device__ __forceinline__ float2 f2r(float a) { return make_float2(a, a); }
 
 template <int TS, int K>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
@@ -133,7 +147,6 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     constexpr int STRIDE = 2 * Cfg::THREADS;
     __shared__ float4 sR[Cfg::BATCH][3];   // staged splats: A, B, C as in the per-tile blend
     __shared__ float4 sD[Cfg::BATCH][3];   // per axis: (c0, c1, c2 in the tile frame, b)
-    __shared__ uint32_t sRid[Cfg::BATCH];
     __shared__ uint32_t smask[Cfg::BATCH];
     __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
     __shared__ unsigned long long s_flagged;
@@ -143,10 +156,11 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
+    const float2 pxc2 = make_float2(pxc, pxc + 1.0f);
     const uint32_t lmask = lanemask_lt();
     RsWin<K> Wn;
-    Wn.key = reinterpret_cast<unsigned long long *>(s_win);
-    Wn.al = reinterpret_cast<float *>(s_win + sizeof(unsigned long long) * K * STRIDE);
+    Wn.col = reinterpret_cast<float4 *>(s_win);
+    Wn.key = reinterpret_cast<uint32_t *>(s_win + sizeof(float4) * K * STRIDE);
     Wn.stride = STRIDE;
     if (tid == 0) s_flagged = 0ull;
     if (a.st->flags & ST_CAPACITY) return;
@@ -168,7 +182,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     RsPix P0, P1;
     P0.T = P1.T = 1.f;
     P0.R = P0.G = P0.B = P0.D = P1.R = P1.G = P1.B = P1.D = 0.f;
-    P0.last = P1.last = 0ull;
+    P0.last = P1.last = 0u;
+    P0.hk = P0.tk = P1.hk = P1.tk = 0u;
     P0.head = P0.n = P1.head = P1.n = 0;
     P0.done = !in0;
     P1.done = !in1;
@@ -196,7 +211,6 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
                 const float4 c = __ldg(rd + k);
                 sD[tid][k] = make_float4(c.x, c.y, fmaf(c.x, ox, fmaf(c.y, oy, c.z)), c.w);
             }
-            sRid[tid] = rid;
         }
         smask[tid] = mask;
         __syncthreads();
@@ -220,33 +234,29 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float u0 = __fmaf_rn(t0, t0, ww), u1 = __fmaf_rn(t1, t1, ww);
             const bool h0 = in0 && u0 <= kLog2_255, h1 = in1 && u1 <= kLog2_255;
             if (!(h0 || h1)) continue;
-            // t* at both pixels: a_k = c0 x + c1 y + c2, t* = sum a_k b_k / sum a_k^2
-            float n0 = 0.f, d0 = 0.f, n1 = 0.f, d1 = 0.f;
+            // t* at both pixels (packed): a_k = c0 x + c1 y + c2, t* = sum a_k b_k / sum a_k^2
+            float2 nn = f2r(0.f), dd = f2r(0.f);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const float4 c = sD[js][q];
-                const float ay = fmaf(c.y, pyc, c.z);
-                const float a0 = fmaf(c.x, pxc, ay), a1 = a0 + c.x;
-                n0 = fmaf(a0, c.w, n0);
-                d0 = fmaf(a0, a0, d0);
-                n1 = fmaf(a1, c.w, n1);
-                d1 = fmaf(a1, a1, d1);
+                const float2 ak = __ffma2_rn(f2r(c.x), pxc2, f2r(fmaf(c.y, pyc, c.z)));
+                nn = __ffma2_rn(ak, f2r(c.w), nn);
+                dd = __ffma2_rn(ak, ak, dd);
             }
-            const unsigned long long rkey = sRid[js];
+            const float2 tt = __fmul2_rn(nn, make_float2(rcp_approx(dd.x), rcp_approx(dd.y)));
+            const float4 C = sR[js][2];
             if (h0) {
                 const float al = fminf(ex2_approx(-u0), 0.99f);
-                const unsigned long long key = ((unsigned long long)fkey(__fdividef(n0, d0)) << 32) | rkey;
-                rs_push<K>(P0, Wn, tid, key, al, a.rec);
+                rs_push<K>(P0, Wn, tid, fkey(tt.x), make_float4(C.x * al, C.y * al, C.z * al, al));
             }
             if (h1) {
                 const float al = fminf(ex2_approx(-u1), 0.99f);
-                const unsigned long long key = ((unsigned long long)fkey(__fdividef(n1, d1)) << 32) | rkey;
-                rs_push<K>(P1, Wn, Cfg::THREADS + tid, key, al, a.rec);
+                rs_push<K>(P1, Wn, Cfg::THREADS + tid, fkey(tt.y), make_float4(C.x * al, C.y * al, C.z * al, al));
             }
         }
     }
-    rs_drain<K>(P0, Wn, tid, a.rec);
-    rs_drain<K>(P1, Wn, Cfg::THREADS + tid, a.rec);
+    rs_drain<K>(P0, Wn, tid);
+    rs_drain<K>(P1, Wn, Cfg::THREADS + tid);
 
     const int64_t HW = (int64_t)V.w * V.h;
     const int64_t lp = (int64_t)py * V.w + px;
@@ -278,7 +288,7 @@ template <int TS, int K>
 static cudaError_t launch_resort_tk(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, cudaStream_t s)
 {
     constexpr int T = BlendCfg<TS>::THREADS;
-    const size_t smem = (size_t)K * 2 * T * (sizeof(unsigned long long) + sizeof(float));
+    const size_t smem = (size_t)K * 2 * T * (sizeof(float4) + sizeof(uint32_t));
     cudaError_t e = cudaFuncSetAttribute(k_render_resort<TS, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
