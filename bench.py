@@ -303,7 +303,7 @@ def _time_loop(fn, flush, iters):
     return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
 
 
-EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m", "per_pixel_order")
+EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m", "per_pixel_order", "inference")
 
 
 def run_extras(args):
@@ -350,7 +350,34 @@ def run_extras(args):
         out["foveal_points_5m"] = _foveal_points(args, flush)
     if "per_pixel_order" in want:
         out["periphery_stereo_05m_per_pixel_order"] = _per_pixel_order(args, flush)
+    if "inference" in want:
+        out["periphery_stereo_05m_inference"] = _inference_variants(args, flush)
     return out
+
+
+def _inference_variants(args, flush):
+    """Sec. 4 "Inference" on the bench frame: baked attributes (bit-identical images) and half
+    precision storage (binary16 SH coefficients in, binary16 images out), each as a CUDA-graph
+    frame with its stages, the half one also end to end with host buffers."""
+    from paper_2410_17932_gb300 import autotune
+    from paper_2410_17932_gb300 import inputs as I
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+    scenes, views = I.periphery_stereo_05m()
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    res = {}
+    for name, st, kw in (("baked", [s.baked_scene() for s in sts], {}),
+                         ("half_sh_half_out", [s.half_sh() for s in sts], {"half_out": True})):
+        ras = Rasterizer(st, views, **kw)
+        runner = autotune.GraphRunner(ras)
+        for _ in range(3):
+            runner.replay()
+        r = {"ms_per_frame": round(_time_loop(runner.replay, flush, args.extra_steps), 4),
+             "stages_ms": _stage_times(ras, flush, args.extra_steps)}
+        if name == "half_sh_half_out" and not args.no_e2e:
+            r["e2e"] = run_e2e(args, scenes, views, st, ras, flush, 1)
+        res[name] = r
+        del runner, ras
+    return res
 
 
 def _stage_times(ras, flush, iters):
@@ -511,11 +538,11 @@ def run_e2e(args, scenes, views, sts, ras, flush, world):
     import torch
     from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
     host = [[x.detach().cpu().pin_memory() for x in s.tensors()] for s in sts]
-    h2d = sum(x.numel() * 4 for hs in host for x in hs)
+    h2d = sum(x.numel() * x.element_size() for hs in host for x in hs)
     # latency: one frame at a time
-    out_rgb = torch.empty(ras.rgb.numel(), dtype=torch.float32).pin_memory()
-    out_d = torch.empty(ras.depth.numel(), dtype=torch.float32).pin_memory()
-    d2h = (out_rgb.numel() + out_d.numel()) * 4
+    out_rgb = torch.empty(ras.rgb.numel(), dtype=ras.rgb.dtype).pin_memory()
+    out_d = torch.empty(ras.depth.numel(), dtype=ras.depth.dtype).pin_memory()
+    d2h = out_rgb.numel() * out_rgb.element_size() + out_d.numel() * out_d.element_size()
     E = args.e2e_steps
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -536,14 +563,15 @@ def run_e2e(args, scenes, views, sts, ras, flush, world):
     latency = statistics.mean(tms)
     # pipelined frame loop: rasterizer r = k % 2 owns its scene buffers and outputs
     sts2 = [SceneTensors(*[torch.empty_like(x) for x in s_.tensors()], s_.sh_degree) for s_ in sts]
-    ras2 = Rasterizer(sts2, views, tile=int(ras.plan.tile), persistent=bool(ras.plan.persistent))
+    ras2 = Rasterizer(sts2, views, tile=int(ras.plan.tile), persistent=bool(ras.plan.persistent),
+                      resort=int(ras.plan.resort), half_out=bool(ras.plan.half_out))
     for s_, hs in zip(sts2, host):
         for dst, src_ in zip(s_.tensors(), hs):
             dst.copy_(src_)
     ras2.forward()
     R = [(ras, sts), (ras2, sts2)]
-    outs = [(torch.empty(ras.rgb.numel(), dtype=torch.float32).pin_memory(),
-             torch.empty(ras.depth.numel(), dtype=torch.float32).pin_memory()) for _ in range(2)]
+    outs = [(torch.empty(ras.rgb.numel(), dtype=ras.rgb.dtype).pin_memory(),
+             torch.empty(ras.depth.numel(), dtype=ras.depth.dtype).pin_memory()) for _ in range(2)]
     s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     torch.cuda.synchronize()
     K = max(E, 8)

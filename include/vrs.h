@@ -87,10 +87,18 @@ typedef struct {
     const float *log_scales;     /* [n][3] */
     const float *quats;          /* [n][4] (w, x, y, z) */
     const float *opacity_logits; /* [n] */
-    const float *sh;             /* [n][(sh_degree+1)^2][3] */
+    const float *sh;             /* [n][(sh_degree+1)^2][3]; IEEE half values when sh_half = 1 */
     int32_t n;                   /* number of Gaussians, >= 0 */
     int32_t sh_degree;           /* 0..3 */
+    const float *baked;          /* nullable: [n][VRS_BAKED_FLOATS] written by vrs_bake; when set,
+                                    vrs_preprocess reads the Gaussian's scales, rotation and opacity
+                                    from it and ignores log_scales, quats and opacity_logits */
+    int32_t sh_half;             /* 1: sh holds IEEE binary16 values (inference only) */
+    int32_t reserved;
 } vrs_scene;
+
+/* Floats per Gaussian in a baked attribute array (see vrs_bake). */
+#define VRS_BAKED_FLOATS 16
 
 /* A pinhole view (host struct). */
 typedef struct {
@@ -119,6 +127,9 @@ typedef struct {
                               4, 8 or 16 = per-pixel depth order (the popping fix of Sec. 3.2)
                               through a sorting window of that many splats per pixel (see
                               vrs_render_fwd); forward only (backward must be 0) */
+    int32_t half_out;      /* 1 = vrs_render_fwd writes rgb, depth and T_final as IEEE binary16
+                              (half the output bytes; inference only, backward must be 0) */
+    int32_t reserved;
 } vrs_plan_opts;
 
 /* Sizes and workspace layout, filled by vrs_plan_batch.  Treat as read-only. */
@@ -167,7 +178,7 @@ typedef struct {
     int64_t view_tile_base[VRS_MAX_VIEWS];  /* global tile id = view_tile_base[v] + ty * gw + tx */
     int64_t view_pix_base[VRS_MAX_VIEWS];   /* view v's pixels start at element view_pix_base[v] */
     int32_t resort;            /* vrs_plan_opts.resort */
-    int32_t reserved;
+    int32_t half_out;          /* vrs_plan_opts.half_out */
     int64_t off_raydepth;      /* resort plans: [n_records][3] float4, per record the terms of the
                                   per-pixel depth (see vrs_render_fwd); 0 otherwise */
     int64_t off_resort_flags;  /* resort plans: [n_pixels] uint8, 1 where the pixel's sorting
@@ -255,6 +266,9 @@ vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
  *   depth   [H][W] per view at depth + plan.view_pix_base[v]   (Eq. 1, not normalised)
  *   T_final [H][W] per view at T_final + plan.view_pix_base[v]
  * Colour is premultiplied with no background; composite with T_final.
+ * For a plan made with half_out = 1 the three outputs are arrays of IEEE
+ * binary16 values (pass their addresses as float*): the same results, each
+ * rounded to half precision at the store.
  * For a plan made with backward = 1 it also writes each pixel's last blended
  * list position at workspace + plan.off_ncontrib, where vrs_render_bwd starts. */
 vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, float *depth,
@@ -272,6 +286,21 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
                           const vrs_camera *views, const float *T_final, const float *dL_drgb,
                           const float *dL_ddepth, const float *dL_dT, const vrs_scene *grads,
                           void *stream);
+
+/* Baked attributes for inference (Sec. 4 "Inference": opacities, features and
+ * covariances are baked into the point cloud to minimise runtime cost).  For
+ * each Gaussian of `scene` (parameter form, device pointers) writes
+ * VRS_BAKED_FLOATS floats to `baked` (device, [n][16], 16-byte aligned): the
+ * scales exp(log_s) (3), the rotation of the normalised quaternion (9,
+ * row-major), the opacity sigmoid(logit) and its log2 (2), a status word (1:
+ * all-zero quaternion, 2: non-finite parameter; as float bits) and one unused
+ * float.  Each value is computed by the same sequence of FP32 operations the
+ * preprocess applies to the parameters, so a scene whose `baked` pointer is
+ * set renders bit for bit the same images as its parameter form, with the
+ * activations skipped.  The SH coefficients stay as they are (the colour
+ * depends on the view).  Re-bake after the parameters change.  Stream
+ * ordered; VRS_ERR_INVALID for a NULL pointer with n > 0. */
+vrs_status vrs_bake(const vrs_scene *scene, float *baked, void *stream);
 
 /* Synchronises `stream`, copies the device status block to *info (nullable)
  * and returns the most severe device status: CAPACITY, then TIMEOUT, then

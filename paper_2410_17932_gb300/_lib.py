@@ -27,7 +27,11 @@ _i32, _i64, _u32, _u64, _f32, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_ui
 
 class vrs_scene(ctypes.Structure):
     _fields_ = [("means", _vp), ("log_scales", _vp), ("quats", _vp), ("opacity_logits", _vp),
-                ("sh", _vp), ("n", _i32), ("sh_degree", _i32)]
+                ("sh", _vp), ("n", _i32), ("sh_degree", _i32), ("baked", _vp), ("sh_half", _i32),
+                ("reserved", _i32)]
+
+
+VRS_BAKED_FLOATS = 16
 
 
 class vrs_camera(ctypes.Structure):
@@ -38,7 +42,8 @@ class vrs_camera(ctypes.Structure):
 
 class vrs_plan_opts(ctypes.Structure):
     _fields_ = [("tile", _i32), ("persistent", _i32), ("backward", _i32), ("sort", _i32),
-                ("max_instances", _i64), ("count_pairs", _i32), ("resort", _i32)]
+                ("max_instances", _i64), ("count_pairs", _i32), ("resort", _i32), ("half_out", _i32),
+                ("reserved", _i32)]
 
 
 class vrs_plan(ctypes.Structure):
@@ -56,7 +61,7 @@ class vrs_plan(ctypes.Structure):
                 ("view_h", _i32 * VRS_MAX_VIEWS), ("view_gw", _i32 * VRS_MAX_VIEWS),
                 ("view_gh", _i32 * VRS_MAX_VIEWS), ("view_rec_base", _i64 * VRS_MAX_VIEWS),
                 ("view_tile_base", _i64 * VRS_MAX_VIEWS), ("view_pix_base", _i64 * VRS_MAX_VIEWS),
-                ("resort", _i32), ("reserved", _i32), ("off_raydepth", _i64), ("off_resort_flags", _i64)]
+                ("resort", _i32), ("half_out", _i32), ("off_raydepth", _i64), ("off_resort_flags", _i64)]
 
 
 class vrs_run_info(ctypes.Structure):
@@ -87,6 +92,7 @@ SIGNATURES = [
     ("vrs_query_status", _i32, [ctypes.POINTER(vrs_plan), _vp, ctypes.POINTER(vrs_run_info), _vp]),
     ("vrs_reset_status", _i32, [ctypes.POINTER(vrs_plan), _vp, _vp]),
     ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    ("vrs_bake", _i32, [ctypes.POINTER(vrs_scene), _vp, _vp]),
     ("vrs_foveal_combine", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
                                   ctypes.POINTER(vrs_combine_opts), _vp, _vp, _vp]),
     ("vrs_foveal_combine_bwd", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
@@ -196,3 +202,7 @@ def vrs_foveal_combine_bwd(P: int, pw: int, ph: int, F: int, w: int, h: int, x0:
     return load().vrs_foveal_combine_bwd(P, pw, ph, F, w, h, x0, y0, ex, ey,
                                          ctypes.byref(opts) if opts is not None else None, dL_dout, dL_dP,
                                          dL_dF, scratch, stream)
+
+
+def vrs_bake(scene, baked: int, stream: int) -> int:
+    return load().vrs_bake(ctypes.byref(scene), baked, stream)

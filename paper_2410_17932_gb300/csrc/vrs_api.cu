@@ -22,13 +22,13 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              unsigned long long cap, int persistent, int count, int n_sms,
+                              unsigned long long cap, int persistent, int count, int half_out, int n_sms,
                               cudaStream_t s);
 cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                                  const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
                                  DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
                                  int64_t n_tiles, int64_t n_records, unsigned long long cap, int window,
-                                 cudaStream_t s);
+                                 int half_out, cudaStream_t s);
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
@@ -105,8 +105,9 @@ vrs_status check_scenes(const vrs_plan *P, const vrs_scene *scenes)
     for (int s = 0; s < P->n_scenes; ++s) {
         const vrs_scene &S = scenes[s];
         if (S.n != P->scene_n[s] || S.sh_degree != P->scene_deg[s]) return VRS_ERR_INVALID;
-        if (S.n > 0 && (!S.means || !S.log_scales || !S.quats || !S.opacity_logits || !S.sh))
-            return VRS_ERR_INVALID;
+        if (S.n > 0 && (!S.means || !S.sh)) return VRS_ERR_INVALID;
+        if (S.n > 0 && !S.baked && (!S.log_scales || !S.quats || !S.opacity_logits)) return VRS_ERR_INVALID;
+        if (S.baked && (reinterpret_cast<uintptr_t>(S.baked) & 15u)) return VRS_ERR_INVALID;
     }
     return VRS_OK;
 }
@@ -119,8 +120,10 @@ DevScene dev_scene(const vrs_scene &S)
     d.quats = S.quats;
     d.logits = S.opacity_logits;
     d.sh = S.sh;
+    d.baked = reinterpret_cast<const float4 *>(S.baked);
     d.n = S.n;
     d.K = (S.sh_degree + 1) * (S.sh_degree + 1);
+    d.sh_half = S.sh_half ? 1 : 0;
     return d;
 }
 
@@ -151,6 +154,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     if (o.sort != 0 && o.sort != 1) return VRS_ERR_INVALID;
     if (o.resort != 0 && o.resort != 4 && o.resort != 8 && o.resort != 16) return VRS_ERR_INVALID;
     if (o.resort && (o.backward || (tile == 32 && o.resort > 8))) return VRS_ERR_INVALID;
+    if (o.half_out && o.backward) return VRS_ERR_INVALID;
     vrs_plan P;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
@@ -161,6 +165,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.sort_mode = o.sort;
     P.count_pairs = o.count_pairs ? 1 : 0;
     P.resort = o.resort;
+    P.half_out = o.half_out ? 1 : 0;
     for (int s = 0; s < n_scenes; ++s) {
         if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
         P.scene_n[s] = scenes[s].n;
@@ -319,7 +324,8 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
             at<float4>(workspace, plan->off_raydepth), at<uint32_t>(workspace, plan->off_vals[sb]),
             at<uint2>(workspace, plan->off_ranges), at<DevStatus>(workspace, plan->off_status), rgb, depth,
             T_final, at<uint8_t>(workspace, plan->off_resort_flags), plan->n_tiles, plan->n_records,
-            (unsigned long long)plan->max_instances, plan->resort, static_cast<cudaStream_t>(stream)));
+            (unsigned long long)plan->max_instances, plan->resort, plan->half_out,
+            static_cast<cudaStream_t>(stream)));
     }
     uint32_t *order = at<uint32_t>(workspace, plan->off_order);
     cudaError_t e = launch_render_fwd(
@@ -328,8 +334,8 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         at<DevStatus>(workspace, plan->off_status), rgb, depth, T_final,
         plan->backward ? at<uint32_t>(workspace, plan->off_ncontrib) : nullptr,   // only the reverse pass reads it
         order, order + plan->n_tiles, plan->n_tiles,
-        plan->n_records, (unsigned long long)plan->max_instances, plan->persistent, plan->count_pairs,
-        plan->n_sms, static_cast<cudaStream_t>(stream));
+        plan->n_records, (unsigned long long)plan->max_instances, plan->persistent,
+        plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->n_sms, static_cast<cudaStream_t>(stream));
     return cuda_status(e);
 }
 
@@ -342,6 +348,8 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
     if (!plan->backward) return VRS_ERR_INVALID;
     vrs_status vs = check_scenes(plan, scenes);
     if (vs != VRS_OK) return vs;
+    for (int s = 0; s < plan->n_scenes; ++s)      // the reverse pass needs the parameter form in FP32
+        if (scenes[s].baked || scenes[s].sh_half) return VRS_ERR_INVALID;
     for (int s = 0; s < plan->n_scenes; ++s) {
         const vrs_scene &G = grads[s];
         if (G.n != plan->scene_n[s] || G.sh_degree != plan->scene_deg[s]) return VRS_ERR_INVALID;

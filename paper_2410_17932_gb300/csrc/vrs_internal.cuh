@@ -1,6 +1,7 @@
 // Internal definitions of libvrs (sm_103a).  Not part of the C-ABI.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,7 +22,9 @@ struct DevView {
 
 struct DevScene {
     const float *means, *log_scales, *quats, *logits, *sh;
+    const float4 *baked;       // nullable: 4 float4 per Gaussian (vrs_bake)
     int32_t n, K;
+    int32_t sh_half;           // sh holds IEEE binary16 values
 };
 
 struct ViewTable {
@@ -250,9 +253,16 @@ struct Decision {
     bool clampx, clampy;
 };
 
-// Per view.  `tile` is the tile edge; gw, gh the view's tile grid.
-__device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, float mx, float my,
-                                       float mz, float logit, int tile, Decision &d)
+// Opacity of the decision path: o = 1 / (1 + e^-logit), each operation rounded.
+__device__ __forceinline__ float decision_opacity(float logit)
+{
+    return FDIV(1.0f, FADD(1.0f, exp32_cw(-logit)));
+}
+
+// Per view.  `tile` is the tile edge; gw, gh the view's tile grid; op the
+// opacity (decision_opacity of the logit, or its baked value).
+__device__ __forceinline__ void decide_op(const DevView &V, const GaussPre &g, float mx, float my,
+                                          float mz, float op, int tile, Decision &d)
 {
     d.visible = false;
     const float *W = V.R;
@@ -344,8 +354,6 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     // that floor are monotone, so the tighter of the two rectangles' bounds is
     // the bound of the nearer edge: max(floor(u - r), floor(u - h)) =
     // floor(u - min(r, h)), one exact floor per side instead of two.
-    const float eo = exp32_cw(-logit);
-    const float op = FDIV(1.0f, FADD(1.0f, eo));
     float thr = FMUL(2.0f, log32_cw(FMUL(255.0f, op)));
     thr = FADD(FMUL(thr, 1.001f), 0.001f);
     if (!(thr > 0.0f)) return;
@@ -362,6 +370,19 @@ __device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, floa
     d.y0 = y0;
     d.y1 = y1;
     d.visible = x1 > x0 && y1 > y0;
+}
+
+__device__ __forceinline__ void decide(const DevView &V, const GaussPre &g, float mx, float my,
+                                       float mz, float logit, int tile, Decision &d)
+{
+    decide_op(V, g, mx, my, mz, decision_opacity(logit), tile, d);
+}
+
+// log2 of the opacity as the records hold it: log2(sigmoid(x)) = -log2(1 + e^-x).
+__device__ __forceinline__ float record_log2_opacity(float logit)
+{
+    return logit >= 0.f ? -__log2f(1.0f + __expf(-logit))
+                        : logit * 1.4426950408889634f - __log2f(1.0f + __expf(logit));
 }
 
 #undef FMUL
@@ -642,6 +663,28 @@ __device__ __forceinline__ uint2 live_range(const uint2 *ranges, int64_t t, cons
     r.x = min(r.x, r.y);
     return r;
 }
+
+// Output stores of the blend kernels: FP32, or IEEE binary16 for half-output plans.
+template <bool HALF>
+struct OutStore {
+    __device__ __forceinline__ static void one(float *base, int64_t i, float v) { base[i] = v; }
+    __device__ __forceinline__ static void two(float *base, int64_t i, float2 v)
+    {
+        *reinterpret_cast<float2 *>(base + i) = v;
+    }
+};
+
+template <>
+struct OutStore<true> {
+    __device__ __forceinline__ static void one(float *base, int64_t i, float v)
+    {
+        reinterpret_cast<__half *>(base)[i] = __float2half_rn(v);
+    }
+    __device__ __forceinline__ static void two(float *base, int64_t i, float2 v)
+    {
+        *reinterpret_cast<__half2 *>(reinterpret_cast<__half *>(base) + i) = __float22half2_rn(v);
+    }
+};
 
 // Launch helpers (host).
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }

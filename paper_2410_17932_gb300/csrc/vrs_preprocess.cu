@@ -61,9 +61,31 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
     const int lane = threadIdx.x & 31;
     const bool in = g < p.S.n;
     float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
-    float logit = 0.f;
+    float logit = 0.f, op = 0.f;
     bool ok = in;
-    if (in) {
+    GaussPre pre;
+    bool zero_quat = false;
+    if (in && p.S.baked) {
+        // baked attributes (vrs_bake): the scales, rotation and opacity the lines below
+        // would compute, bit for bit
+        m[0] = __ldg(p.S.means + 3 * g);
+        m[1] = __ldg(p.S.means + 3 * g + 1);
+        m[2] = __ldg(p.S.means + 3 * g + 2);
+        const float4 b0 = __ldg(p.S.baked + 4 * g), b1 = __ldg(p.S.baked + 4 * g + 1);
+        const float4 b2 = __ldg(p.S.baked + 4 * g + 2), b3 = __ldg(p.S.baked + 4 * g + 3);
+        pre.s[0] = b0.x; pre.s[1] = b0.y; pre.s[2] = b0.z;
+        pre.Rq[0] = b0.w; pre.Rq[1] = b1.x; pre.Rq[2] = b1.y; pre.Rq[3] = b1.z; pre.Rq[4] = b1.w;
+        pre.Rq[5] = b2.x; pre.Rq[6] = b2.y; pre.Rq[7] = b2.z; pre.Rq[8] = b2.w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pre.M[3 * k + j] = __fmul_rn(pre.Rq[3 * k + j], pre.s[j]);
+        op = b3.x;
+        const uint32_t bst = __float_as_uint(b3.z);
+        const float chk = __fmaf_rn(m[0], 0.f, __fmaf_rn(m[1], 0.f, __fmaf_rn(m[2], 0.f, 0.f)));
+        zero_quat = (bst & 1u) != 0;
+        ok = isfinite(chk) && bst == 0u;
+    } else if (in) {
         m[0] = __ldg(p.S.means + 3 * g);
         m[1] = __ldg(p.S.means + 3 * g + 1);
         m[2] = __ldg(p.S.means + 3 * g + 2);
@@ -86,12 +108,11 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
 #pragma unroll
         for (int i = 0; i < 11; ++i) chk = __fmaf_rn(vals[i], 0.f, chk);
         if (!isfinite(chk)) ok = false;
-    }
-    GaussPre pre;
-    bool zero_quat = false;
-    if (ok && !gauss_pre(ls, q, pre)) {
-        ok = false;
-        zero_quat = true;
+        if (ok && !gauss_pre(ls, q, pre)) {
+            ok = false;
+            zero_quat = true;
+        }
+        op = decision_opacity(logit);
     }
     if (in && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
     if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
@@ -105,7 +126,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
         const DevView &V = vt.v[p.views[vi]];
         Decision d;
         d.visible = false;
-        if (ok) decide(V, pre, m[0], m[1], m[2], logit, vt.tile, d);
+        if (ok) decide_op(V, pre, m[0], m[1], m[2], op, vt.tile, d);
         const uint32_t vb = wok ? __ballot_sync(FULL, d.visible) : 0u;
         const int par = vi & 1;
         if (lane == 0) s_cnt[par][wp] = __popc(vb);
@@ -134,7 +155,61 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
     }
 }
 
-template <int K>
+// SH coefficient rows in FP32 or, for scenes stored in half precision, IEEE binary16.
+template <bool HALF>
+struct ShRow;
+
+template <>
+struct ShRow<false> {
+    // visits the 3K coefficients of row g in order: f(index, value)
+    template <int K, typename F>
+    __device__ __forceinline__ static void visit(const float *sh, int g, F f)
+    {
+        const float *src = sh + (size_t)g * 3 * K;
+        if ((12 * K) % 16 == 0 && (reinterpret_cast<uintptr_t>(sh) & 15u) == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+            for (int c = 0; c < 3 * K / 4; ++c) {
+                const float4 v4 = __ldg(s4 + c);
+                f(4 * c, v4.x);
+                f(4 * c + 1, v4.y);
+                f(4 * c + 2, v4.z);
+                f(4 * c + 3, v4.w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3 * K; ++i) f(i, __ldg(src + i));
+        }
+    }
+};
+
+template <>
+struct ShRow<true> {
+    template <int K, typename F>
+    __device__ __forceinline__ static void visit(const float *sh, int g, F f)
+    {
+        const __half *src = reinterpret_cast<const __half *>(sh) + (size_t)g * 3 * K;
+        if ((6 * K) % 16 == 0 && (reinterpret_cast<uintptr_t>(sh) & 15u) == 0) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll
+            for (int c = 0; c < 3 * K / 8; ++c) {
+                const uint4 v = __ldg(s4 + c);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+                    f(8 * c + 2 * e, h.x);
+                    f(8 * c + 2 * e + 1, h.y);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3 * K; ++i) f(i, __half2float(src[i]));
+        }
+    }
+};
+
+template <int K, bool HALF>
 __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ ViewTable vt,
                                                         const __grid_constant__ PreParams p)
 {
@@ -142,7 +217,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
     const int lane = threadIdx.x & 31;
     const unsigned long long n_pairs_raw = p.st->scene_pairs[p.scene];
     const unsigned long long n_pairs = n_pairs_raw < p.pair_cap ? n_pairs_raw : p.pair_cap;
-    const bool vec = (12 * K) % 16 == 0 && (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
     bool nonfinite_sh = false;
     __shared__ uint32_t s_wtot[kPairThreads / 32];
     __shared__ unsigned long long s_wbase[kPairThreads / 32];
@@ -171,10 +245,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             mx = __ldg(p.S.means + 3 * g);
             my = __ldg(p.S.means + 3 * g + 1);
             mz = __ldg(p.S.means + 3 * g + 2);
-            const float logit = __ldg(p.S.logits + g);
-            // log2(sigmoid(x)) = -log2(1 + e^-x)
-            lo = logit >= 0.f ? -__log2f(1.0f + __expf(-logit))
-                              : logit * 1.4426950408889634f - __log2f(1.0f + __expf(logit));
+            lo = p.S.baked ? __ldg(p.S.baked + 4 * g + 3).y : record_log2_opacity(__ldg(p.S.logits + g));
             // colour from the view direction (camera centre = -R^T t)
             const float cc0 = -(V.R[0] * V.t[0] + V.R[3] * V.t[1] + V.R[6] * V.t[2]);
             const float cc1 = -(V.R[1] * V.t[0] + V.R[4] * V.t[1] + V.R[7] * V.t[2]);
@@ -185,29 +256,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
             float Y[16];
             sh_basis(dx, dy, dz, K, Y);
             float shs = 0.f;
-            const float *src = p.S.sh + (size_t)g * 3 * K;
-            if (vec) {
-                const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-                for (int c = 0; c < 3 * K / 4; ++c) {
-                    const float4 v4 = __ldg(s4 + c);
-                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        shs = __fmaf_rn(vv[e], 0.f, shs);     // NaN iff some value is not finite
-                        col[(4 * c + e) % 3] += Y[(4 * c + e) / 3] * vv[e];
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < K; ++k)
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        const float v = __ldg(src + 3 * k + ch);
-                        shs = __fmaf_rn(v, 0.f, shs);
-                        col[ch] += Y[k] * v;
-                    }
-            }
+            ShRow<HALF>::template visit<K>(p.S.sh, g, [&](int i, float v) {
+                shs = __fmaf_rn(v, 0.f, shs);       // NaN iff some value is not finite
+                col[i % 3] += Y[i / 3] * v;
+            });
             if (!isfinite(shs)) {
                 vis = false;
                 nonfinite_sh = true;
@@ -239,19 +291,33 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
                 // e_k = W R_k of the Gaussian and u, v the pixel centre minus the principal
                 // point, a_k = (e_k . (u/fx, v/fy, 1)) / s_k and b_k = (e_k . mu_cam) / s_k;
                 // the record holds (e_kx / (fx s_k), e_ky / (fy s_k), e_kz / s_k, b_k)
-                float q[4];
+                // scales and rotation as the decision path has them (or baked), so that baked
+                // and parameter scenes key and order alike
+                float sk[3], Rq[9];
+                if (p.S.baked) {
+                    const float4 b0 = __ldg(p.S.baked + 4 * g), b1 = __ldg(p.S.baked + 4 * g + 1);
+                    const float4 b2 = __ldg(p.S.baked + 4 * g + 2);
+                    sk[0] = b0.x; sk[1] = b0.y; sk[2] = b0.z;
+                    Rq[0] = b0.w; Rq[1] = b1.x; Rq[2] = b1.y; Rq[3] = b1.z; Rq[4] = b1.w;
+                    Rq[5] = b2.x; Rq[6] = b2.y; Rq[7] = b2.z; Rq[8] = b2.w;
+                } else {
+                    float lsv[3], q[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
-                const float iq = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-                const float w = q[0] * iq, x = q[1] * iq, y = q[2] * iq, z = q[3] * iq;
-                const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
-                                     2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
-                                     2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+                    for (int i = 0; i < 3; ++i) lsv[i] = __ldg(p.S.log_scales + 3 * g + i);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
+                    GaussPre gp;
+                    gauss_pre(lsv, q, gp);          // visible, so the quaternion is not zero
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) sk[i] = gp.s[i];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Rq[i] = gp.Rq[i];
+                }
                 const float mc0 = xh + xl, mc1 = yh + yl, mc2 = zh + zl;
                 float4 *rdp = p.raydepth + (size_t)(V.rec_base + g) * 3;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float is = __expf(-__ldg(p.S.log_scales + 3 * g + k));
+                    const float is = 1.0f / sk[k];
                     const float e0 = V.R[0] * Rq[k] + V.R[1] * Rq[3 + k] + V.R[2] * Rq[6 + k];
                     const float e1_ = V.R[3] * Rq[k] + V.R[4] * Rq[3 + k] + V.R[5] * Rq[6 + k];
                     const float e2 = V.R[6] * Rq[k] + V.R[7] * Rq[3 + k] + V.R[8] * Rq[6 + k];
@@ -406,11 +472,15 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     (void)n_sms;
     const int64_t want = grid_for((int64_t)S.n * n_views, kPairThreads);
     const unsigned grid = (unsigned)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
-    switch (S.K) {
-        case 1: k_pairs<1><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 4: k_pairs<4><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 9: k_pairs<9><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 16: k_pairs<16><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+    switch (S.K + (S.sh_half ? 100 : 0)) {
+        case 1: k_pairs<1, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 4: k_pairs<4, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 9: k_pairs<9, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 16: k_pairs<16, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 101: k_pairs<1, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 104: k_pairs<4, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 109: k_pairs<9, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 116: k_pairs<16, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

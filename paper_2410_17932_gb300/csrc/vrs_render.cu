@@ -32,6 +32,7 @@ struct FwdArgs {
     int64_t n_records;
     unsigned long long cap;
     int persistent;
+    int half_out;               // write the outputs as IEEE binary16
 };
 
 // The state of a thread's two pixels, packed in pairs so that the blend's
@@ -98,7 +99,7 @@ __device__ __forceinline__ float2 pair_u2v(const float4 &A, const float4 &B, flo
     return __ffma2_rn(t, t, f2(w));
 }
 
-template <int TS, bool COUNT, bool LAST, bool PERSIST>
+template <int TS, bool COUNT, bool LAST, bool PERSIST, bool HALF = false>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCKS)
     k_render_fwd(const __grid_constant__ ViewTable vt, const FwdArgs a)
 {
@@ -218,27 +219,31 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
         const bool bases8 = ((reinterpret_cast<uintptr_t>(a.rgb) | reinterpret_cast<uintptr_t>(a.depth) |
                               reinterpret_cast<uintptr_t>(a.Tf) | reinterpret_cast<uintptr_t>(a.ncontrib)) & 7u) == 0;
         const bool pair = bases8 && in1 && ((3 * V.pix_base + lp) & 1) == 0 && (HW & 1) == 0 && (pix & 1) == 0;
+        // (half-output plans address the same planes as binary16 arrays; rgb is then
+        // a half pointer in float's clothing, offset by element counts below)
+        using O = OutStore<HALF>;
+        float *rgbv = HALF ? reinterpret_cast<float *>(reinterpret_cast<__half *>(a.rgb) + 3 * V.pix_base) : rgb;
         if (pair) {
-            *reinterpret_cast<float2 *>(rgb + lp) = P.R;
-            *reinterpret_cast<float2 *>(rgb + HW + lp) = P.G;
-            *reinterpret_cast<float2 *>(rgb + 2 * HW + lp) = P.B;
-            *reinterpret_cast<float2 *>(a.depth + pix) = P.D;
-            *reinterpret_cast<float2 *>(a.Tf + pix) = P.T;
+            O::two(rgbv, lp, P.R);
+            O::two(rgbv, HW + lp, P.G);
+            O::two(rgbv, 2 * HW + lp, P.B);
+            O::two(a.depth, pix, P.D);
+            O::two(a.Tf, pix, P.T);
             if (LAST) *reinterpret_cast<uint2 *>(a.ncontrib + pix) = make_uint2(P.last0, P.last1);
         } else if (in0) {
-            rgb[lp] = P.R.x;
-            rgb[HW + lp] = P.G.x;
-            rgb[2 * HW + lp] = P.B.x;
-            a.depth[pix] = P.D.x;
-            a.Tf[pix] = P.T.x;
+            O::one(rgbv, lp, P.R.x);
+            O::one(rgbv, HW + lp, P.G.x);
+            O::one(rgbv, 2 * HW + lp, P.B.x);
+            O::one(a.depth, pix, P.D.x);
+            O::one(a.Tf, pix, P.T.x);
             if (LAST) a.ncontrib[pix] = P.last0;
         }
         if (in1 && !pair) {
-            rgb[lp + 1] = P.R.y;
-            rgb[HW + lp + 1] = P.G.y;
-            rgb[2 * HW + lp + 1] = P.B.y;
-            a.depth[pix + 1] = P.D.y;
-            a.Tf[pix + 1] = P.T.y;
+            O::one(rgbv, lp + 1, P.R.y);
+            O::one(rgbv, HW + lp + 1, P.G.y);
+            O::one(rgbv, 2 * HW + lp + 1, P.B.y);
+            O::one(a.depth, pix + 1, P.D.y);
+            O::one(a.Tf, pix + 1, P.T.y);
             if (LAST) a.ncontrib[pix + 1] = P.last1;
         }
     }
@@ -301,7 +306,8 @@ static void launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool
 {
     // the last-blended-position plane is written only when the caller keeps it
     constexpr int T = BlendCfg<TS>::THREADS;
-    if (count && a.ncontrib) k_render_fwd<TS, true, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
+    if (a.half_out) k_render_fwd<TS, false, false, PERSIST, true><<<grid, T, 0, s>>>(vt, a);
+    else if (count && a.ncontrib) k_render_fwd<TS, true, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
     else if (count) k_render_fwd<TS, true, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
     else if (a.ncontrib) k_render_fwd<TS, false, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
     else k_render_fwd<TS, false, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
@@ -321,10 +327,11 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              unsigned long long cap, int persistent, int count, int n_sms,
+                              unsigned long long cap, int persistent, int count, int half_out, int n_sms,
                               cudaStream_t s)
 {
     FwdArgs a;
+    a.half_out = half_out;
     a.cap = cap;
     a.viewtab = viewtab;
     a.rec = rec;

@@ -33,6 +33,7 @@ struct ResortArgs {
     uint8_t *flags;
     int64_t n_records;
     unsigned long long cap;
+    int half_out;
 };
 
 // Order-preserving map of a float to an unsigned integer, and back.
@@ -139,7 +140,7 @@ __device__ __forceinline__ void rs_drain(RsPix &P, const RsWin<K> &W, int col)
 
 __device__ __forceinline__ float2 f2r(float a) { return make_float2(a, a); }
 
-template <int TS, int K>
+template <int TS, int K, bool HALF>
 __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     k_render_resort(const __grid_constant__ ViewTable vt, const ResortArgs a)
 {
@@ -261,21 +262,23 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const int64_t HW = (int64_t)V.w * V.h;
     const int64_t lp = (int64_t)py * V.w + px;
     const int64_t pix = V.pix_base + lp;
-    float *rgb = a.rgb + 3 * V.pix_base;
+    using O = OutStore<HALF>;
+    float *rgb = HALF ? reinterpret_cast<float *>(reinterpret_cast<__half *>(a.rgb) + 3 * V.pix_base)
+                      : a.rgb + 3 * V.pix_base;
     if (in0) {
-        rgb[lp] = P0.R;
-        rgb[HW + lp] = P0.G;
-        rgb[2 * HW + lp] = P0.B;
-        a.depth[pix] = P0.D;
-        a.Tf[pix] = P0.T;
+        O::one(rgb, lp, P0.R);
+        O::one(rgb, HW + lp, P0.G);
+        O::one(rgb, 2 * HW + lp, P0.B);
+        O::one(a.depth, pix, P0.D);
+        O::one(a.Tf, pix, P0.T);
         a.flags[pix] = P0.flag ? 1 : 0;
     }
     if (in1) {
-        rgb[lp + 1] = P1.R;
-        rgb[HW + lp + 1] = P1.G;
-        rgb[2 * HW + lp + 1] = P1.B;
-        a.depth[pix + 1] = P1.D;
-        a.Tf[pix + 1] = P1.T;
+        O::one(rgb, lp + 1, P1.R);
+        O::one(rgb, HW + lp + 1, P1.G);
+        O::one(rgb, 2 * HW + lp + 1, P1.B);
+        O::one(a.depth, pix + 1, P1.D);
+        O::one(a.Tf, pix + 1, P1.T);
         a.flags[pix + 1] = P1.flag ? 1 : 0;
     }
     const uint32_t nf = __reduce_add_sync(FULL, (in0 && P0.flag ? 1u : 0u) + (in1 && P1.flag ? 1u : 0u));
@@ -284,16 +287,23 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     if (tid == 0 && s_flagged) atomicAdd(&a.st->resort_flagged, s_flagged);
 }
 
-template <int TS, int K>
-static cudaError_t launch_resort_tk(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, cudaStream_t s)
+template <int TS, int K, bool HALF>
+static cudaError_t launch_resort_tkh(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, cudaStream_t s)
 {
     constexpr int T = BlendCfg<TS>::THREADS;
     const size_t smem = (size_t)K * 2 * T * (sizeof(float4) + sizeof(uint32_t));
-    cudaError_t e = cudaFuncSetAttribute(k_render_resort<TS, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_render_resort<TS, K, HALF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_render_resort<TS, K><<<(unsigned)n_tiles, T, smem, s>>>(vt, a);
+    k_render_resort<TS, K, HALF><<<(unsigned)n_tiles, T, smem, s>>>(vt, a);
     return cudaGetLastError();
+}
+
+template <int TS, int K>
+static cudaError_t launch_resort_tk(const ViewTable &vt, const ResortArgs &a, int64_t n_tiles, cudaStream_t s)
+{
+    return a.half_out ? launch_resort_tkh<TS, K, true>(vt, a, n_tiles, s)
+                      : launch_resort_tkh<TS, K, false>(vt, a, n_tiles, s);
 }
 
 template <int TS>
@@ -314,9 +324,10 @@ cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, con
                                  const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
                                  DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
                                  int64_t n_tiles, int64_t n_records, unsigned long long cap, int window,
-                                 cudaStream_t s)
+                                 int half_out, cudaStream_t s)
 {
     ResortArgs a;
+    a.half_out = half_out;
     a.viewtab = viewtab;
     a.rec = rec;
     a.raydepth = raydepth;

@@ -20,13 +20,17 @@ PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 @dataclass
 class SceneTensors:
-    """One scene's Gaussian parameters as contiguous float32 CUDA tensors."""
+    """One scene's Gaussian parameters as contiguous float32 CUDA tensors.
+
+    For inference a scene may carry `baked` attributes (see `baked_scene`), and its
+    SH coefficients may be float16 (see `half_sh`)."""
     means: torch.Tensor
     log_scales: torch.Tensor
     quats: torch.Tensor
     opacity_logits: torch.Tensor
     sh: torch.Tensor
     sh_degree: int
+    baked: Optional[torch.Tensor] = None
 
     @property
     def n(self) -> int:
@@ -47,16 +51,37 @@ class SceneTensors:
         return SceneTensors(*[torch.zeros_like(x, requires_grad=False) for x in self.tensors()],
                             self.sh_degree)
 
+    def baked_scene(self, stream=None) -> "SceneTensors":
+        """The same scene with its activations baked by vrs_bake (Sec. 4 "Inference"):
+        renders bit for bit like this one, without evaluating them per frame."""
+        baked = torch.empty((self.n, L.VRS_BAKED_FLOATS), dtype=torch.float32, device=self.means.device)
+        L._check(L.vrs_bake(scene_struct(self), baked.data_ptr() if self.n else None, _stream_handle(stream)),
+                 "vrs_bake")
+        return SceneTensors(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh,
+                            self.sh_degree, baked)
+
+    def half_sh(self) -> "SceneTensors":
+        """The same scene with its SH coefficients stored in float16 (inference)."""
+        return SceneTensors(self.means, self.log_scales, self.quats, self.opacity_logits,
+                            self.sh.to(torch.float16).contiguous(), self.sh_degree, self.baked)
+
 
 def scene_struct(st: SceneTensors) -> L.vrs_scene:
     s = L.vrs_scene()
     for name in PARAM_NAMES:
         x = getattr(st, name)
-        if x.numel() and (not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous()):
-            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        ok_dtype = x.dtype == torch.float32 or (name == "sh" and x.dtype == torch.float16)
+        if x.numel() and (not x.is_cuda or not ok_dtype or not x.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor (sh may be float16)")
         setattr(s, name, x.data_ptr() if x.numel() else None)
     s.n = st.n
     s.sh_degree = st.sh_degree
+    s.sh_half = 1 if st.sh.dtype == torch.float16 else 0
+    if st.baked is not None:
+        b = st.baked
+        if not b.is_cuda or b.dtype != torch.float32 or not b.is_contiguous() or tuple(b.shape) != (st.n, L.VRS_BAKED_FLOATS):
+            raise ValueError("baked must be a contiguous float32 CUDA tensor [n, 16]")
+        s.baked = b.data_ptr() if st.n else None
     return s
 
 
@@ -86,7 +111,7 @@ class Rasterizer:
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
                  persistent: bool = False, backward: bool = False, max_instances: int = 0,
-                 sort: int = 0, resort: int = 0, device="cuda"):
+                 sort: int = 0, resort: int = 0, half_out: bool = False, device="cuda"):
         self.scenes = list(scenes)
         self.views = list(views)
         self.device = torch.device(device)
@@ -95,6 +120,7 @@ class Rasterizer:
         self.backward = bool(backward)
         self.sort = int(sort)
         self.resort = int(resort)    # 0: list order; 4/8/16: per-pixel order through a window of that size
+        self.half_out = bool(half_out)   # outputs as float16 (inference)
         self.generation = 0          # forward passes and re-plans; the autograd glue checks it
         self._make_plan(max_instances)
 
@@ -105,15 +131,16 @@ class Rasterizer:
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
         opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), self.sort,
-                               int(max_instances), 0, self.resort)
+                               int(max_instances), 0, self.resort, int(self.half_out), 0)
         plan = L.vrs_plan()
         L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
         self.plan = plan
         self.workspace = torch.empty(int(plan.workspace_bytes), dtype=torch.uint8, device=self.device)
         P = int(plan.n_pixels)
-        self.rgb = torch.empty(3 * P, dtype=torch.float32, device=self.device)
-        self.depth = torch.empty(P, dtype=torch.float32, device=self.device)
-        self.T = torch.empty(P, dtype=torch.float32, device=self.device)
+        dt = torch.float16 if self.half_out else torch.float32
+        self.rgb = torch.empty(3 * P, dtype=dt, device=self.device)
+        self.depth = torch.empty(P, dtype=dt, device=self.device)
+        self.T = torch.empty(P, dtype=dt, device=self.device)
 
     def set_views(self, views: Sequence):
         """New poses for views of the same sizes (no re-plan)."""

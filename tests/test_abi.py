@@ -55,6 +55,7 @@ int main(void) {
   P(vrs_plan_opts, max_instances) P(vrs_plan, off_pairs) P(vrs_cull_opts, abs_margin)
   P(vrs_run_info, visible_pairs) P(vrs_run_info, resort_flagged) P(vrs_plan, resort)
   P(vrs_plan, off_raydepth) P(vrs_plan, off_resort_flags) P(vrs_plan_opts, resort)
+  P(vrs_scene, baked) P(vrs_scene, sh_half) P(vrs_plan_opts, half_out) P(vrs_plan, half_out)
   return 0;
 }
 """
