@@ -129,6 +129,10 @@ typedef struct {
                               vrs_render_fwd); forward only (backward must be 0) */
     int32_t half_out;      /* 1 = vrs_render_fwd writes rgb, depth and T_final as IEEE binary16
                               (half the output bytes; inference only, backward must be 0) */
+    int32_t key_bits;      /* 0 = the minimal radix-sort key width (tile-id bits + 32); otherwise a
+                              width of at least that, up to 64 (more passes, the same order) */
+    int32_t tiles_per_pull;/* persistent blend: work-order items a CTA claims per atomic (1..64;
+                              0 = 1); any value gives the same images */
     int32_t reserved;
 } vrs_plan_opts;
 
@@ -179,6 +183,8 @@ typedef struct {
     int64_t view_pix_base[VRS_MAX_VIEWS];   /* view v's pixels start at element view_pix_base[v] */
     int32_t resort;            /* vrs_plan_opts.resort */
     int32_t half_out;          /* vrs_plan_opts.half_out */
+    int32_t tiles_per_pull;    /* vrs_plan_opts.tiles_per_pull (>= 1) */
+    int32_t reserved;
     int64_t off_raydepth;      /* resort plans: [n_records][3] float4, per record the terms of the
                                   per-pixel depth (see vrs_render_fwd); 0 otherwise */
     int64_t off_resort_flags;  /* resort plans: [n_pixels] uint8, 1 where the pixel's sorting

@@ -43,7 +43,7 @@ class vrs_camera(ctypes.Structure):
 class vrs_plan_opts(ctypes.Structure):
     _fields_ = [("tile", _i32), ("persistent", _i32), ("backward", _i32), ("sort", _i32),
                 ("max_instances", _i64), ("count_pairs", _i32), ("resort", _i32), ("half_out", _i32),
-                ("reserved", _i32)]
+                ("key_bits", _i32), ("tiles_per_pull", _i32), ("reserved", _i32)]
 
 
 class vrs_plan(ctypes.Structure):
@@ -61,7 +61,8 @@ class vrs_plan(ctypes.Structure):
                 ("view_h", _i32 * VRS_MAX_VIEWS), ("view_gw", _i32 * VRS_MAX_VIEWS),
                 ("view_gh", _i32 * VRS_MAX_VIEWS), ("view_rec_base", _i64 * VRS_MAX_VIEWS),
                 ("view_tile_base", _i64 * VRS_MAX_VIEWS), ("view_pix_base", _i64 * VRS_MAX_VIEWS),
-                ("resort", _i32), ("half_out", _i32), ("off_raydepth", _i64), ("off_resort_flags", _i64)]
+                ("resort", _i32), ("half_out", _i32), ("tiles_per_pull", _i32), ("reserved", _i32),
+                ("off_raydepth", _i64), ("off_resort_flags", _i64)]
 
 
 class vrs_run_info(ctypes.Structure):

@@ -9,9 +9,11 @@ replayed every frame.
 
 The tuner times candidate plans on the caller's own batch and caches the
 fastest under a key of (GPU name, view sizes, scene sizes):
-  - blend schedule: one CTA per tile, or the persistent longest-first grid;
-  - sort: tile buckets, or the global LSD radix sort (the key width is the
-    plan's minimal tile-id bits + 32 either way);
+  - blend schedule: one CTA per tile, or the persistent longest-first grid,
+    whose CTAs claim 1 or 4 tiles of the work order per atomic (the
+    batch-per-block knob);
+  - sort: tile buckets, or the global LSD radix sort with the minimal key
+    width (tile-id bits + 32) or the full 64 bits;
   - tile edge 8 / 16 / 32 only when ``allow_tile_change`` is set, because the
     tile size changes which splats a pixel sees (pixels also see a splat
     beyond its 3-sigma ellipse inside the tiles it touches).
@@ -35,7 +37,7 @@ CACHE_PATH = os.environ.get("VRS_AUTOTUNE_CACHE",
 
 def _key(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: bool) -> str:
     dev = torch.cuda.get_device_name()
-    sig = json.dumps([dev, [(v.width, v.height, v.scene) for v in views],
+    sig = json.dumps(["v2", dev, [(v.width, v.height, v.scene) for v in views],
                       [(s.n, s.sh_degree) for s in scenes], allow_tile_change])
     return hashlib.sha1(sig.encode()).hexdigest()
 
@@ -78,12 +80,19 @@ def time_ms(fn, iters: int = 20, warmup: int = 3) -> float:
 
 def candidates(allow_tile_change: bool, tile: int = 16) -> List[Dict]:
     tiles = (8, 16, 32) if allow_tile_change else (tile,)
-    return [dict(tile=t, persistent=p, sort=s) for t, p, s in itertools.product(tiles, (0, 1), (0, 1))]
+    out = []
+    for t, p, s in itertools.product(tiles, (0, 1), (0, 1)):
+        for pull in ((1, 4) if p else (1,)):
+            for kb in ((0, 64) if s == 1 and pull == 1 else (0,)):
+                out.append(dict(tile=t, persistent=p, sort=s, tiles_per_pull=pull, key_bits=kb))
+    return out
 
 
 def tune(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: bool = False,
-         tile: int = 16, iters: int = 10, use_cache: bool = True, verbose: bool = False) -> Dict:
-    """Returns the fastest {tile, persistent, sort} for this batch (cached)."""
+         tile: int = 16, iters: int = 10, use_cache: bool = True, verbose: bool = False,
+         timings_out: Optional[list] = None) -> Dict:
+    """Returns the fastest plan options {tile, persistent, sort, tiles_per_pull, key_bits} for
+    this batch (cached); timings_out, when given, receives every (ms, options) measured."""
     key = _key(scenes, views, allow_tile_change)
     cache = {}
     if use_cache and os.path.exists(CACHE_PATH):
@@ -105,6 +114,8 @@ def tune(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: boo
         del runner, ras
     results.sort(key=lambda x: x[0])
     best = results[0][1]
+    if timings_out is not None:
+        timings_out.extend(results)
     if use_cache:
         cache[key] = {"best": best, "timings": [(ms, c) for ms, c in results]}
         try:
@@ -114,3 +125,29 @@ def tune(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: boo
         except OSError:
             pass
     return best
+
+
+class ViewsGraphRunner:
+    """One CUDA graph replaying several rasterizers' forward passes one after another
+    (the per-view baseline of a batch, captured the same way as the batched frame)."""
+
+    def __init__(self, rasterizers: Sequence[Rasterizer], warmup: int = 2):
+        self.rasterizers = list(rasterizers)
+        for r in self.rasterizers:
+            r.forward()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                for r in self.rasterizers:
+                    r.forward_async()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            for r in self.rasterizers:
+                r.forward_async()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()

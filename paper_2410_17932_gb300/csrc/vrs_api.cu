@@ -22,8 +22,8 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              unsigned long long cap, int persistent, int count, int half_out, int n_sms,
-                              cudaStream_t s);
+                              unsigned long long cap, int persistent, int count, int half_out,
+                              int tiles_per_pull, int n_sms, cudaStream_t s);
 cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                                  const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
                                  DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
@@ -155,6 +155,8 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     if (o.resort != 0 && o.resort != 4 && o.resort != 8 && o.resort != 16) return VRS_ERR_INVALID;
     if (o.resort && (o.backward || (tile == 32 && o.resort > 8))) return VRS_ERR_INVALID;
     if (o.half_out && o.backward) return VRS_ERR_INVALID;
+    if (o.tiles_per_pull < 0 || o.tiles_per_pull > 64) return VRS_ERR_INVALID;
+    if (o.key_bits < 0 || o.key_bits > 64) return VRS_ERR_INVALID;
     vrs_plan P;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
@@ -166,6 +168,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.count_pairs = o.count_pairs ? 1 : 0;
     P.resort = o.resort;
     P.half_out = o.half_out ? 1 : 0;
+    P.tiles_per_pull = o.tiles_per_pull > 0 ? o.tiles_per_pull : 1;
     for (int s = 0; s < n_scenes; ++s) {
         if (scenes[s].n < 0 || scenes[s].sh_degree < 0 || scenes[s].sh_degree > 3) return VRS_ERR_INVALID;
         P.scene_n[s] = scenes[s].n;
@@ -193,6 +196,10 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.n_tiles = tiles;
     P.n_pixels = pix;
     P.key_bits = 32 + bits_for(tiles);
+    if (o.key_bits) {                     // a wider radix key: more passes, the same order
+        if (o.key_bits < P.key_bits) return VRS_ERR_INVALID;
+        P.key_bits = o.key_bits;
+    }
     P.sort_passes = (P.key_bits + 7) / 8;
     P.sorted_buf = P.sort_mode == 0 ? 0 : P.sort_passes % 2;
     int64_t cap = o.max_instances > 0 ? o.max_instances : 4 * rec + 65536;
@@ -335,7 +342,8 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         plan->backward ? at<uint32_t>(workspace, plan->off_ncontrib) : nullptr,   // only the reverse pass reads it
         order, order + plan->n_tiles, plan->n_tiles,
         plan->n_records, (unsigned long long)plan->max_instances, plan->persistent,
-        plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->n_sms, static_cast<cudaStream_t>(stream));
+        plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->tiles_per_pull, plan->n_sms,
+        static_cast<cudaStream_t>(stream));
     return cuda_status(e);
 }
 

@@ -33,6 +33,7 @@ struct FwdArgs {
     unsigned long long cap;
     int persistent;
     int half_out;               // write the outputs as IEEE binary16
+    int tiles_per_pull;         // persistent: work-order items claimed per atomic
 };
 
 // The state of a thread's two pixels, packed in pairs so that the blend's
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
     __shared__ uint32_t smask[Cfg::BATCH];
     __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
     __shared__ int64_t s_tile;
+    __shared__ uint32_t s_k, s_left;      // persistent: the CTA's claimed run of the work order
     __shared__ unsigned long long s_cnt[3];
 
     const unsigned FULL = 0xffffffffu;
@@ -116,7 +118,10 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
     const float2 pxc2 = make_float2(pxc, pxc + 1.0f);
     const uint32_t lmask = lanemask_lt();
-    if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0ull;
+    if (tid == 0) {
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0ull;
+        s_left = 0u;
+    }
     __syncthreads();
     const bool skip_all = (a.st->flags & ST_CAPACITY) != 0;
     uint32_t n_eval = 0, n_blend = 0, n_blk = 0;
@@ -125,7 +130,13 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
         int64_t t;
         if (PERSIST) {
             if (tid == 0) {
-                const uint32_t k = atomicAdd(&a.st->work[0], 1u);
+                // one atomic claims the next tiles_per_pull items of the order
+                if (s_left == 0u) {
+                    s_k = atomicAdd(&a.st->work[0], (uint32_t)a.tiles_per_pull);
+                    s_left = (uint32_t)a.tiles_per_pull;
+                }
+                const uint32_t k = s_k + ((uint32_t)a.tiles_per_pull - s_left);
+                --s_left;
                 s_tile = (int64_t)k < a.n_tiles ? (int64_t)a.order[k] : -1;
             }
             __syncthreads();
@@ -327,11 +338,12 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
-                              unsigned long long cap, int persistent, int count, int half_out, int n_sms,
-                              cudaStream_t s)
+                              unsigned long long cap, int persistent, int count, int half_out,
+                              int tiles_per_pull, int n_sms, cudaStream_t s)
 {
     FwdArgs a;
     a.half_out = half_out;
+    a.tiles_per_pull = tiles_per_pull < 1 ? 1 : tiles_per_pull;
     a.cap = cap;
     a.viewtab = viewtab;
     a.rec = rec;

@@ -111,7 +111,8 @@ class Rasterizer:
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
                  persistent: bool = False, backward: bool = False, max_instances: int = 0,
-                 sort: int = 0, resort: int = 0, half_out: bool = False, device="cuda"):
+                 sort: int = 0, resort: int = 0, half_out: bool = False, key_bits: int = 0,
+                 tiles_per_pull: int = 1, device="cuda"):
         self.scenes = list(scenes)
         self.views = list(views)
         self.device = torch.device(device)
@@ -121,6 +122,8 @@ class Rasterizer:
         self.sort = int(sort)
         self.resort = int(resort)    # 0: list order; 4/8/16: per-pixel order through a window of that size
         self.half_out = bool(half_out)   # outputs as float16 (inference)
+        self.key_bits = int(key_bits)    # radix key width, 0 = minimal
+        self.tiles_per_pull = int(tiles_per_pull)
         self.generation = 0          # forward passes and re-plans; the autograd glue checks it
         self._make_plan(max_instances)
 
@@ -131,7 +134,8 @@ class Rasterizer:
         self._scene_arr = (L.vrs_scene * n_s)(*[scene_struct(s) for s in self.scenes])
         self._view_arr = (L.vrs_camera * n_v)(*[camera_struct(v) for v in self.views])
         opts = L.vrs_plan_opts(self.tile, int(self.persistent), int(self.backward), self.sort,
-                               int(max_instances), 0, self.resort, int(self.half_out), 0)
+                               int(max_instances), 0, self.resort, int(self.half_out), self.key_bits,
+                               self.tiles_per_pull, 0)
         plan = L.vrs_plan()
         L._check(L.vrs_plan_batch(self._scene_arr, n_s, self._view_arr, n_v, opts, plan), "vrs_plan_batch")
         self.plan = plan

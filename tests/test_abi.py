@@ -56,6 +56,7 @@ int main(void) {
   P(vrs_run_info, visible_pairs) P(vrs_run_info, resort_flagged) P(vrs_plan, resort)
   P(vrs_plan, off_raydepth) P(vrs_plan, off_resort_flags) P(vrs_plan_opts, resort)
   P(vrs_scene, baked) P(vrs_scene, sh_half) P(vrs_plan_opts, half_out) P(vrs_plan, half_out)
+  P(vrs_plan_opts, key_bits) P(vrs_plan_opts, tiles_per_pull) P(vrs_plan, tiles_per_pull)
   return 0;
 }
 """

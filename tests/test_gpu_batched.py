@@ -65,6 +65,7 @@ def test_autotune_choice_keeps_images(tmp_path, monkeypatch):
     sts = [SceneTensors.from_scene(s) for s in scenes]
     best = autotune.tune(sts, views, iters=3)
     assert best["tile"] == 16 and best["persistent"] in (0, 1) and best["sort"] in (0, 1)
+    assert best["tiles_per_pull"] in (1, 4) and best["key_bits"] in (0, 64)
     assert autotune.tune(sts, views) == best          # served from the cache
     a = Rasterizer(sts, views)
     b = Rasterizer(sts, views, **best)
@@ -105,3 +106,36 @@ def test_batched_full_size_views_match_oracle():
         rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(v)]
         w = compare_images((rgb, depth, T), orc, f"view{v}")
         print(f"batched view{v} {cam.width}x{cam.height} scene {cam.scene}: {w}")
+
+
+def test_schedule_and_key_width_knobs_keep_images():
+    """Tiles per pull of the persistent blend and the radix key width change no image."""
+    torch = torch_cuda()
+    scenes, views = _multiview(0.01)
+    ref, sts = make_rasterizer(scenes, views)
+    ref.forward()
+    for kw in (dict(persistent=True, tiles_per_pull=4), dict(persistent=True, tiles_per_pull=3),
+               dict(sort=1, key_bits=64), dict(sort=1, key_bits=int(ref.plan.key_bits) + 3)):
+        from paper_2410_17932_gb300.render import Rasterizer
+        r = Rasterizer(sts, views, **kw)
+        r.forward()
+        assert torch.equal(r.rgb, ref.rgb) and torch.equal(r.depth, ref.depth) and torch.equal(r.T, ref.T), kw
+
+
+def test_autotuned_tile_edge_matches_oracle_at_that_tile(tmp_path, monkeypatch):
+    """With the tile edge free, the tuner's choice is compared with the oracle at that edge."""
+    torch = torch_cuda()
+    from paper_2410_17932_gb300 import autotune
+    from paper_2410_17932_gb300.render import Rasterizer, SceneTensors
+    monkeypatch.setattr(autotune, "CACHE_PATH", str(tmp_path / "cache.json"))
+    scenes, views = _multiview(0.01)
+    views = [views[i] for i in (0, 12, 13, 28)]
+    sts = [SceneTensors.from_scene(s) for s in scenes]
+    best = autotune.tune(sts, views, allow_tile_change=True, iters=2)
+    ras = Rasterizer(sts, views, **best)
+    ras.forward()
+    torch.cuda.synchronize()
+    for v, cam in enumerate(views):
+        orc = oracle.render(scenes[cam.scene], cam, best["tile"])
+        w = compare_images(tuple(x.cpu().numpy() for x in ras.outputs(v)), orc, f"tile {best['tile']} view{v}")
+        print("autotuned", best, "view", v, w)
