@@ -308,6 +308,39 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
  * ordered; VRS_ERR_INVALID for a NULL pointer with n > 0. */
 vrs_status vrs_bake(const vrs_scene *scene, float *baked, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Training-loop pieces (Sec. 3.5, Sec. 4 "Training").
+ *
+ * vrs_image_loss: the Gaussian branch's loss L = (1 - lambda) L1 +
+ * lambda (1 - SSIM) of `image` against `target` (Sec. 3.5: the first two terms
+ * of the loss are those of 3DGS, with lambda = 0.2), and optionally dL/dimage,
+ * the upstream colour gradient vrs_render_bwd takes.  L1 is the mean absolute
+ * difference over the C H W values; SSIM is the mean over channels and pixels
+ * of Wang et al.'s structural similarity with an 11 x 11 Gaussian window of
+ * standard deviation 1.5, zero outside the image, C1 = 0.01^2, C2 = 0.03^2
+ * (images in [0, 1]).  Where image and target are equal, the L1 term's
+ * gradient is 0.
+ *   image, target: device float32 [C][H][W] (one view's planes, e.g. a view of
+ *     vrs_render_fwd's rgb output); dL_dimage: nullable device [C][H][W]
+ *     (overwritten, not accumulated);
+ *   loss_out: device float[3] = (L, L1, SSIM), reduced in FP64 in a fixed order;
+ *   scratch: device, 16-byte aligned, at least vrs_image_loss_scratch bytes.
+ * VRS_ERR_INVALID for sizes < 1, lambda outside [0, 1], NULL pointers or short
+ * scratch. */
+vrs_status vrs_image_loss_scratch(int32_t C, int32_t H, int32_t W, int64_t *bytes);
+vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, int32_t H, int32_t W,
+                          float lambda, float *loss_out, float *dL_dimage, void *scratch,
+                          int64_t scratch_bytes, void *stream);
+
+/* vrs_opacity_decay: the opacity decay and pruning test of training (Sec. 4:
+ * opacities are multiplied by 0.999 at intervals; Gaussians below 0.005 are
+ * pruned).  In place on device `opacity_logits` [n]: o = factor sigmoid(logit),
+ * logit <- ln(o / (1 - o)); keep[i] = 1 where o >= threshold (device uint8 [n]);
+ * *n_kept (device uint32) = the number kept.  factor in (0, 1], threshold in
+ * [0, 1). */
+vrs_status vrs_opacity_decay(float *opacity_logits, int64_t n, float factor, float threshold,
+                             uint8_t *keep, uint32_t *n_kept, void *stream);
+
 /* Synchronises `stream`, copies the device status block to *info (nullable)
  * and returns the most severe device status: CAPACITY, then TIMEOUT, then
  * NONFINITE, then INVALID, else VRS_OK. */

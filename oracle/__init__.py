@@ -126,6 +126,10 @@ def lib():
             L.orc_cull_points.argtypes = [ctypes.c_int64, P, ctypes.POINTER(OrcCamera), ctypes.c_int32,
                                           ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(OrcCullOpts), P]
+            L.orc_image_loss.restype = None
+            L.orc_image_loss.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P]
+            L.orc_opacity_decay.restype = None
+            L.orc_opacity_decay.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double, P, P, P]
             _lib = L
     return _lib
 
@@ -500,3 +504,34 @@ def combine_bwd(P, F, x0: int, y0: int, ex: float, ey: float, g, d_f: float = CO
     lib().orc_combine_bwd(_p(Pf), pw, ph, _p(Ff), w, h, int(x0), int(y0), float(ex), float(ey), float(d_f),
                           float(m), float(gamma), _p(gg), _p(dP), _p(dF))
     return dP, dF
+
+
+# Sec. 3.5: the Gaussian branch's loss weights D-SSIM by lambda = 0.2 (as 3DGS).
+LOSS_LAMBDA = 0.2
+
+
+def image_loss(image, target, lam: float = LOSS_LAMBDA, grad: bool = True):
+    """L = (1 - lambda) L1 + lambda (1 - SSIM) of image against target ([C, H, W]).
+    Returns (L, L1, SSIM, dL/dimage [C, H, W] or None), in FP64."""
+    x = _f32(image)
+    y = _f32(target)
+    assert x.shape == y.shape and x.ndim == 3
+    C, H, W = x.shape
+    out = np.zeros(3)
+    g = np.zeros(x.shape) if grad else None
+    lib().orc_image_loss(_p(x), _p(y), C, H, W, float(lam), _p(out), None if g is None else _p(g))
+    return float(out[0]), float(out[1]), float(out[2]), g
+
+
+# Sec. 4 "Training": opacity decay factor and pruning threshold.
+DECAY_FACTOR, PRUNE_THRESHOLD = 0.999, 0.005
+
+
+def opacity_decay(logits, factor: float = DECAY_FACTOR, threshold: float = PRUNE_THRESHOLD):
+    """(new logits, new opacities, keep mask) after multiplying every opacity by `factor`."""
+    lg = _f32(logits).reshape(-1)
+    nl = np.zeros(len(lg))
+    no = np.zeros(len(lg))
+    keep = np.zeros(len(lg), np.uint8)
+    lib().orc_opacity_decay(len(lg), _p(lg), float(factor), float(threshold), _p(nl), _p(no), _p(keep))
+    return nl, no, keep

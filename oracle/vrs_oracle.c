@@ -1552,3 +1552,117 @@ void orc_combine_bwd(const float *P, int pw, int ph, const float *F, int w, int 
         for (int ch = 0; ch < 3; ++ch) dF[ch * hw + q] += dL[q] / 3.0;
     free(dL);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Training loss of the Gaussian branch (Sec. 3.5: the first two terms of L,
+ * identical to 3DGS, with lambda = 0.2): L = (1 - lambda) L1 + lambda (1 - SSIM),
+ * L1 the mean absolute difference over the C H W values and SSIM the mean over
+ * channels and pixels of the structural similarity of Wang et al. (2004) with
+ * an 11 x 11 Gaussian window of standard deviation 1.5 (normalised to sum 1),
+ * the window zero outside the image, C1 = 0.01^2 and C2 = 0.03^2:
+ *   S = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)),
+ *   mu_x = w * x, s_x^2 = w * x^2 - mu_x^2, s_xy = w * (x y) - mu_x mu_y.
+ * Every window sum is written out over the 121 taps (no separable shortcut).
+ * The gradient dL/dx follows from S as a function of mu_x, A = w * x^2 and
+ * B = w * (x y): dS/dx_p = sum_q w(q - p) (S_mu(q) + 2 x_p S_A(q) + y_p S_B(q)).
+ * At x = y the L1 term's gradient is taken as 0 (the subgradient sign(0) = 0). */
+
+#define SSIM_R 5
+
+static void ssim_window(double w[2 * SSIM_R + 1][2 * SSIM_R + 1])
+{
+    double sum = 0.0;
+    for (int i = -SSIM_R; i <= SSIM_R; ++i)
+        for (int j = -SSIM_R; j <= SSIM_R; ++j) {
+            double v = exp(-(double)(i * i + j * j) / (2.0 * 1.5 * 1.5));
+            w[i + SSIM_R][j + SSIM_R] = v;
+            sum += v;
+        }
+    for (int i = 0; i < 2 * SSIM_R + 1; ++i)
+        for (int j = 0; j < 2 * SSIM_R + 1; ++j) w[i][j] /= sum;
+}
+
+/* image, target: [C][H][W] float32.  out: [0] L, [1] L1, [2] SSIM.  grad (nullable): [C][H][W]. */
+void orc_image_loss(const float *image, const float *target, int C, int H, int W, double lambda,
+                    double *out, double *grad)
+{
+    double w[2 * SSIM_R + 1][2 * SSIM_R + 1];
+    ssim_window(w);
+    const size_t HW = (size_t)H * W, N = (size_t)C * HW;
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double *Smu = (double *)calloc(N, sizeof(double));
+    double *SA = (double *)calloc(N, sizeof(double));
+    double *SB = (double *)calloc(N, sizeof(double));
+    double l1 = 0.0, ssim = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : l1, ssim)
+    for (long long e = 0; e < (long long)N; ++e) {
+        const int c = (int)(e / HW);
+        const int py = (int)((e % HW) / W), px = (int)(e % W);
+        const float *x = image + (size_t)c * HW, *y = target + (size_t)c * HW;
+        double mx = 0, my = 0, ex2 = 0, ey2 = 0, exy = 0;
+        for (int i = -SSIM_R; i <= SSIM_R; ++i)
+            for (int j = -SSIM_R; j <= SSIM_R; ++j) {
+                const int qy = py + i, qx = px + j;
+                if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
+                const double wv = w[i + SSIM_R][j + SSIM_R];
+                const double a = x[(size_t)qy * W + qx], b = y[(size_t)qy * W + qx];
+                mx += wv * a;
+                my += wv * b;
+                ex2 += wv * a * a;
+                ey2 += wv * b * b;
+                exy += wv * a * b;
+            }
+        const double n1 = 2.0 * mx * my + C1, n2 = 2.0 * (exy - mx * my) + C2;
+        const double d1 = mx * mx + my * my + C1, d2 = (ex2 - mx * mx) + (ey2 - my * my) + C2;
+        const double S = n1 * n2 / (d1 * d2);
+        ssim += S;
+        Smu[e] = S * (2.0 * my / n1 - 2.0 * my / n2 - 2.0 * mx / d1 + 2.0 * mx / d2);
+        SA[e] = -S / d2;
+        SB[e] = 2.0 * S / n2;
+        l1 += fabs((double)x[(size_t)py * W + px] - (double)y[(size_t)py * W + px]);
+    }
+    l1 /= (double)N;
+    ssim /= (double)N;
+    out[0] = (1.0 - lambda) * l1 + lambda * (1.0 - ssim);
+    out[1] = l1;
+    out[2] = ssim;
+    if (grad) {
+#pragma omp parallel for schedule(static)
+        for (long long e = 0; e < (long long)N; ++e) {
+            const int c = (int)(e / HW);
+            const int py = (int)((e % HW) / W), px = (int)(e % W);
+            const size_t base = (size_t)c * HW;
+            const double xp = image[base + (size_t)py * W + px], yp = target[base + (size_t)py * W + px];
+            double gm = 0, ga = 0, gb = 0;
+            for (int i = -SSIM_R; i <= SSIM_R; ++i)
+                for (int j = -SSIM_R; j <= SSIM_R; ++j) {
+                    const int qy = py + i, qx = px + j;
+                    if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
+                    const double wv = w[i + SSIM_R][j + SSIM_R];
+                    const size_t q = base + (size_t)qy * W + qx;
+                    gm += wv * Smu[q];
+                    ga += wv * SA[q];
+                    gb += wv * SB[q];
+                }
+            const double dssim = (gm + 2.0 * xp * ga + yp * gb) / (double)N;
+            const double sgn = xp > yp ? 1.0 : (xp < yp ? -1.0 : 0.0);
+            grad[e] = (1.0 - lambda) * sgn / (double)N - lambda * dssim;
+        }
+    }
+    free(Smu); free(SA); free(SB);
+}
+
+/* Opacity decay of training (Sec. 4 "Training": opacities multiplied by 0.999 at
+ * intervals) and the pruning threshold (0.005): o' = factor sigmoid(logit), the
+ * new logit ln(o' / (1 - o')), keep = o' >= threshold.  FP64. */
+void orc_opacity_decay(int n, const float *logits, double factor, double threshold, double *new_logits,
+                       double *new_opacity, uint8_t *keep)
+{
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < n; ++g) {
+        const double o = factor / (1.0 + exp(-(double)logits[g]));
+        new_opacity[g] = o;
+        new_logits[g] = log(o / (1.0 - o));
+        keep[g] = o >= threshold;
+    }
+}

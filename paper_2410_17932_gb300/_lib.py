@@ -94,6 +94,9 @@ SIGNATURES = [
     ("vrs_reset_status", _i32, [ctypes.POINTER(vrs_plan), _vp, _vp]),
     ("vrs_sort_pairs_noalloc", _i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     ("vrs_bake", _i32, [ctypes.POINTER(vrs_scene), _vp, _vp]),
+    ("vrs_image_loss_scratch", _i32, [_i32, _i32, _i32, ctypes.POINTER(_i64)]),
+    ("vrs_image_loss", _i32, [_vp, _vp, _i32, _i32, _i32, _f32, _vp, _vp, _vp, _i64, _vp]),
+    ("vrs_opacity_decay", _i32, [_vp, _i64, _f32, _f32, _vp, _vp, _vp]),
     ("vrs_foveal_combine", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
                                   ctypes.POINTER(vrs_combine_opts), _vp, _vp, _vp]),
     ("vrs_foveal_combine_bwd", _i32, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _f32, _f32,
@@ -207,3 +210,20 @@ def vrs_foveal_combine_bwd(P: int, pw: int, ph: int, F: int, w: int, h: int, x0:
 
 def vrs_bake(scene, baked: int, stream: int) -> int:
     return load().vrs_bake(ctypes.byref(scene), baked, stream)
+
+
+def vrs_image_loss_scratch(C: int, H: int, W: int) -> int:
+    b = _i64(0)
+    _check(load().vrs_image_loss_scratch(C, H, W, ctypes.byref(b)), "vrs_image_loss_scratch")
+    return int(b.value)
+
+
+def vrs_image_loss(image: int, target: int, C: int, H: int, W: int, lam: float, loss_out: int,
+                   dL_dimage: Optional[int], scratch: int, scratch_bytes: int, stream: int) -> int:
+    return load().vrs_image_loss(image, target, C, H, W, lam, loss_out, dL_dimage, scratch, scratch_bytes,
+                                 stream)
+
+
+def vrs_opacity_decay(logits: int, n: int, factor: float, threshold: float, keep: int, n_kept: int,
+                      stream: int) -> int:
+    return load().vrs_opacity_decay(logits, n, factor, threshold, keep, n_kept, stream)

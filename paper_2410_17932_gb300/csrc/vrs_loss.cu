@@ -1,0 +1,293 @@
+// Training-loop pieces of the Gaussian branch.
+//
+// vrs_image_loss: L = (1 - lambda) L1 + lambda (1 - SSIM) of a rendered image
+// against its target and dL/dimage, the upstream gradient of vrs_render_bwd
+// (Sec. 3.5: the first two terms of the loss are those of 3DGS, lambda = 0.2).
+// SSIM (Wang et al. 2004) with an 11 x 11 Gaussian window (sigma 1.5, zero
+// outside the image), C1 = 0.01^2, C2 = 0.03^2, averaged over channels and
+// pixels.  The window is the outer product of a 1-D Gaussian, so every window
+// sum is two 11-tap passes over a shared-memory tile with a 5-pixel halo.
+//   k_ssim_fwd: per pixel and channel the five window moments (means of x, y,
+//     x^2, y^2, x y), S, and the three partials of S with respect to mu_x,
+//     w * x^2 and w * (x y); per-CTA sums of S and |x - y|.
+//   k_ssim_bwd: the window sums of the three partials (the adjoint of a
+//     zero-padded symmetric window is the same window) give
+//     dSSIM/dx_p = (w * S_mu + 2 x_p w * S_A + y_p w * S_B) / N.
+//   k_loss_reduce: the per-CTA sums in FP64, in a fixed order.
+//
+// vrs_opacity_decay: Sec. 4 "Training" multiplies the opacities by 0.999 at
+// intervals and prunes below 0.005: the new logit of factor * sigmoid(logit),
+// a keep mask and the number kept.
+#include "vrs_internal.cuh"
+
+namespace vrs {
+
+constexpr int kLW = 32, kLH = 8, kLR = 5;                 // output tile, window radius
+constexpr int kLThreads = kLW * kLH;
+constexpr int kLPW = kLW + 2 * kLR, kLPH = kLH + 2 * kLR;  // padded tile
+
+__constant__ float c_gauss[2 * kLR + 1];
+
+struct LossArgs {
+    const float *x, *y;
+    float *smu, *sa, *sb;      // [C][H][W] partials of S
+    float *dx;                 // nullable: dL/dimage
+    float2 *block_sums;        // per CTA: (sum S, sum |x - y|)
+    int C, H, W;
+    float lambda, inv_n;
+};
+
+// Loads a padded tile of one channel (zero outside the image).
+__device__ __forceinline__ void load_tile(const float *src, int H, int W, int x0, int y0, float (*t)[kLPW])
+{
+    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
+        const int r = i / kLPW, c = i - r * kLPW;
+        const int gy = y0 + r - kLR, gx = x0 + c - kLR;
+        t[r][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? __ldg(src + (size_t)gy * W + gx) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
+{
+    __shared__ float sx[kLPH][kLPW], sy[kLPH][kLPW];
+    __shared__ float hb[5][kLPH][kLW];
+    __shared__ float2 red[kLThreads / 32];
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
+    const int tx = threadIdx.x % kLW, ty = threadIdx.x / kLW;
+    const int px = x0 + tx, py = y0 + ty;
+    const bool in = px < a.W && py < a.H;
+    float s_sum = 0.f, l1_sum = 0.f;
+    for (int c = 0; c < a.C; ++c) {
+        const size_t base = (size_t)c * a.H * a.W;
+        __syncthreads();                                   // the previous channel's tiles are read
+        load_tile(a.x + base, a.H, a.W, x0, y0, sx);
+        load_tile(a.y + base, a.H, a.W, x0, y0, sy);
+        __syncthreads();
+        // horizontal pass over every padded row
+        for (int i = threadIdx.x; i < kLPH * kLW; i += kLThreads) {
+            const int r = i / kLW, col = i - r * kLW;
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kLR + 1; ++k) {
+                const float g = c_gauss[k], u = sx[r][col + k], v = sy[r][col + k];
+                m0 = fmaf(g, u, m0);
+                m1 = fmaf(g, v, m1);
+                m2 = fmaf(g, u * u, m2);
+                m3 = fmaf(g, v * v, m3);
+                m4 = fmaf(g, u * v, m4);
+            }
+            hb[0][r][col] = m0;
+            hb[1][r][col] = m1;
+            hb[2][r][col] = m2;
+            hb[3][r][col] = m3;
+            hb[4][r][col] = m4;
+        }
+        __syncthreads();
+        float mx = 0.f, my = 0.f, ex2 = 0.f, ey2 = 0.f, exy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float g = c_gauss[k];
+            mx = fmaf(g, hb[0][ty + k][tx], mx);
+            my = fmaf(g, hb[1][ty + k][tx], my);
+            ex2 = fmaf(g, hb[2][ty + k][tx], ex2);
+            ey2 = fmaf(g, hb[3][ty + k][tx], ey2);
+            exy = fmaf(g, hb[4][ty + k][tx], exy);
+        }
+        if (in) {
+            const float n1 = 2.f * mx * my + C1, n2 = 2.f * (exy - mx * my) + C2;
+            const float d1 = mx * mx + my * my + C1, d2 = (ex2 - mx * mx) + (ey2 - my * my) + C2;
+            const float S = (n1 * n2) / (d1 * d2);
+            const size_t e = base + (size_t)py * a.W + px;
+            a.smu[e] = S * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
+            a.sa[e] = -S / d2;
+            a.sb[e] = 2.f * S / n2;
+            s_sum += S;
+            l1_sum += fabsf(sx[ty + kLR][tx + kLR] - sy[ty + kLR][tx + kLR]);
+        }
+    }
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s_sum += __shfl_xor_sync(FULL, s_sum, o);
+        l1_sum += __shfl_xor_sync(FULL, l1_sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(s_sum, l1_sum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = red[0];
+        for (int w = 1; w < kLThreads / 32; ++w) {
+            t.x += red[w].x;
+            t.y += red[w].y;
+        }
+        a.block_sums[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kLThreads) k_ssim_bwd(const LossArgs a)
+{
+    __shared__ float sm[3][kLPH][kLPW];
+    __shared__ float hb[3][kLPH][kLW];
+    const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
+    const int tx = threadIdx.x % kLW, ty = threadIdx.x / kLW;
+    const int px = x0 + tx, py = y0 + ty;
+    const bool in = px < a.W && py < a.H;
+    for (int c = 0; c < a.C; ++c) {
+        const size_t base = (size_t)c * a.H * a.W;
+        __syncthreads();
+        load_tile(a.smu + base, a.H, a.W, x0, y0, sm[0]);
+        load_tile(a.sa + base, a.H, a.W, x0, y0, sm[1]);
+        load_tile(a.sb + base, a.H, a.W, x0, y0, sm[2]);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kLPH * kLW; i += kLThreads) {
+            const int r = i / kLW, col = i - r * kLW;
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kLR + 1; ++k) {
+                const float g = c_gauss[k];
+                m0 = fmaf(g, sm[0][r][col + k], m0);
+                m1 = fmaf(g, sm[1][r][col + k], m1);
+                m2 = fmaf(g, sm[2][r][col + k], m2);
+            }
+            hb[0][r][col] = m0;
+            hb[1][r][col] = m1;
+            hb[2][r][col] = m2;
+        }
+        __syncthreads();
+        if (!in) continue;
+        float gm = 0.f, ga = 0.f, gb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float g = c_gauss[k];
+            gm = fmaf(g, hb[0][ty + k][tx], gm);
+            ga = fmaf(g, hb[1][ty + k][tx], ga);
+            gb = fmaf(g, hb[2][ty + k][tx], gb);
+        }
+        const size_t e = base + (size_t)py * a.W + px;
+        const float xp = __ldg(a.x + e), yp = __ldg(a.y + e);
+        const float sgn = xp > yp ? 1.f : (xp < yp ? -1.f : 0.f);
+        const float dssim = (gm + 2.f * xp * ga + yp * gb) * a.inv_n;
+        a.dx[e] = (1.f - a.lambda) * sgn * a.inv_n - a.lambda * dssim;
+    }
+}
+
+__global__ void k_loss_reduce(const float2 *block_sums, int n_blocks, float lambda, double inv_n, float *out)
+{
+    __shared__ double rs[256], rl[256];
+    double s = 0.0, l = 0.0;
+    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
+        s += (double)block_sums[i].x;
+        l += (double)block_sums[i].y;
+    }
+    rs[threadIdx.x] = s;
+    rl[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            rs[threadIdx.x] += rs[threadIdx.x + o];
+            rl[threadIdx.x] += rl[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ssim = rs[0] * inv_n, l1 = rl[0] * inv_n;
+        out[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
+        out[1] = (float)l1;
+        out[2] = (float)ssim;
+    }
+}
+
+__global__ void k_opacity_decay(float *logits, int64_t n, float factor, float threshold, uint8_t *keep,
+                                uint32_t *n_kept)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool k = false;
+    if (i < n) {
+        const float o = factor / (1.0f + expf(-logits[i]));
+        logits[i] = logf(o) - log1pf(-o);
+        k = o >= threshold;
+        keep[i] = k ? 1 : 0;
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, k);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_kept, (uint32_t)__popc(b));
+}
+
+namespace {
+bool g_gauss_ready[64];
+}
+
+// Scratch layout: the three partial maps (n floats each), then the per-CTA float2 sums at
+// the next 16-byte boundary (3 n floats end on a 4-byte one when n is odd).
+inline int64_t sums_offset(int64_t n) { return (3 * n * 4 + 15) / 16 * 16; }
+
+}  // namespace vrs
+
+using namespace vrs;
+
+extern "C" {
+
+vrs_status vrs_image_loss_scratch(int32_t C, int32_t H, int32_t W, int64_t *bytes)
+{
+    if (C < 1 || H < 1 || W < 1 || !bytes) return VRS_ERR_INVALID;
+    const int64_t n = (int64_t)C * H * W;
+    const int64_t blocks = (int64_t)((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH);
+    *bytes = sums_offset(n) + blocks * 8;
+    return VRS_OK;
+}
+
+vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, int32_t H, int32_t W, float lambda,
+                          float *loss_out, float *dL_dimage, void *scratch, int64_t scratch_bytes, void *stream)
+{
+    int64_t need = 0;
+    if (vrs_image_loss_scratch(C, H, W, &need) != VRS_OK) return VRS_ERR_INVALID;
+    if (!image || !target || !loss_out || !scratch || scratch_bytes < need) return VRS_ERR_INVALID;
+    if (!(lambda >= 0.f && lambda <= 1.f)) return VRS_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(scratch) & 15u) != 0) return VRS_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VRS_ERR_CUDA;
+    if (!g_gauss_ready[dev]) {           // the normalised 1-D Gaussian of the SSIM window
+        float g[2 * kLR + 1];
+        double s = 0.0, v[2 * kLR + 1];
+        for (int i = 0; i < 2 * kLR + 1; ++i) {
+            v[i] = exp(-(double)((i - kLR) * (i - kLR)) / (2.0 * 1.5 * 1.5));
+            s += v[i];
+        }
+        for (int i = 0; i < 2 * kLR + 1; ++i) g[i] = (float)(v[i] / s);
+        if (cudaMemcpyToSymbol(c_gauss, g, sizeof(g)) != cudaSuccess) return VRS_ERR_CUDA;
+        g_gauss_ready[dev] = true;
+    }
+    const int64_t n = (int64_t)C * H * W;
+    LossArgs a;
+    a.x = image;
+    a.y = target;
+    a.smu = static_cast<float *>(scratch);
+    a.sa = a.smu + n;
+    a.sb = a.sa + n;
+    a.block_sums = reinterpret_cast<float2 *>(static_cast<char *>(scratch) + sums_offset(n));
+    a.dx = dL_dimage;
+    a.C = C;
+    a.H = H;
+    a.W = W;
+    a.lambda = lambda;
+    a.inv_n = (float)(1.0 / (double)n);
+    const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_ssim_fwd<<<grid, kLThreads, 0, s>>>(a);
+    k_loss_reduce<<<1, 256, 0, s>>>(a.block_sums, (int)(grid.x * grid.y), lambda, 1.0 / (double)n, loss_out);
+    if (dL_dimage) k_ssim_bwd<<<grid, kLThreads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
+}
+
+vrs_status vrs_opacity_decay(float *opacity_logits, int64_t n, float factor, float threshold, uint8_t *keep,
+                             uint32_t *n_kept, void *stream)
+{
+    if (n < 0 || !(factor > 0.f && factor <= 1.f) || !(threshold >= 0.f && threshold < 1.f)) return VRS_ERR_INVALID;
+    if (n > 0 && (!opacity_logits || !keep || !n_kept)) return VRS_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_kept && cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s) != cudaSuccess) return VRS_ERR_CUDA;
+    if (n == 0) return VRS_OK;
+    k_opacity_decay<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(opacity_logits, n, factor, threshold, keep, n_kept);
+    return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
+}
+
+}  // extern "C"
