@@ -45,6 +45,12 @@ WORKLOADS = {
 # pixel-changing work (culling and early exit raise it; evaluating pairs that
 # cannot contribute lowers it).
 ALU_OPS_PER_BLEND = 25
+# FP32 lane-ops of one blended pair in the reverse pass: the forward's evaluation of the pair
+# (offset, quadratic form, exp, clamp: 15), T recovered by a reciprocal and a multiply (3), the
+# weight and the four colour/depth gradient FMAs (5), dL/dalpha from the pixel's colour and the
+# suffix sums (10), the suffix-sum updates (4), the opacity term with its exp (3), and the mean
+# and 2D-covariance terms (10).
+ALU_OPS_PER_BWD_BLEND = 50
 METRIC = "ms per stereo frame @2016x2240/eye (0.5M SH-3 Gaussians)"
 CSRC = os.path.join(ROOT, "paper_2410_17932_gb300", "csrc")
 # DRAM bytes (read + write) of one launch of the blend kernel on the periphery stereo frame,
@@ -306,6 +312,39 @@ def _time_loop(fn, flush, iters):
 EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m", "per_pixel_order", "inference")
 
 
+def stage_rooflines(ras, scenes, stage_ms, inst, pair_blends, peaks, src):
+    """Per-stage rooflines of one frame: preprocess and bin/sort against the measured HBM
+    copy bandwidth (algorithmic bytes below), the blend against the FP32 issue peak."""
+    p = ras.plan
+    hbm = float(peaks["hbm_gbs"])
+    n = sum(s.n for s in scenes)
+    K_ = max((s.sh_degree + 1) ** 2 for s in scenes)
+    pairs = int(ras.visible_pairs)
+    # geometry of every Gaussian (44 B); per visible pair: its list entry written and read
+    # (2 x 32 B), mean and logit (16 B), SH row (12 K B), record (48 B); per instance: key + value
+    pre_bytes = n * 44 + pairs * (64 + 16 + 12 * K_ + 48) + 12 * inst
+    if int(p.sort_mode) == 0:
+        # scatter reads key + value (12 B), takes a cursor (4 B), writes the composite (8 B); the
+        # per-tile sort reads it (8 B) and writes key + value (12 B); per tile: count, cursor, range
+        sort_bytes = inst * (12 + 4 + 8 + 8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
+    else:
+        sort_bytes = 24 * inst * int(p.sort_passes) + 8 * inst * int(p.sort_passes)
+    alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    out = []
+    for name, byts in (("preprocess", pre_bytes), ("bin_sort", sort_bytes)):
+        gbs = byts / (stage_ms[name] * 1e-3) / 1e9
+        out.append({"stage": name, "bound": "hbm", "bytes": int(byts), "ms": round(stage_ms[name], 4),
+                    "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                    "peak_source": src})
+    ops = ALU_OPS_PER_BLEND * pair_blends
+    t = ops / (stage_ms["render_fwd"] * 1e-3) / 1e12
+    out.append({"stage": "render_fwd", "bound": "alu", "ops": int(ops), "ms": round(stage_ms["render_fwd"], 4),
+                "achieved": round(t, 3), "peak": round(alu_peak, 2), "unit": "T FP32 lane-ops/s",
+                "frac": round(t / alu_peak, 4),
+                "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz"})
+    return out
+
+
 def run_extras(args):
     import torch
     from paper_2410_17932_gb300 import inputs as I
@@ -343,6 +382,44 @@ def run_extras(args):
             step()
         out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(step, flush, args.extra_steps), 4)
         out["training_view_1m_fwd_ms"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+        # the step's stages in order, then the backward's roofline: its reverse blend dominates
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.extra_steps)]
+        for e in evs:
+            flush.zero_()
+            e[0].record()
+            ras.preprocess()
+            e[1].record()
+            ras.bin_sort()
+            e[2].record()
+            ras.render_fwd()
+            e[3].record()
+            ras.backward_params(gC, gD, None, grads)
+            e[4].record()
+        torch.cuda.synchronize()
+        names = ("preprocess", "bin_sort", "render_fwd", "render_bwd")
+        st_ms = {n: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, n in enumerate(names)}
+        _, blends, _ = ras.count_pairs()
+        peaks, src = measured_peaks()
+        alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        t = ALU_OPS_PER_BWD_BLEND * blends / (st_ms["render_bwd"] * 1e-3) / 1e12
+        out["training_view_1m_stages_ms"] = {k: round(v, 4) for k, v in st_ms.items()}
+        out["training_view_1m_backward_roofline"] = {
+            "bound": "alu", "stage": "render_bwd (reverse blend + chain rule)", "achieved": round(t, 3),
+            "peak": round(alu_peak, 2), "unit": "T FP32 lane-ops/s", "frac": round(t / alu_peak, 4),
+            "units": f"{blends} blended pairs x {ALU_OPS_PER_BWD_BLEND} ops"}
+        # the loss of Sec. 3.5 on the rendered view, against a nearby target, with its gradient
+        from paper_2410_17932_gb300 import train
+        img = ras.outputs(0)[0].contiguous()
+        tgt = (img + 0.05).contiguous()
+        H_, W_ = img.shape[1], img.shape[2]
+        nb = (W_ + 31) // 32 * ((H_ + 7) // 8)
+        ms_loss = _time_loop(lambda: train.image_loss(img, tgt), flush, args.extra_steps)
+        # read image + target and write three partial maps (20 B per value); read the partials and
+        # both images again and write the gradient (24 B per value); per CTA 8 B
+        lbytes = img.numel() * (20 + 24) + nb * 8
+        out["training_view_1m_loss"] = {"ms": round(ms_loss, 4), "bytes": int(lbytes), "bound": "hbm",
+                                        "achieved_gbs": round(lbytes / (ms_loss * 1e-3) / 1e9, 1),
+                                        "frac": round(lbytes / (ms_loss * 1e-3) / 1e9 / float(peaks["hbm_gbs"]), 4)}
         del ras, sts, grads
     if "batched_32" in want:
         out["batched_32_views"] = _batched_32(args, flush)
@@ -804,6 +881,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "stages_ms": {k: round(v, 4) for k, v in stage.items()},
             "roofline": roof,
+            "roofline_stages": stage_rooflines(ras, scenes, stage, inst, pair_blends, peaks, src),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * K,

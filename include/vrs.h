@@ -42,9 +42,10 @@
  *  - Errors detectable on the host (bad sizes, null pointers, a camera that
  *    does not match the plan) return a status at once and launch nothing.
  *    Errors detectable only on the device (instance capacity exceeded, a
- *    non-finite parameter, an all-zero quaternion, a bounded wait that gave
- *    up) set bits in a status word inside the workspace; kernels after a
- *    capacity overflow skip their work.  vrs_query_status reads that word.
+ *    non-finite parameter, an all-zero quaternion) set bits in a status word
+ *    inside the workspace; kernels after a capacity overflow skip their work.
+ *    vrs_query_status reads that word.  No kernel waits on another, so no
+ *    call can hang on the device.
  *
  * Parameterisation (Sec. 3.1: opacity, colour, scale and rotation per splat):
  *  means [n][3], log_scales [n][3] (log of the per-axis standard deviation),
@@ -77,7 +78,7 @@ typedef enum {
     VRS_ERR_INVALID = 1,     /* bad argument; on the device: an all-zero quaternion */
     VRS_ERR_CAPACITY = 2,    /* more tile instances than plan.max_instances */
     VRS_ERR_CUDA = 3,        /* a CUDA runtime call failed (launch, copy) */
-    VRS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    VRS_ERR_TIMEOUT = 4,     /* reserved: no call of this version waits on the device */
     VRS_ERR_NONFINITE = 5    /* a Gaussian parameter was NaN or Inf (that Gaussian is skipped) */
 } vrs_status;
 
@@ -194,7 +195,7 @@ typedef struct {
 /* Device status block, copied to the host by vrs_query_status. */
 typedef struct {
     uint32_t flags;            /* bit 0: all-zero quaternion, 1: non-finite parameter,
-                                  2: capacity exceeded, 3: bounded wait timed out */
+                                  2: capacity exceeded, 3: reserved */
     uint32_t reserved;
     uint64_t instances;        /* tile instances requested by the last vrs_preprocess
                                   (may exceed max_instances on overflow) */
@@ -342,7 +343,7 @@ vrs_status vrs_opacity_decay(float *opacity_logits, int64_t n, float factor, flo
                              uint8_t *keep, uint32_t *n_kept, void *stream);
 
 /* Synchronises `stream`, copies the device status block to *info (nullable)
- * and returns the most severe device status: CAPACITY, then TIMEOUT, then
+ * and returns the most severe device status: CAPACITY, then (reserved) TIMEOUT, then
  * NONFINITE, then INVALID, else VRS_OK. */
 vrs_status vrs_query_status(const vrs_plan *plan, const void *workspace, vrs_run_info *info,
                             void *stream);

@@ -72,3 +72,20 @@ def record_grads_wrt_sigma(g2: np.ndarray, conic: np.ndarray) -> np.ndarray:
     h11 = -(cg10 * b + cg11 * c)
     out[:, 2], out[:, 3], out[:, 4] = h00, 2.0 * h01, h11
     return out
+
+
+def plain_200_c9(seed: int = 91, dark_frac: float = 0.15):
+    """The 200x200 workload with the colour reading where "RGB ~ U[0, 1]" is the rendered colour:
+    the DC coefficient is (rgb - 0.5) / Y_00, so a splat renders exactly rgb.  A fraction of the
+    splats get channels below 0 before the max(0, .) clamp (rgb drawn from [-0.3, 0)), so the
+    clamp and dark colours are exercised."""
+    from paper_2410_17932_gb300 import inputs as I
+    scs, cams = I.plain_200()
+    sc = scs[0]
+    rng = np.random.default_rng(seed)
+    rgb = rng.uniform(0.0, 1.0, (sc.n, 3))
+    dark = rng.uniform(size=(sc.n, 3)) < dark_frac
+    rgb[dark] = rng.uniform(-0.3, 0.0, dark.sum())
+    y00 = 0.5 / math.sqrt(math.pi)
+    sc.sh[:, 0, :] = ((rgb - 0.5) / y00).astype(np.float32)
+    return [sc], cams

@@ -158,3 +158,19 @@ def test_autograd_rejects_a_stale_rasterizer():
         rgb1.sum().backward()
     rgb2.sum().backward()                      # the latest pass is still differentiable
     assert st.means.grad is not None
+
+
+def test_backward_with_clamped_colours():
+    """The colour clamp passes no gradient: a 64x64 window of the rendered-colour scene, where
+    some channels are clamped at 0, against the oracle's chain rule."""
+    from tests.gpu_util import plain_200_c9
+    scs, _ = plain_200_c9()
+    sc = scs[0].subset(np.arange(300))
+    cam = I.Camera(np.eye(3), np.zeros(3), 100.0, 100.0, 32.0, 32.0, 64, 64)
+    g = I.upstream_grads([cam], 21)[0]
+    ref = oracle.grads(sc, cam, g[0], g[1], None)
+    p = oracle.project(sc, cam)
+    d = oracle.decide(sc, cam)
+    assert (p["clamp_rgb"][d["visible"] > 0]).sum() > 10
+    _, got = _gpu_grads([sc], [cam], [g[0]], [g[1]])
+    _check(got[0], ref, "clamped colours")

@@ -72,6 +72,18 @@ def test_plain_200_image_parity(backward):
     print("plain_200 worst", worst)
 
 
+def test_plain_200_rendered_colour_reading():
+    """The rendered-colour reading of "RGB ~ U[0, 1]", with some channels clamped at 0."""
+    from tests.gpu_util import plain_200_c9
+    scs, cams = plain_200_c9()
+    p = oracle.project(scs[0], cams[0])
+    assert p["clamp_rgb"].sum() > 500 and (p["rgb"] < 0.05).mean() > 0.05
+    ras = _run(scs, cams, backward=True)
+    _check_sort(ras, scs, cams)
+    rgb, depth, T = [x.cpu().numpy() for x in ras.outputs(0)]
+    print("plain_200 rendered colours", compare_images((rgb, depth, T), oracle.render(scs[0], cams[0]), "c9"))
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_tile_sizes_ragged(tile):
     # 203 x 141: not a multiple of any tile size
