@@ -312,6 +312,14 @@ def _time_loop(fn, flush, iters):
 EXTRAS = ("dense_3m", "training_1m", "batched_32", "foveal_points_5m", "per_pixel_order", "inference")
 
 
+def instances_in_tiles_over(ras, m: int) -> int:
+    """Instances of the last frame that lie in tiles holding more than m."""
+    _, _, ranges = ras.sorted_lists()
+    r = ranges.cpu().numpy().astype(np.int64)
+    c = r[:, 1] - r[:, 0]
+    return int(c[c > m].sum())
+
+
 def stage_rooflines(ras, scenes, stage_ms, inst, pair_blends, peaks, src):
     """Per-stage rooflines of one frame: preprocess and bin/sort against the measured HBM
     copy bandwidth (algorithmic bytes below), the blend against the FP32 issue peak."""
@@ -323,10 +331,13 @@ def stage_rooflines(ras, scenes, stage_ms, inst, pair_blends, peaks, src):
     # geometry of every Gaussian (44 B); per visible pair: its list entry written and read
     # (2 x 32 B), mean and logit (16 B), SH row (12 K B), record (48 B); per instance: key + value
     pre_bytes = n * 44 + pairs * (64 + 16 + 12 * K_ + 48) + 12 * inst
-    if int(p.sort_mode) == 0:
+    if int(p.sort_mode) != 1:
         # scatter reads key + value (12 B), takes a cursor (4 B), writes the composite (8 B); the
-        # per-tile sort reads it (8 B) and writes key + value (12 B); per tile: count, cursor, range
-        sort_bytes = inst * (12 + 4 + 8 + 8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
+        # per-tile sort reads it (8 B) and writes key + value (12 B); per tile: count, cursor, range.
+        # Sort mode 2 leaves the tiles of one blend batch to the blend: only the instances of
+        # larger tiles are sorted in this stage
+        sorted_here = inst if int(p.sort_mode) == 0 else instances_in_tiles_over(ras, int(p.tile) ** 2 // 2)
+        sort_bytes = inst * (12 + 4 + 8) + sorted_here * (8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
     else:
         sort_bytes = 24 * inst * int(p.sort_passes) + 8 * inst * int(p.sort_passes)
     alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -714,6 +725,7 @@ def main():
     ap.add_argument("--workload", default="periphery_stereo_05m", choices=list(WORKLOADS))
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=-1, help="-1: autotuned choice")
+    ap.add_argument("--sort", type=int, default=0, help="sort mode of the plan (0, 1 or 2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
@@ -742,7 +754,7 @@ def main():
     scenes, views = load_workload(args.workload)
     sts = [SceneTensors.from_scene(s) for s in scenes]
     persistent = bool(args.persistent) if args.persistent >= 0 else False
-    ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent)
+    ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent, sort=args.sort)
     ras.forward()                       # sizes the instance list
     code, flags, inst = ras.last_status
     pair_evals, pair_blends, block_evals = ras.count_pairs()   # work units, one untimed counting pass
@@ -829,10 +841,11 @@ def main():
             K_ = max((s.sh_degree + 1) ** 2 for s in scenes)
             pairs = ras.visible_pairs
             byts = n * 44 + pairs * (64 + 16 + 12 * K_ + 48) + 12 * inst
-        elif p.sort_mode == 0:
+        elif p.sort_mode != 1:
             # bucketed: scatter reads key + value, takes a cursor, writes the composite; the
             # per-tile sort reads the composite and writes key + value; counts, cursors, ranges
-            byts = inst * (12 + 4 + 8 + 8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
+            sorted_here = inst if p.sort_mode == 0 else instances_in_tiles_over(ras, int(p.tile) ** 2 // 2)
+            byts = inst * (12 + 4 + 8) + sorted_here * (8 + 12) + int(p.n_tiles) * (4 + 4 + 8)
         else:
             byts = 24 * inst * int(p.sort_passes) + 8 * inst * int(p.sort_passes)
         achieved = byts / (stage[dominant] * 1e-3) / 1e9
@@ -861,7 +874,7 @@ def main():
         extra = run_extras(args)
 
     # (decide, pairs) per scene; the sort's kernels; the blend (+ the order kernels)
-    if p.sort_mode == 0:
+    if p.sort_mode != 1:
         # scan (+ block sums beyond 64 Ki tiles), scatter, tile sort
         sort_launches = 3 + (1 if (int(p.n_tiles) + 1023) // 1024 > 64 else 0)
         launches_per_step = 2 * len(scenes) + sort_launches + (3 if p.persistent else 1)

@@ -120,7 +120,11 @@ typedef struct {
                               launch, heaviest tiles first; 0 = one CTA per tile */
     int32_t backward;      /* 1 = reserve the workspace that vrs_render_bwd needs */
     int32_t sort;          /* 0 = bucket by tile, then sort each tile's bucket (default);
-                              1 = one global LSD radix sort of all keys.  Same result. */
+                              1 = one global LSD radix sort of all keys;
+                              2 = bucket by tile and sort only the tiles larger than one blend
+                                  batch (tile^2 / 2 instances); vrs_render_fwd orders the others
+                                  while staging them and writes their sorted lists back.  The
+                                  same result; mode 2 needs resort = 0. */
     int64_t max_instances; /* capacity of the (tile, Gaussian) instance list; 0 = 4 x records + 65536 */
     int32_t count_pairs;   /* 1 = vrs_render_fwd also counts the Gaussian-pixel pairs it evaluated
                               and blended into the status block (a slower, measuring variant) */
@@ -242,8 +246,8 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
  * (a warp per tile of <= 256 instances, a CTA otherwise); mode 1 runs an 8-bit
  * LSD radix sort over plan.key_bits bits and orders runs of equal keys by
  * record index.  Both give the same list.
- * After it, the sorted keys and record indices are at
- * workspace + plan.off_keys[plan.sorted_buf] / off_vals[plan.sorted_buf]. */
+ * After it (after vrs_render_fwd for sort mode 2), the sorted keys and record
+ * indices are at workspace + plan.off_keys[plan.sorted_buf] / off_vals[plan.sorted_buf]. */
 vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream);
 
 /* Step 3 (Sec. 3.1 blending to screen; Sec. 3.2 Eq. 1).  For every pixel,

@@ -17,13 +17,15 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
                              unsigned long long *bucket, unsigned long long *keys_out, uint32_t *vals_out,
                              const uint32_t *cnt, uint32_t *cursor, uint32_t *blocksum, uint32_t *big_list,
                              uint2 *ranges, DevStatus *st, unsigned long long cap, int64_t n_tiles,
-                             int n_sms, cudaStream_t s);
+                             uint32_t blend_max, int n_sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
                               unsigned long long cap, int persistent, int count, int half_out,
-                              int tiles_per_pull, int n_sms, cudaStream_t s);
+                              int tiles_per_pull, const unsigned long long *bucket,
+                              unsigned long long *keys_w, uint32_t *vals_w, uint32_t blend_max, int n_sms,
+                              cudaStream_t s);
 cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                                  const float4 *raydepth, const uint32_t *vals, const uint2 *ranges,
                                  DevStatus *st, float *rgb, float *depth, float *Tf, uint8_t *flags,
@@ -127,6 +129,12 @@ DevScene dev_scene(const vrs_scene &S)
     return d;
 }
 
+// Sort mode 2: tiles of at most one blend batch (tile^2 / 2 instances) are ordered by the blend.
+uint32_t blend_sorted_max(const vrs_plan *P)
+{
+    return P->sort_mode == 2 ? (uint32_t)(P->tile * P->tile / 2) : 0u;
+}
+
 int views_of_scene(const vrs_plan *P, int s, int8_t *out)
 {
     int n = 0;
@@ -151,7 +159,8 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     const int tile = o.tile == 0 ? 16 : o.tile;
     if (tile != 8 && tile != 16 && tile != 32) return VRS_ERR_INVALID;
     if (o.max_instances < 0) return VRS_ERR_INVALID;
-    if (o.sort != 0 && o.sort != 1) return VRS_ERR_INVALID;
+    if (o.sort != 0 && o.sort != 1 && o.sort != 2) return VRS_ERR_INVALID;
+    if (o.sort == 2 && o.resort) return VRS_ERR_INVALID;     // the window kernel reads sorted lists
     if (o.resort != 0 && o.resort != 4 && o.resort != 8 && o.resort != 16) return VRS_ERR_INVALID;
     if (o.resort && (o.backward || (tile == 32 && o.resort > 8))) return VRS_ERR_INVALID;
     if (o.half_out && o.backward) return VRS_ERR_INVALID;
@@ -201,7 +210,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
         P.key_bits = o.key_bits;
     }
     P.sort_passes = (P.key_bits + 7) / 8;
-    P.sorted_buf = P.sort_mode == 0 ? 0 : P.sort_passes % 2;
+    P.sorted_buf = P.sort_mode == 1 ? P.sort_passes % 2 : 0;
     int64_t cap = o.max_instances > 0 ? o.max_instances : 4 * rec + 65536;
     if (cap > ((int64_t)1 << 31)) cap = (int64_t)1 << 31;
     P.max_instances = cap;
@@ -261,7 +270,7 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
     // scene has Gaussians
     uint32_t *tile_cnt = nullptr;
     int first = -1;
-    if (plan->sort_mode == 0) {
+    if (plan->sort_mode != 1) {
         tile_cnt = at<uint32_t>(workspace, plan->off_tilesort);
         for (int sc = 0; sc < plan->n_scenes && first < 0; ++sc)
             if (plan->scene_n[sc] > 0) {
@@ -294,7 +303,7 @@ vrs_status vrs_preprocess(const vrs_plan *plan, const vrs_scene *scenes, const v
 vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream)
 {
     if (!plan || !workspace) return VRS_ERR_INVALID;
-    if (plan->sort_mode == 0) {
+    if (plan->sort_mode != 1) {
         uint32_t *ts = at<uint32_t>(workspace, plan->off_tilesort);
         const int64_t nt = plan->n_tiles;
         cudaError_t e = launch_tile_sort(
@@ -302,7 +311,8 @@ vrs_status vrs_bin_sort(const vrs_plan *plan, void *workspace, void *stream)
             at<unsigned long long>(workspace, plan->off_keys[1]), at<unsigned long long>(workspace, plan->off_keys[0]),
             at<uint32_t>(workspace, plan->off_vals[0]), ts, ts + nt, ts + 3 * nt, ts + 2 * nt,
             at<uint2>(workspace, plan->off_ranges), at<DevStatus>(workspace, plan->off_status),
-            (unsigned long long)plan->max_instances, nt, plan->n_sms, static_cast<cudaStream_t>(stream));
+            (unsigned long long)plan->max_instances, nt, blend_sorted_max(plan), plan->n_sms,
+            static_cast<cudaStream_t>(stream));
         return cuda_status(e);
     }
     uint32_t *hist = at<uint32_t>(workspace, plan->off_hist);
@@ -342,7 +352,9 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         plan->backward ? at<uint32_t>(workspace, plan->off_ncontrib) : nullptr,   // only the reverse pass reads it
         order, order + plan->n_tiles, plan->n_tiles,
         plan->n_records, (unsigned long long)plan->max_instances, plan->persistent,
-        plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->tiles_per_pull, plan->n_sms,
+        plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->tiles_per_pull,
+        at<unsigned long long>(workspace, plan->off_keys[1]), at<unsigned long long>(workspace, plan->off_keys[sb]),
+        at<uint32_t>(workspace, plan->off_vals[sb]), blend_sorted_max(plan), plan->n_sms,
         static_cast<cudaStream_t>(stream));
     return cuda_status(e);
 }

@@ -34,6 +34,13 @@ struct FwdArgs {
     int persistent;
     int half_out;               // write the outputs as IEEE binary16
     int tiles_per_pull;         // persistent: work-order items claimed per atomic
+    // sort mode 2: a tile of <= blend_max instances is still an unsorted bucket of composites
+    // (depth bits << 32 | record index); the blend orders it while staging and writes the
+    // sorted key and record-index lists back
+    const unsigned long long *bucket;
+    unsigned long long *keys_w;
+    uint32_t *vals_w;
+    uint32_t blend_max;
 };
 
 // The state of a thread's two pixels, packed in pairs so that the blend's
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
     __shared__ uint16_t slist[Cfg::WARPS][Cfg::BATCH];
     __shared__ int64_t s_tile;
     __shared__ uint32_t s_k, s_left;      // persistent: the CTA's claimed run of the work order
+    __shared__ unsigned long long s_comp[Cfg::BATCH];   // sort mode 2: the tile's composites
     __shared__ unsigned long long s_cnt[3];
 
     const unsigned FULL = 0xffffffffu;
@@ -159,6 +167,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
         tile_origin((float)(tx * TS), pp.x, oxh, oxl);
         tile_origin((float)(ty * TS), pp.y, oyh, oyl);
         const uint2 range = live_range(a.ranges, t, a.st, a.cap);
+        // sort mode 2, a tile of one batch at most: order it here (CTA-uniform)
+        const bool rank_sort = a.blend_max != 0u && range.y - range.x <= a.blend_max;
 
         PixAcc2 P;
         P.T = f2(1.f);
@@ -174,22 +184,41 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
             // when all of its pixels have stopped (the first batch needs neither)
             if (bs != range.x && __syncthreads_and(P.done0 && P.done1)) break;
             const uint32_t j = bs + tid;
-            const uint32_t rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
+            uint32_t rid, slot = tid;
+            if (rank_sort) {
+                // the composites are unique (record indices differ): a splat's place is the
+                // number of smaller composites in the tile
+                const unsigned long long comp = j < range.y ? a.bucket[j] : ~0ull;
+                s_comp[tid] = comp;
+                __syncthreads();
+                const uint32_t n = range.y - range.x;
+                uint32_t r = 0;
+                for (uint32_t i = 0; i < n; ++i) r += s_comp[i] < comp ? 1u : 0u;
+                rid = 0xffffffffu;
+                if (j < range.y) {
+                    slot = r;
+                    rid = (uint32_t)comp;
+                    a.keys_w[range.x + r] = ((unsigned long long)t << 32) | (comp >> 32);
+                    a.vals_w[range.x + r] = rid;
+                }
+            } else {
+                rid = j < range.y ? __ldg(a.vals + j) : 0xffffffffu;
+            }
             uint32_t mask = 0u;
             if ((int64_t)rid < a.n_records) {
                 float4 r0, r1, r2, A, B, C;
                 load_record(a.rec, rid, r0, r1, r2);
                 stage_record(r0, r1, r2, oxh, oxl, oyh, oyl, A, B, C);
-                C.w = __int_as_float((int)(j - range.x + 1));
+                C.w = __int_as_float((int)(bs - range.x + slot + 1));
                 mask = cull_blocks<Cfg::WGX, Cfg::WARPS / Cfg::WGX>(cull_setup(A.x, A.y, A.z, A.w, B.x, B.z));
                 float K, L;
                 splat_KL(A.x, A.y, A.z, A.w, B.x, K, L);
-                sR[tid][0] = make_float4(K, L, -A.z, -A.w);   // the mean enters only through K and L
+                sR[slot][0] = make_float4(K, L, -A.z, -A.w);   // the mean enters only through K and L
                 B.x = -B.x;
-                sR[tid][1] = B;
-                sR[tid][2] = C;
+                sR[slot][1] = B;
+                sR[slot][2] = C;
             }
-            smask[tid] = mask;
+            smask[slot] = mask;
             __syncthreads();
             int cnt = 0;
 #pragma unroll
@@ -339,9 +368,15 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
                               unsigned long long cap, int persistent, int count, int half_out,
-                              int tiles_per_pull, int n_sms, cudaStream_t s)
+                              int tiles_per_pull, const unsigned long long *bucket,
+                              unsigned long long *keys_w, uint32_t *vals_w, uint32_t blend_max, int n_sms,
+                              cudaStream_t s)
 {
     FwdArgs a;
+    a.bucket = bucket;
+    a.keys_w = keys_w;
+    a.vals_w = vals_w;
+    a.blend_max = blend_max;
     a.half_out = half_out;
     a.tiles_per_pull = tiles_per_pull < 1 ? 1 : tiles_per_pull;
     a.cap = cap;

@@ -11,7 +11,7 @@
 //                                  of <= 256 instances (a bitonic network in
 //                                  registers and shuffles), and larger tiles one
 //                                  CTA each (a bitonic network in shared memory
-//                                  up to 4096, beyond that sorted 4096-runs
+//                                  up to 1024, beyond that sorted 1024-runs
 //                                  merged in global memory)
 // Sorting the composite orders equal depths by record index, so the result is
 // the unique (tile, depth, record) order and matches the radix path bit for bit.
@@ -21,7 +21,7 @@ namespace vrs {
 
 constexpr int kScanBlock = 1024;
 constexpr int kSmallMax = 256;
-constexpr int kBigChunk = 4096;
+constexpr int kBigChunk = 1024;       // shared-memory run of the big-tile path (8 KB)
 constexpr int kBigThreads = 256;
 
 struct TileSortArgs {
@@ -38,6 +38,8 @@ struct TileSortArgs {
     DevStatus *st;
     unsigned long long cap;
     int64_t n_tiles;
+    uint32_t blend_max;                  // sort mode 2: tiles of <= blend_max instances are left
+                                         // unsorted in the bucket for the blend to order (0: none)
 };
 
 __device__ __forceinline__ uint32_t live_instances(const DevStatus *st, unsigned long long cap)
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, 
     if (t < a.n_tiles) {
         a.ranges[t] = v ? make_uint2(off, off + v) : make_uint2(0u, 0u);
         a.cursor[t] = off;
-        if (v > (uint32_t)kSmallMax) a.big_list[atomicAdd(&a.st->work[1], 1u)] = (uint32_t)t;
+        if (v > (uint32_t)kSmallMax && v > a.blend_max) a.big_list[atomicAdd(&a.st->work[1], 1u)] = (uint32_t)t;
     }
 }
 
@@ -247,9 +249,10 @@ __device__ __forceinline__ void warp_sort_tile(const TileSortArgs &a, uint32_t t
 __device__ __forceinline__ void sort_small_tile(const TileSortArgs &a, int64_t t, int lane)
 {
     if (t >= a.n_tiles) return;
-    const uint32_t n = a.cnt[t];
-    if (n == 0 || n > (uint32_t)kSmallMax) return;
-    const uint32_t start = a.ranges[t].x;
+    const uint2 r = a.ranges[t];          // {start, end}, {0, 0} when empty: one load, no chain
+    const uint32_t n = r.y - r.x;
+    if (n == 0 || n > (uint32_t)kSmallMax || n <= a.blend_max) return;
+    const uint32_t start = r.x;
     if (n <= 32) warp_sort_tile<1>(a, (uint32_t)t, start, n, lane);
     else if (n <= 64) warp_sort_tile<2>(a, (uint32_t)t, start, n, lane);
     else if (n <= 128) warp_sort_tile<4>(a, (uint32_t)t, start, n, lane);
@@ -351,7 +354,7 @@ __device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned l
 // Both sorts in one launch, so that the few long big-tile CTAs overlap the many
 // short warp sorts: CTAs below n_big work through the big-tile list, the others
 // give each of their warps one tile.
-__global__ void __launch_bounds__(kBigThreads, 4) k_tile_sort(const TileSortArgs a, unsigned n_big)
+__global__ void __launch_bounds__(kBigThreads, 5) k_tile_sort(const TileSortArgs a, unsigned n_big)
 {
     __shared__ unsigned long long s[kBigChunk];
     __shared__ uint32_t s_idx;
@@ -368,11 +371,11 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
                              unsigned long long *bucket, unsigned long long *keys_out, uint32_t *vals_out,
                              const uint32_t *cnt, uint32_t *cursor, uint32_t *blocksum, uint32_t *big_list,
                              uint2 *ranges, DevStatus *st, unsigned long long cap, int64_t n_tiles,
-                             int n_sms, cudaStream_t s)
+                             uint32_t blend_max, int n_sms, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
     TileSortArgs a{keys_in, vals_in, bucket, keys_out, vals_out, cnt, cursor, blocksum, big_list,
-                   ranges, st, cap, n_tiles};
+                   ranges, st, cap, n_tiles, blend_max};
     cudaError_t e = cudaMemsetAsync(&st->work[1], 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((n_tiles + kScanBlock - 1) / kScanBlock);

@@ -252,3 +252,35 @@ def test_emission_large_rectangles(tile):
     bs = _check_sort(ras, [sc], [cam], tile)
     r = bs["ranges"]
     assert len(bs["keys"]) > 20 * 96 and (r[:, 1] - r[:, 0]).max() > 40
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_sort_mode_2_matches_mode_0(tile):
+    """Tiles of one blend batch ordered inside the blend: the same images bit for bit, the same
+    sorted lists after the forward (checked against the oracle), persistent too."""
+    torch = torch_cuda()
+    scenes, views = I.batched_multiview(scale=0.01)
+    views = views[:6] + views[12:16] + views[28:]
+    a = _run(scenes, views, tile=tile)
+    for kw in (dict(sort=2), dict(sort=2, persistent=True)):
+        b = _run(scenes, views, tile=tile, **kw)
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.depth, b.depth) and torch.equal(a.T, b.T), kw
+    _check_sort(b, scenes, views, tile)
+
+
+def test_sort_mode_2_backward_identical():
+    # the gradients accumulate with float atomics in no fixed order, so two runs agree to
+    # rounding, not bit for bit, in either mode
+    torch = torch_cuda()
+    scs, cams = I.plain_200()
+    g = I.upstream_grads(cams, 3)[0]
+    out = []
+    for sort in (0, 2):
+        ras, sts = make_rasterizer(scs, cams, backward=True, sort=sort)
+        ras.forward()
+        gr = ras.backward_params(torch.as_tensor(g[0].reshape(-1), device="cuda"),
+                                 torch.as_tensor(g[1].reshape(-1), device="cuda"))
+        torch.cuda.synchronize()
+        out.append([x.clone() for x in gr[0].tensors()])
+    for x, y in zip(*out):
+        assert torch.allclose(x, y, rtol=1e-5, atol=1e-6 * float(y.abs().max()))
