@@ -21,21 +21,30 @@ struct PreParams {
     uint32_t *tile_cnt;              // nullable: instances per tile (bucketed sort)
     DevStatus *st;
     unsigned long long cap;
-    float4 *viewtab;                 // [VRS_MAX_VIEWS] principal points, written by k_decide's first CTA
-    int64_t zero_tiles;              // > 0: k_decide clears tile_cnt[0, zero_tiles) (the frame's first
+    float4 *viewtab;                 // [VRS_MAX_VIEWS] principal points, written by the decision kernel's first CTA
+    int64_t zero_tiles;              // > 0: the decision kernel clears tile_cnt[0, zero_tiles) (the frame's first
                                      // scene, before any pair kernel counts into it)
     float4 *raydepth;                // nullable (per-pixel order plans): 3 float4 per record
 };
 
 // The step runs as two kernels per scene.
 //
-// k_decide reads only the 44 bytes of geometry per Gaussian (mean, log-scales,
-// quaternion, opacity logit), takes the FP32 integer decisions for every view
-// of the scene and appends each visible (Gaussian, view) pair to a list with
-// the decision values the record needs (one slot atomic per CTA and view).  Only about a quarter of the pairs of a VR view are visible, and
-// the visible ones cluster by Gaussian index (the scene's Gaussians come in
-// spatial clusters), so a fused kernel leaves most warps idle or most SMs
-// waiting on a few CTAs; the list makes the second kernel dense.
+// The decision kernel reads only the 44 bytes of geometry per Gaussian (mean,
+// log-scales, quaternion, opacity logit), applies the parameter rules, takes
+// the FP32 integer decisions for every view of the scene and appends each
+// visible (Gaussian, view) pair to a list with the decision values the record
+// needs (one slot atomic per CTA and round).  Only about a quarter of the pairs
+// of a VR view are visible, so the second kernel walks a list, not the scene.
+// It comes in two forms:
+//   k_decide         one view: each thread decides its own pair in place;
+//   k_decide_listed  several views: a cheap conservative bound of the splat's
+//                    extent screens every pair first, and the CTA's threads
+//                    take the exact decisions of the pairs it keeps densely,
+//                    from a candidate list in shared memory (the scene's
+//                    Gaussians are not ordered in space, so deciding every pair
+//                    in place runs the exact path on nearly every warp for every
+//                    view; with one view a list would leave most warps of the
+//                    CTA waiting at its barriers instead).
 //
 // k_pairs walks the list, one pair per thread: it reads the pair's SH row
 // (only visible Gaussians' colour coefficients are ever read), checks it,
@@ -44,6 +53,114 @@ struct PreParams {
 // per-lane counts, one atomic per CTA for the slots, coalesced key writes).
 constexpr int kDecideThreads = 256;
 constexpr int kPairThreads = 128;
+
+// The conservative bound of a splat's screen extent that screens the (Gaussian,
+// view) pairs before the exact path: Sigma' = V V^T + 0.3 I with V = (J W)(R S),
+// so the eigenvalue the radius takes (at most the trace plus sqrt(0.1), as the
+// discriminant is floored at 0.1) is below (|J_0|^2 + |J_1|^2) s_max^2 + 0.92,
+// with |J_0|^2 = (fx/z)^2 (1 + x'^2) for the clamped x' = x/z; the radius
+// ceil(3 sqrt(lambda)) is then below 3 sqrt(trace bound) + 1.  The bound adds 1 %
+// and 1 px more than FP32 rounding needs, and the rectangle clipped to the alpha
+// box only shrinks.  The camera-space depth is the exact path's own sequence, so
+// the near-plane test is the same.  True: the exact path could find the pair
+// visible; false: its rectangle would be empty.
+__device__ __forceinline__ bool may_touch_grid(const DevView &V, int tile, float mx, float my, float mz,
+                                               float s2)
+{
+    float tc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float a_ = __fmul_rn(V.R[3 * r], mx);
+        a_ = __fadd_rn(a_, __fmul_rn(V.R[3 * r + 1], my));
+        a_ = __fadd_rn(a_, __fmul_rn(V.R[3 * r + 2], mz));
+        tc[r] = __fadd_rn(a_, V.t[r]);
+    }
+    if (!(tc[2] > V.znear)) return false;
+    const float iz = rcp_approx(tc[2]);           // approximations: the bound has 1 % margins
+    const float rx = tc[0] * iz, ry = tc[1] * iz;
+    const float limx = 1.3f * V.tanx, limy = 1.3f * V.tany;
+    const float cx_ = fminf(limx, fmaxf(-limx, rx)), cy_ = fminf(limy, fmaxf(-limy, ry));
+    const float jx = V.fx * iz, jy = V.fy * iz;
+    const float tr = (jx * jx * (1.f + cx_ * cx_) + jy * jy * (1.f + cy_ * cy_)) * s2 + 1.0f;
+    const float R = 3.03f * sqrt_approx(tr) + 2.0f;
+    const float u = V.fx * rx + V.cx, v = V.fy * ry + V.cy;
+    const float gx = (float)(V.gw * tile), gy = (float)(V.gh * tile);
+    // written so that a NaN (from an overflowing mean) keeps the pair for the exact path
+    return !(u + R < 0.f || u - R >= gx || v + R < 0.f || v - R >= gy);
+}
+
+// The exact FP32 decisions of pair (Gaussian cg, view vi of the scene), from the
+// parameters or their baked form (decide_op: the only definition of visibility,
+// radius and rectangle).  The caller has applied the parameter rules.
+__device__ __forceinline__ void decide_pair(const ViewTable &vt, const PreParams &p, int cg, int vi, Decision &d)
+{
+    const float mx = __ldg(p.S.means + 3 * cg), my = __ldg(p.S.means + 3 * cg + 1);
+    const float mz = __ldg(p.S.means + 3 * cg + 2);
+    GaussPre pre;
+    float op;
+    if (p.S.baked) {
+        // the scales, rotation and opacity gauss_pre and decision_opacity compute, bit for bit
+        const float4 b0 = __ldg(p.S.baked + 4 * cg), b1 = __ldg(p.S.baked + 4 * cg + 1);
+        const float4 b2 = __ldg(p.S.baked + 4 * cg + 2), b3 = __ldg(p.S.baked + 4 * cg + 3);
+        pre.s[0] = b0.x; pre.s[1] = b0.y; pre.s[2] = b0.z;
+        pre.Rq[0] = b0.w; pre.Rq[1] = b1.x; pre.Rq[2] = b1.y; pre.Rq[3] = b1.z; pre.Rq[4] = b1.w;
+        pre.Rq[5] = b2.x; pre.Rq[6] = b2.y; pre.Rq[7] = b2.z; pre.Rq[8] = b2.w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pre.M[3 * k + j] = __fmul_rn(pre.Rq[3 * k + j], pre.s[j]);
+        op = b3.x;
+    } else {
+        float ls[3], q[4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ls[k] = __ldg(p.S.log_scales + 3 * cg + k);
+        if ((reinterpret_cast<uintptr_t>(p.S.quats) & 15u) == 0) {
+            const float4 qv = __ldg(reinterpret_cast<const float4 *>(p.S.quats) + cg);
+            q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = __ldg(p.S.quats + 4 * cg + k);
+        }
+        gauss_pre(ls, q, pre);                    // the rules have excluded a zero quaternion
+        op = decision_opacity(__ldg(p.S.logits + cg));
+    }
+    decide_op(vt.v[p.views[vi]], pre, mx, my, mz, op, vt.tile, d);
+}
+
+// Appends the visible pairs of one round (every thread of the CTA calls it, with
+// d.visible false where it has none): one slot atomic per CTA and round.
+__device__ __forceinline__ void append_visible(const PreParams &p, const Decision &d, int cg, int vi,
+                                               uint32_t *s_cnt, unsigned long long *s_base)
+{
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const uint32_t vb = __ballot_sync(0xffffffffu, d.visible);
+    if (lane == 0) s_cnt[wp] = __popc(vb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long sum = 0;
+        for (int w = 0; w < kDecideThreads / 32; ++w) sum += s_cnt[w];
+        unsigned long long b = sum ? atomicAdd(&p.st->scene_pairs[p.scene], sum) : 0ull;
+        for (int w = 0; w < kDecideThreads / 32; ++w) {
+            s_base[w] = b;
+            b += s_cnt[w];
+        }
+    }
+    __syncthreads();
+    if (d.visible) {
+        const unsigned long long slot = s_base[wp] + __popc(vb & lanemask_lt());
+        if (slot < p.pair_cap) {
+            uint4 *e = p.pairs + 2 * slot;
+            e[0] = make_uint4((uint32_t)cg, (uint32_t)vi, (uint32_t)d.x0 | ((uint32_t)d.x1 << 16),
+                              (uint32_t)d.y0 | ((uint32_t)d.y1 << 16));
+            e[1] = make_uint4(__float_as_uint(d.n1), __float_as_uint(d.b), __float_as_uint(d.det),
+                              __float_as_uint(d.tz));
+        }
+    }
+    // (a later round's counts are written only after every thread has passed the
+    // second barrier above, so no third one is needed)
+}
+
+constexpr int kViewChunk = 4;       // views screened per candidate list
 
 __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant__ ViewTable vt,
                                                            const __grid_constant__ PreParams p)
@@ -151,6 +268,114 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
                 e[1] = make_uint4(__float_as_uint(d.n1), __float_as_uint(d.b), __float_as_uint(d.det),
                                   __float_as_uint(d.tz));
             }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kDecideThreads) k_decide_listed(const __grid_constant__ ViewTable vt,
+                                                                  const __grid_constant__ PreParams p)
+{
+    // the views' principal points, read by the blend kernels to build each
+    // tile's local frame (the plan holds sizes only); every scene's launch
+    // writes the same values
+    if (blockIdx.x == 0 && threadIdx.x < vt.n_views)
+        p.viewtab[threadIdx.x] = make_float4(vt.v[threadIdx.x].cx, vt.v[threadIdx.x].cy, 0.f, 0.f);
+    for (int64_t t = (int64_t)blockIdx.x * kDecideThreads + threadIdx.x; t < p.zero_tiles;
+         t += (int64_t)gridDim.x * kDecideThreads)
+        p.tile_cnt[t] = 0u;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g0 = blockIdx.x * kDecideThreads;
+    const int g = g0 + tid;
+    const bool in = g < p.S.n;
+    // the parameter rules (non-finite values, the all-zero quaternion) and the
+    // largest scale, per Gaussian
+    float m[3] = {0.f, 0.f, 0.f}, smax = 0.f;
+    bool ok = in, zero_quat = false;
+    if (in) {
+        m[0] = __ldg(p.S.means + 3 * g);
+        m[1] = __ldg(p.S.means + 3 * g + 1);
+        m[2] = __ldg(p.S.means + 3 * g + 2);
+        // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so the sum of
+        // those products is finite exactly when every parameter is (a plain sum of the
+        // values could overflow on large finite ones)
+        float chk = __fmaf_rn(m[0], 0.f, __fmaf_rn(m[1], 0.f, __fmaf_rn(m[2], 0.f, 0.f)));
+        if (p.S.baked) {
+            // baked attributes (vrs_bake) carry the rules' outcome in their status word
+            const float4 b0 = __ldg(p.S.baked + 4 * g), b3 = __ldg(p.S.baked + 4 * g + 3);
+            const uint32_t bst = __float_as_uint(b3.z);
+            smax = fmaxf(b0.x, fmaxf(b0.y, b0.z));
+            zero_quat = (bst & 1u) != 0;
+            ok = isfinite(chk) && bst == 0u;
+        } else {
+            float ls[3], q[4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ls[i] = __ldg(p.S.log_scales + 3 * g + i);
+            if ((reinterpret_cast<uintptr_t>(p.S.quats) & 15u) == 0) {
+                const float4 qv = __ldg(reinterpret_cast<const float4 *>(p.S.quats) + g);
+                q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
+            }
+            const float logit = __ldg(p.S.logits + g);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) chk = __fmaf_rn(ls[i], 0.f, chk);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) chk = __fmaf_rn(q[i], 0.f, chk);
+            chk = __fmaf_rn(logit, 0.f, chk);
+            ok = isfinite(chk);
+            if (ok) {
+                // the zero-quaternion rule, with gauss_pre's own |q|^2
+                float qq = __fmul_rn(q[0], q[0]);
+                qq = __fadd_rn(qq, __fmul_rn(q[1], q[1]));
+                qq = __fadd_rn(qq, __fmul_rn(q[2], q[2]));
+                qq = __fadd_rn(qq, __fmul_rn(q[3], q[3]));
+                zero_quat = !(qq > 0.0f);
+                ok = !zero_quat;
+            }
+            smax = __expf(fmaxf(ls[0], fmaxf(ls[1], ls[2])));
+        }
+    }
+    if (in && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
+    if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
+    const float s2 = smax * smax * 1.01f;
+
+    __shared__ uint32_t s_cnt[kDecideThreads / 32];
+    __shared__ unsigned long long s_base[kDecideThreads / 32];
+    // Per chunk of views, the pairs the bound keeps form a list in shared memory and
+    // the CTA's threads take their exact decisions densely, one candidate each:
+    // only about a quarter of a VR view's pairs are visible and the scene's
+    // Gaussians are not ordered in space, so deciding every pair in place would
+    // run the exact path on nearly every warp for every view.
+    __shared__ uint16_t s_list[kViewChunk * kDecideThreads];   // (view in chunk) << 8 | thread
+    __shared__ uint32_t s_ncand;
+    for (int vc = 0; vc < p.n_views; vc += kViewChunk) {
+        const int nvc = min(kViewChunk, p.n_views - vc);
+        if (tid == 0) s_ncand = 0u;
+        __syncthreads();                          // (and the previous chunk's list is read)
+        for (int c = 0; c < nvc; ++c) {
+            const bool cand = ok && may_touch_grid(vt.v[p.views[vc + c]], vt.tile, m[0], m[1], m[2], s2);
+            const uint32_t vb = __ballot_sync(FULL, cand);
+            uint32_t base = 0u;
+            if (lane == 0 && vb) base = atomicAdd(&s_ncand, (uint32_t)__popc(vb));
+            base = __shfl_sync(FULL, base, 0);
+            if (cand) s_list[base + __popc(vb & lanemask_lt())] = (uint16_t)((c << 8) | tid);
+        }
+        __syncthreads();
+        const uint32_t nc = s_ncand;
+        for (uint32_t r0 = 0; r0 < nc; r0 += kDecideThreads) {
+            const uint32_t i = r0 + tid;
+            Decision d;
+            d.visible = false;
+            int cg = 0, vi = 0;
+            if (i < nc) {
+                const uint32_t e = s_list[i];
+                cg = g0 + (int)(e & 255u);
+                vi = vc + (int)(e >> 8);
+                decide_pair(vt, p, cg, vi, d);
+            }
+            append_visible(p, d, cg, vi, s_cnt, s_base);
         }
     }
 }
@@ -464,7 +689,9 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     p.cap = cap;
     p.viewtab = viewtab;
     p.zero_tiles = tile_cnt ? zero_tiles : 0;
-    k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
+    // one view: each thread decides its pair in place; several: the candidate lists
+    if (n_views == 1) k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
+    else k_decide_listed<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one pair per thread up to the list's capacity; CTAs past the device-side
