@@ -323,6 +323,52 @@ struct ParamArgs {
     uint32_t *list_count;
 };
 
+// The 3K values of an SH row in order, f(index, value), as 16-byte loads where
+// the row's length and start allow (vec: the array base is 16-byte aligned).
+template <int K, typename F>
+__device__ __forceinline__ void sh_row_read(const float *row, bool vec, F f)
+{
+    if constexpr ((12 * K) % 16 == 0) {
+        if (vec) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+            for (int c = 0; c < 3 * K / 4; ++c) {
+                const float4 v = __ldg(r4 + c);
+                f(4 * c, v.x);
+                f(4 * c + 1, v.y);
+                f(4 * c + 2, v.z);
+                f(4 * c + 3, v.w);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) f(i, __ldg(row + i));
+}
+
+// row[i] += val(i) over an SH gradient row, as 16-byte loads and stores where allowed.
+template <int K, typename F>
+__device__ __forceinline__ void sh_row_add(float *row, bool vec, F val)
+{
+    if constexpr ((12 * K) % 16 == 0) {
+        if (vec) {
+            float4 *r4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+            for (int c = 0; c < 3 * K / 4; ++c) {
+                float4 v = r4[c];
+                v.x += val(4 * c);
+                v.y += val(4 * c + 1);
+                v.z += val(4 * c + 2);
+                v.w += val(4 * c + 3);
+                r4[c] = v;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3 * K; ++i) row[i] += val(i);
+}
+
 template <int K>
 __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const ParamArgs &p, int g)
 {
@@ -336,17 +382,22 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
     float *gs_out = const_cast<float *>(p.G.sh) + (size_t)g * 3 * K;
     float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gqh[4] = {0.f, 0.f, 0.f, 0.f}, glogit = 0.f;
     const float o = 1.0f / (1.0f + expf(-logit));
+    const bool vec_in = (reinterpret_cast<uintptr_t>(p.S.sh) & 15u) == 0;
+    const bool vec_out = (reinterpret_cast<uintptr_t>(p.G.sh) & 15u) == 0;
     bool any = false;
 
     for (int vi = 0; vi < p.n_views; ++vi) {
         const DevView &V = vt.v[p.views[vi]];
-        const float *G2 = p.grad2d + (size_t)(V.rec_base + g) * kGrad2D;
+        // a record's 10 gradients are 5 float2 (40-byte records in an aligned array)
+        const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(V.rec_base + g) * kGrad2D);
         float G[kGrad2D];
         bool nz = false;
 #pragma unroll
-        for (int i = 0; i < kGrad2D; ++i) {
-            G[i] = G2[i];
-            nz |= G[i] != 0.f;
+        for (int i = 0; i < kGrad2D / 2; ++i) {
+            const float2 v = G2[i];
+            G[2 * i] = v.x;
+            G[2 * i + 1] = v.y;
+            nz |= v.x != 0.f || v.y != 0.f;
         }
         if (!nz) continue;
         Decision d;
@@ -367,22 +418,14 @@ __device__ __forceinline__ void param_grads_one(const ViewTable &vt, const Param
         float Y[16];
         sh_basis(dx, dy, dz, K, Y);
         float col[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) col[ch] += Y[k] * __ldg(shg + 3 * k + ch);
+        sh_row_read<K>(shg, vec_in, [&](int i, float v) { col[i % 3] += Y[i / 3] * v; });
         // max(0, .) clamped channels pass no gradient
         const float gc[3] = {col[0] < 0.f ? 0.f : G[6], col[1] < 0.f ? 0.f : G[7], col[2] < 0.f ? 0.f : G[8]};
         float wY[16];                                 // dL/dY_k
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            wY[k] = 0.f;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                wY[k] += gc[ch] * __ldg(shg + 3 * k + ch);
-                gs_out[3 * k + ch] += gc[ch] * Y[k];
-            }
-        }
+        for (int k = 0; k < 16; ++k) wY[k] = 0.f;
+        sh_row_read<K>(shg, vec_in, [&](int i, float v) { wY[i / 3] += gc[i % 3] * v; });
+        sh_row_add<K>(gs_out, vec_out, [&](int i) { return gc[i % 3] * Y[i / 3]; });
         float Yx[16], Yy[16], Yz[16];
         sh_basis_grad(dx, dy, dz, K, Yx, Yy, Yz);
         float gd0 = 0.f, gd1 = 0.f, gd2 = 0.f;
