@@ -113,15 +113,18 @@ __device__ __forceinline__ void flush_group(float (*G)[kGStride], const uint32_t
 {
     __syncwarp();
     for (int p = lane; p < ng * kGrad2D; p += 32) {
+        // the row's 32 values as 16 FP32x2 pairs: two packed accumulators
         const float4 *row = reinterpret_cast<const float4 *>(G[p]);
-        float4 acc = row[0];
+        const float4 r0 = row[0];
+        float2 a01 = make_float2(r0.x, r0.y), a23 = make_float2(r0.z, r0.w);
 #pragma unroll
         for (int j = 1; j < 8; ++j) {
             const float4 q = row[j];
-            acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
+            a01 = __fadd2_rn(a01, make_float2(q.x, q.y));
+            a23 = __fadd2_rn(a23, make_float2(q.z, q.w));
         }
         const int sp = p / kGrad2D, v = p - sp * kGrad2D;
-        atomicAdd(grad2d + (size_t)R[sp] * kGrad2D + v, (acc.x + acc.y) + (acc.z + acc.w));
+        atomicAdd(grad2d + (size_t)R[sp] * kGrad2D + v, (a01.x + a01.y) + (a23.x + a23.y));
     }
     __syncwarp();
 }
@@ -133,6 +136,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     using Cfg = BlendCfg<TS>;
     __shared__ float4 wA[Cfg::WARPS][32], wB[Cfg::WARPS][32], wC[Cfg::WARPS][32];
     __shared__ uint32_t wR[Cfg::WARPS][32];
+    __shared__ float2 wKL[Cfg::WARPS][32];     // the staged splats' K, L (splat_KL)
     // per-lane gradient contributions of up to kGroup splats, reduced together
     __shared__ __align__(16) float wG[Cfg::WARPS][kGroup * kGrad2D][kGStride];
     __shared__ uint32_t wGR[Cfg::WARPS][kGroup];
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const uint32_t lmask = lanemask_lt();
     const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
+    const float2 pxc2 = make_float2(pxc, pxc + 1.0f);
 
     const int64_t t = blockIdx.x;
     const int vi = view_of_tile(vt, t);
@@ -211,6 +216,9 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             wB[w][slot] = B;
             wC[w][slot] = C;
             wR[w][slot] = rid;
+            float K, L;
+            splat_KL(A.x, A.y, A.z, A.w, B.x, K, L);
+            wKL[w][slot] = make_float2(K, L);
         }
         __syncwarp();
         for (int k = __popc(bal) - 1; k >= 0; --k) {
@@ -218,9 +226,14 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
             const float4 Bk = wB[w][k];
             const float4 Ck = wC[w][k];
             const uint32_t pos = (uint32_t)bi * 32 + (uint32_t)__float_as_int(Ck.w) + 1;
-            float u0, u1, K, L;
-            splat_KL(Ak.x, Ak.y, Ak.z, Ak.w, Bk.x, K, L);
-            pair_u2(K, L, Ak.z, Ak.w, Bk.x, Bk.y, pxc, pyc, u0, u1);
+            // pair_u2 with the per-pixel steps packed (each component the same rounded FMA)
+            const float2 KL = wKL[w][k];
+            const float s_ = __fmaf_rn(-Bk.x, pyc, KL.y);
+            const float w_ = __fmaf_rn(s_, s_, -Bk.y);
+            const float r_ = __fmaf_rn(-Ak.w, pyc, KL.x);
+            const float2 t_ = __ffma2_rn(f2(-Ak.z), pxc2, f2(r_));
+            const float2 u_ = __ffma2_rn(t_, t_, f2(w_));
+            const float u0 = u_.x, u1 = u_.y;
             const bool c0 = pos <= P.last0 && u0 <= kLog2_255;
             const bool c1 = pos <= P.last1 && u1 <= kLog2_255;
             if (!__any_sync(FULL, c0 || c1)) continue;
