@@ -29,22 +29,17 @@ struct PreParams {
 
 // The step runs as two kernels per scene.
 //
-// The decision kernel reads only the 44 bytes of geometry per Gaussian (mean,
-// log-scales, quaternion, opacity logit), applies the parameter rules, takes
-// the FP32 integer decisions for every view of the scene and appends each
-// visible (Gaussian, view) pair to a list with the decision values the record
-// needs (one slot atomic per CTA and round).  Only about a quarter of the pairs
-// of a VR view are visible, so the second kernel walks a list, not the scene.
-// It comes in two forms:
-//   k_decide         one view: each thread decides its own pair in place;
-//   k_decide_listed  several views: a cheap conservative bound of the splat's
-//                    extent screens every pair first, and the CTA's threads
-//                    take the exact decisions of the pairs it keeps densely,
-//                    from a candidate list in shared memory (the scene's
-//                    Gaussians are not ordered in space, so deciding every pair
-//                    in place runs the exact path on nearly every warp for every
-//                    view; with one view a list would leave most warps of the
-//                    CTA waiting at its barriers instead).
+// k_decide_listed reads only the 44 bytes of geometry per Gaussian (mean,
+// log-scales, quaternion, opacity logit), applies the parameter rules, screens
+// every (Gaussian, view) pair with a cheap conservative bound of the splat's
+// extent, and the CTA's threads take the exact FP32 integer decisions of the
+// pairs the bound keeps densely, from a candidate list in shared memory; each
+// visible pair is appended to a list with the decision values the record needs
+// (one slot atomic per CTA and round).  Only a fraction of a view's pairs is
+// visible (a quarter in a VR eye, 6 % in the training view) and the scene's
+// Gaussians are not ordered in space, so deciding every pair in place would run
+// the exact path on nearly every warp; the list also makes the second kernel
+// walk the visible pairs, not the scene.
 //
 // k_pairs walks the list, one pair per thread: it reads the pair's SH row
 // (only visible Gaussians' colour coefficients are ever read), checks it,
@@ -162,53 +157,32 @@ __device__ __forceinline__ void append_visible(const PreParams &p, const Decisio
 
 constexpr int kViewChunk = 4;       // views screened per candidate list
 
-__global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant__ ViewTable vt,
-                                                           const __grid_constant__ PreParams p)
+// The parameter rules of Gaussian g (non-finite values, the all-zero
+// quaternion; flagged in the status block when `flag`) and what the screening
+// bound needs: the mean and 1.01 x the largest scale squared.  False when the
+// rules exclude the Gaussian.
+__device__ __forceinline__ bool gauss_rules(const PreParams &p, int g, bool flag, float (&m)[3], float &s2)
 {
-    // the views' principal points, read by the blend kernels to build each
-    // tile's local frame (the plan holds sizes only); every scene's launch
-    // writes the same values
-    if (blockIdx.x == 0 && threadIdx.x < vt.n_views)
-        p.viewtab[threadIdx.x] = make_float4(vt.v[threadIdx.x].cx, vt.v[threadIdx.x].cy, 0.f, 0.f);
-    for (int64_t t = (int64_t)blockIdx.x * kDecideThreads + threadIdx.x; t < p.zero_tiles;
-         t += (int64_t)gridDim.x * kDecideThreads)
-        p.tile_cnt[t] = 0u;
-    const unsigned FULL = 0xffffffffu;
-    const int g = blockIdx.x * kDecideThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const bool in = g < p.S.n;
-    float m[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
-    float logit = 0.f, op = 0.f;
-    bool ok = in;
-    GaussPre pre;
-    bool zero_quat = false;
-    if (in && p.S.baked) {
-        // baked attributes (vrs_bake): the scales, rotation and opacity the lines below
-        // would compute, bit for bit
-        m[0] = __ldg(p.S.means + 3 * g);
-        m[1] = __ldg(p.S.means + 3 * g + 1);
-        m[2] = __ldg(p.S.means + 3 * g + 2);
-        const float4 b0 = __ldg(p.S.baked + 4 * g), b1 = __ldg(p.S.baked + 4 * g + 1);
-        const float4 b2 = __ldg(p.S.baked + 4 * g + 2), b3 = __ldg(p.S.baked + 4 * g + 3);
-        pre.s[0] = b0.x; pre.s[1] = b0.y; pre.s[2] = b0.z;
-        pre.Rq[0] = b0.w; pre.Rq[1] = b1.x; pre.Rq[2] = b1.y; pre.Rq[3] = b1.z; pre.Rq[4] = b1.w;
-        pre.Rq[5] = b2.x; pre.Rq[6] = b2.y; pre.Rq[7] = b2.z; pre.Rq[8] = b2.w;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) pre.M[3 * k + j] = __fmul_rn(pre.Rq[3 * k + j], pre.s[j]);
-        op = b3.x;
+    m[0] = __ldg(p.S.means + 3 * g);
+    m[1] = __ldg(p.S.means + 3 * g + 1);
+    m[2] = __ldg(p.S.means + 3 * g + 2);
+    // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so the sum of
+    // those products is finite exactly when every parameter is (a plain sum of the
+    // values could overflow on large finite ones)
+    float chk = __fmaf_rn(m[0], 0.f, __fmaf_rn(m[1], 0.f, __fmaf_rn(m[2], 0.f, 0.f)));
+    bool ok, zero_quat = false;
+    float smax;
+    if (p.S.baked) {
+        // baked attributes (vrs_bake) carry the rules' outcome in their status word
+        const float4 b0 = __ldg(p.S.baked + 4 * g), b3 = __ldg(p.S.baked + 4 * g + 3);
         const uint32_t bst = __float_as_uint(b3.z);
-        const float chk = __fmaf_rn(m[0], 0.f, __fmaf_rn(m[1], 0.f, __fmaf_rn(m[2], 0.f, 0.f)));
+        smax = fmaxf(b0.x, fmaxf(b0.y, b0.z));
         zero_quat = (bst & 1u) != 0;
         ok = isfinite(chk) && bst == 0u;
-    } else if (in) {
-        m[0] = __ldg(p.S.means + 3 * g);
-        m[1] = __ldg(p.S.means + 3 * g + 1);
-        m[2] = __ldg(p.S.means + 3 * g + 2);
-        ls[0] = __ldg(p.S.log_scales + 3 * g);
-        ls[1] = __ldg(p.S.log_scales + 3 * g + 1);
-        ls[2] = __ldg(p.S.log_scales + 3 * g + 2);
+    } else {
+        float ls[3], q[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ls[i] = __ldg(p.S.log_scales + 3 * g + i);
         if ((reinterpret_cast<uintptr_t>(p.S.quats) & 15u) == 0) {
             const float4 qv = __ldg(reinterpret_cast<const float4 *>(p.S.quats) + g);
             q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
@@ -216,62 +190,34 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const __grid_constant
 #pragma unroll
             for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
         }
-        logit = __ldg(p.S.logits + g);
-        // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so the sum of
-        // those products is finite exactly when every parameter is (a plain sum of the
-        // values could overflow on large finite ones)
-        const float vals[11] = {m[0], m[1], m[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
-        float chk = 0.f;
+        const float logit = __ldg(p.S.logits + g);
 #pragma unroll
-        for (int i = 0; i < 11; ++i) chk = __fmaf_rn(vals[i], 0.f, chk);
-        if (!isfinite(chk)) ok = false;
-        if (ok && !gauss_pre(ls, q, pre)) {
-            ok = false;
-            zero_quat = true;
+        for (int i = 0; i < 3; ++i) chk = __fmaf_rn(ls[i], 0.f, chk);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) chk = __fmaf_rn(q[i], 0.f, chk);
+        chk = __fmaf_rn(logit, 0.f, chk);
+        ok = isfinite(chk);
+        if (ok) {
+            // the zero-quaternion rule, with gauss_pre's own |q|^2
+            float qq = __fmul_rn(q[0], q[0]);
+            qq = __fadd_rn(qq, __fmul_rn(q[1], q[1]));
+            qq = __fadd_rn(qq, __fmul_rn(q[2], q[2]));
+            qq = __fadd_rn(qq, __fmul_rn(q[3], q[3]));
+            zero_quat = !(qq > 0.0f);
+            ok = !zero_quat;
         }
-        op = decision_opacity(logit);
+        smax = __expf(fmaxf(ls[0], fmaxf(ls[1], ls[2])));
     }
-    if (in && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
-    if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
-    // one slot atomic per CTA and view (all CTAs add to the same counter): the warps'
-    // counts meet in shared memory, double-buffered by view parity
-    __shared__ uint32_t s_cnt[2][kDecideThreads / 32];
-    __shared__ unsigned long long s_base[2][kDecideThreads / 32];
-    const int wp = threadIdx.x >> 5;
-    const bool wok = __any_sync(FULL, ok);
-    for (int vi = 0; vi < p.n_views; ++vi) {
-        const DevView &V = vt.v[p.views[vi]];
-        Decision d;
-        d.visible = false;
-        if (ok) decide_op(V, pre, m[0], m[1], m[2], op, vt.tile, d);
-        const uint32_t vb = wok ? __ballot_sync(FULL, d.visible) : 0u;
-        const int par = vi & 1;
-        if (lane == 0) s_cnt[par][wp] = __popc(vb);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long sum = 0;
-            for (int q = 0; q < kDecideThreads / 32; ++q) sum += s_cnt[par][q];
-            unsigned long long b = sum ? atomicAdd(&p.st->scene_pairs[p.scene], sum) : 0ull;
-            for (int q = 0; q < kDecideThreads / 32; ++q) {
-                s_base[par][q] = b;
-                b += s_cnt[par][q];
-            }
-        }
-        __syncthreads();
-        const unsigned long long base = s_base[par][wp];
-        if (d.visible) {
-            const unsigned long long slot = base + __popc(vb & lanemask_lt());
-            if (slot < p.pair_cap) {
-                uint4 *e = p.pairs + 2 * slot;
-                e[0] = make_uint4((uint32_t)g, (uint32_t)vi, (uint32_t)d.x0 | ((uint32_t)d.x1 << 16),
-                                  (uint32_t)d.y0 | ((uint32_t)d.y1 << 16));
-                e[1] = make_uint4(__float_as_uint(d.n1), __float_as_uint(d.b), __float_as_uint(d.det),
-                                  __float_as_uint(d.tz));
-            }
-        }
-    }
+    if (flag && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
+    if (flag && zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
+    s2 = smax * smax * 1.01f;
+    return ok;
 }
 
+// Gaussians per thread of the listed decision kernel: one CTA screens
+// kDecideThreads x PER Gaussians into one candidate list, so the latency of the
+// exact path is paid once for all of them.
+template <int PER>
 __global__ void __launch_bounds__(kDecideThreads) k_decide_listed(const __grid_constant__ ViewTable vt,
                                                                   const __grid_constant__ PreParams p)
 {
@@ -285,82 +231,35 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide_listed(const __grid_c
         p.tile_cnt[t] = 0u;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int g0 = blockIdx.x * kDecideThreads;
-    const int g = g0 + tid;
-    const bool in = g < p.S.n;
-    // the parameter rules (non-finite values, the all-zero quaternion) and the
-    // largest scale, per Gaussian
-    float m[3] = {0.f, 0.f, 0.f}, smax = 0.f;
-    bool ok = in, zero_quat = false;
-    if (in) {
-        m[0] = __ldg(p.S.means + 3 * g);
-        m[1] = __ldg(p.S.means + 3 * g + 1);
-        m[2] = __ldg(p.S.means + 3 * g + 2);
-        // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so the sum of
-        // those products is finite exactly when every parameter is (a plain sum of the
-        // values could overflow on large finite ones)
-        float chk = __fmaf_rn(m[0], 0.f, __fmaf_rn(m[1], 0.f, __fmaf_rn(m[2], 0.f, 0.f)));
-        if (p.S.baked) {
-            // baked attributes (vrs_bake) carry the rules' outcome in their status word
-            const float4 b0 = __ldg(p.S.baked + 4 * g), b3 = __ldg(p.S.baked + 4 * g + 3);
-            const uint32_t bst = __float_as_uint(b3.z);
-            smax = fmaxf(b0.x, fmaxf(b0.y, b0.z));
-            zero_quat = (bst & 1u) != 0;
-            ok = isfinite(chk) && bst == 0u;
-        } else {
-            float ls[3], q[4];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) ls[i] = __ldg(p.S.log_scales + 3 * g + i);
-            if ((reinterpret_cast<uintptr_t>(p.S.quats) & 15u) == 0) {
-                const float4 qv = __ldg(reinterpret_cast<const float4 *>(p.S.quats) + g);
-                q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) q[i] = __ldg(p.S.quats + 4 * g + i);
-            }
-            const float logit = __ldg(p.S.logits + g);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) chk = __fmaf_rn(ls[i], 0.f, chk);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) chk = __fmaf_rn(q[i], 0.f, chk);
-            chk = __fmaf_rn(logit, 0.f, chk);
-            ok = isfinite(chk);
-            if (ok) {
-                // the zero-quaternion rule, with gauss_pre's own |q|^2
-                float qq = __fmul_rn(q[0], q[0]);
-                qq = __fadd_rn(qq, __fmul_rn(q[1], q[1]));
-                qq = __fadd_rn(qq, __fmul_rn(q[2], q[2]));
-                qq = __fadd_rn(qq, __fmul_rn(q[3], q[3]));
-                zero_quat = !(qq > 0.0f);
-                ok = !zero_quat;
-            }
-            smax = __expf(fmaxf(ls[0], fmaxf(ls[1], ls[2])));
-        }
-    }
-    if (in && !ok && !zero_quat) atomicOr(&p.st->flags, ST_NONFINITE);
-    if (zero_quat) atomicOr(&p.st->flags, ST_ZERO_QUAT);
-    const float s2 = smax * smax * 1.01f;
+    const int g0 = blockIdx.x * kDecideThreads * PER;
 
     __shared__ uint32_t s_cnt[kDecideThreads / 32];
     __shared__ unsigned long long s_base[kDecideThreads / 32];
     // Per chunk of views, the pairs the bound keeps form a list in shared memory and
     // the CTA's threads take their exact decisions densely, one candidate each:
-    // only about a quarter of a VR view's pairs are visible and the scene's
-    // Gaussians are not ordered in space, so deciding every pair in place would
-    // run the exact path on nearly every warp for every view.
-    __shared__ uint16_t s_list[kViewChunk * kDecideThreads];   // (view in chunk) << 8 | thread
+    // only a fraction of a view's pairs is visible (a quarter in a VR eye, 6 % in
+    // the training view) and the scene's Gaussians are not ordered in space, so
+    // deciding every pair in place would run the exact path on nearly every warp.
+    __shared__ uint32_t s_list[kViewChunk * kDecideThreads * PER];   // view in chunk << 16 | Gaussian in CTA
     __shared__ uint32_t s_ncand;
     for (int vc = 0; vc < p.n_views; vc += kViewChunk) {
         const int nvc = min(kViewChunk, p.n_views - vc);
         if (tid == 0) s_ncand = 0u;
         __syncthreads();                          // (and the previous chunk's list is read)
-        for (int c = 0; c < nvc; ++c) {
-            const bool cand = ok && may_touch_grid(vt.v[p.views[vc + c]], vt.tile, m[0], m[1], m[2], s2);
-            const uint32_t vb = __ballot_sync(FULL, cand);
-            uint32_t base = 0u;
-            if (lane == 0 && vb) base = atomicAdd(&s_ncand, (uint32_t)__popc(vb));
-            base = __shfl_sync(FULL, base, 0);
-            if (cand) s_list[base + __popc(vb & lanemask_lt())] = (uint16_t)((c << 8) | tid);
+#pragma unroll 1
+        for (int r = 0; r < PER; ++r) {
+            const int lg = r * kDecideThreads + tid;
+            const int g = g0 + lg;
+            float m[3] = {0.f, 0.f, 0.f}, s2 = 0.f;
+            const bool ok = g < p.S.n && gauss_rules(p, g, vc == 0, m, s2);
+            for (int c = 0; c < nvc; ++c) {
+                const bool cand = ok && may_touch_grid(vt.v[p.views[vc + c]], vt.tile, m[0], m[1], m[2], s2);
+                const uint32_t vb = __ballot_sync(FULL, cand);
+                uint32_t base = 0u;
+                if (lane == 0 && vb) base = atomicAdd(&s_ncand, (uint32_t)__popc(vb));
+                base = __shfl_sync(FULL, base, 0);
+                if (cand) s_list[base + __popc(vb & lanemask_lt())] = ((uint32_t)c << 16) | (uint32_t)lg;
+            }
         }
         __syncthreads();
         const uint32_t nc = s_ncand;
@@ -371,8 +270,8 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide_listed(const __grid_c
             int cg = 0, vi = 0;
             if (i < nc) {
                 const uint32_t e = s_list[i];
-                cg = g0 + (int)(e & 255u);
-                vi = vc + (int)(e >> 8);
+                cg = g0 + (int)(e & 0xffffu);
+                vi = vc + (int)(e >> 16);
                 decide_pair(vt, p, cg, vi, d);
             }
             append_visible(p, d, cg, vi, s_cnt, s_base);
@@ -689,9 +588,12 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     p.cap = cap;
     p.viewtab = viewtab;
     p.zero_tiles = tile_cnt ? zero_tiles : 0;
-    // one view: each thread decides its pair in place; several: the candidate lists
-    if (n_views == 1) k_decide<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
-    else k_decide_listed<<<grid_for(S.n, kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
+    // one view: 8 Gaussians per thread (about 6 % of a training view's pairs survive
+    // the screen, so a CTA gathers enough candidates to keep its threads busy);
+    // several views: 2 per thread (a quarter of an eye's pairs survive, and more
+    // CTAs keep more of the exact path's latency in flight)
+    if (n_views == 1) k_decide_listed<8><<<grid_for(S.n, 8 * kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
+    else k_decide_listed<2><<<grid_for(S.n, 2 * kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one pair per thread up to the list's capacity; CTAs past the device-side
