@@ -10,9 +10,10 @@
 //   k_tile_sort                    one launch for both sizes: one warp per tile
 //                                  of <= 256 instances (a bitonic network in
 //                                  registers and shuffles), and larger tiles one
-//                                  CTA each (a bitonic network in shared memory
-//                                  up to 1024, beyond that sorted 1024-runs
-//                                  merged in global memory)
+//                                  CTA each (runs of 128 sorted by its warps in
+//                                  registers and merged in shared memory up to
+//                                  1024, beyond that sorted 1024-runs merged in
+//                                  global memory)
 // Sorting the composite orders equal depths by record index, so the result is
 // the unique (tile, depth, record) order and matches the radix path bit for bit.
 #include "vrs_internal.cuh"
@@ -148,13 +149,6 @@ __global__ void __launch_bounds__(256) k_tile_scatter(const TileSortArgs a)
     }
 }
 
-__device__ __forceinline__ void cmp_swap(unsigned long long &x, unsigned long long &y, bool asc)
-{
-    const unsigned long long lo = x < y ? x : y, hi = x < y ? y : x;
-    x = asc ? lo : hi;
-    y = asc ? hi : lo;
-}
-
 // Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i],
 // in the form whose comparators all put the minimum at the lower element: each
 // merge of width k starts by comparing e with its mirror e ^ (k - 1), then
@@ -259,23 +253,46 @@ __device__ __forceinline__ void sort_small_tile(const TileSortArgs &a, int64_t t
     else warp_sort_tile<8>(a, (uint32_t)t, start, n, lane);
 }
 
-// Bitonic sort of P (a power of two <= kBigChunk) composites in shared memory.
-__device__ void block_bitonic(unsigned long long *s, uint32_t P)
+// Sorts the P composites of s (P a power of two, 256 <= P <= kBigChunk; the
+// caller pads with ~0): each warp sorts a run of 128 in registers (the warp
+// bitonic network), then log2(P / 128) merge-path passes in shared memory, each
+// thread writing P / kBigThreads consecutive outputs of its pair of runs.
+// Returns the buffer that holds the result (s or t).
+__device__ unsigned long long *chunk_sort(unsigned long long *s, unsigned long long *t, uint32_t P)
 {
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t e = threadIdx.x; e < P; e += blockDim.x) {
-                const uint32_t o = e ^ j;
-                if (o > e) {
-                    unsigned long long x = s[e], y = s[o];
-                    cmp_swap(x, y, (e & k) == 0);
-                    s[e] = x;
-                    s[o] = y;
-                }
-            }
-            __syncthreads();
-        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if ((uint32_t)(128 * w) < P) {
+        unsigned long long v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = s[128 * w + 32 * i + lane];
+        warp_bitonic<4>(v, lane);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s[128 * w + 32 * i + lane] = v[i];
     }
+    __syncthreads();
+    unsigned long long *src = s, *dst = t;
+    const uint32_t ipt = P / kBigThreads;
+    for (uint32_t L = 128; L < P; L <<= 1) {
+        const uint32_t o0 = threadIdx.x * ipt;
+        const uint32_t pr = o0 / (2 * L), d = o0 - pr * 2 * L;
+        const unsigned long long *A = src + pr * 2 * L, *B = A + L;
+        // split of diagonal d: the number of elements taken from A
+        uint32_t lo = d > L ? d - L : 0u, hi = d < L ? d : L;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+        }
+        uint32_t i = lo, j = d - lo;
+        for (uint32_t k = 0; k < ipt; ++k) {
+            const bool takeA = j >= L || (i < L && A[i] <= B[j]);
+            dst[o0 + k] = takeA ? A[i++] : B[j++];
+        }
+        __syncthreads();
+        unsigned long long *x = src;
+        src = dst;
+        dst = x;
+    }
+    return src;
 }
 
 // Merges sorted src[0, la) and src[la, la + lb) into dst (merge path; one CTA).
@@ -301,7 +318,8 @@ __device__ void block_merge(const unsigned long long *src, uint32_t la, uint32_t
 
 // One CTA pulls tiles of more than 256 instances from the big-tile list until it
 // is empty: sorted runs of kBigChunk in shared memory, merged in global memory.
-__device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned long long *s, uint32_t &s_idx)
+__device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned long long *s, unsigned long long *s2,
+                                               uint32_t &s_idx)
 {
     const uint32_t n_big = a.st->work[1];
     for (;;) {
@@ -317,12 +335,12 @@ __device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned l
         // sorted runs of kBigChunk in the bucket
         for (uint32_t c0 = 0; c0 < n; c0 += kBigChunk) {
             const uint32_t m = min((uint32_t)kBigChunk, n - c0);
-            uint32_t P = 32;
+            uint32_t P = 256;
             while (P < m) P <<= 1;
             for (uint32_t e = threadIdx.x; e < P; e += blockDim.x) s[e] = e < m ? bk[c0 + e] : ~0ull;
             __syncthreads();
-            block_bitonic(s, P);
-            for (uint32_t e = threadIdx.x; e < m; e += blockDim.x) bk[c0 + e] = s[e];
+            const unsigned long long *r = chunk_sort(s, s2, P);
+            for (uint32_t e = threadIdx.x; e < m; e += blockDim.x) bk[c0 + e] = r[e];
             __syncthreads();
         }
         // pairwise merges, bucket <-> scratch
@@ -356,11 +374,11 @@ __device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned l
 // give each of their warps one tile.
 __global__ void __launch_bounds__(kBigThreads, 5) k_tile_sort(const TileSortArgs a, unsigned n_big)
 {
-    __shared__ unsigned long long s[kBigChunk];
+    __shared__ unsigned long long s[kBigChunk], s2[kBigChunk];
     __shared__ uint32_t s_idx;
     if (live_instances(a.st, a.cap) == 0) return;
     if (blockIdx.x < n_big) {
-        sort_big_tiles(a, s, s_idx);
+        sort_big_tiles(a, s, s2, s_idx);
         return;
     }
     const int64_t t = (int64_t)(blockIdx.x - n_big) * (kBigThreads / 32) + (threadIdx.x >> 5);
