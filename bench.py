@@ -423,7 +423,7 @@ def run_extras(args):
         img = ras.outputs(0)[0].contiguous()
         tgt = (img + 0.05).contiguous()
         H_, W_ = img.shape[1], img.shape[2]
-        nb = (W_ + 31) // 32 * ((H_ + 7) // 8)
+        nb = (W_ + 31) // 32 * ((H_ + 39) // 40) * img.shape[0]
         ms_loss = _time_loop(lambda: train.image_loss(img, tgt), flush, args.extra_steps)
         # read image + target and write three partial maps (20 B per value); read the partials and
         # both images again and write the gradient (24 B per value); per CTA 8 B

@@ -22,9 +22,13 @@
 
 namespace vrs {
 
-constexpr int kLW = 32, kLH = 8, kLR = 5;                 // output tile, window radius
-constexpr int kLThreads = kLW * kLH;
-constexpr int kLPW = kLW + 2 * kLR, kLPH = kLH + 2 * kLR;  // padded tile
+constexpr int kLW = 32, kLH = 40, kLR = 5;                // output tile, window radius
+constexpr int kLThreads = 256;
+constexpr int kLPW = kLW + 2 * kLR, kLPH = kLH + 2 * kLR;  // padded tile (42 x 50)
+constexpr int kHSeg = 8;                                  // row-pass outputs per thread
+constexpr int kVSeg = kLH / (kLThreads / kLW);            // column-pass outputs per thread (5)
+static_assert((kLThreads / kLW) * kVSeg == kLH, "the column pass covers the tile");
+static_assert(kLPH * (kLW / kHSeg) <= kLThreads, "the row pass is one round");
 
 __constant__ float c_gauss[2 * kLR + 1];
 
@@ -37,73 +41,105 @@ struct LossArgs {
     float lambda, inv_n;
 };
 
-// Loads a padded tile of one channel (zero outside the image).
-__device__ __forceinline__ void load_tile(const float *src, int H, int W, int x0, int y0, float (*t)[kLPW])
+// The 11-tap row pass of one padded array, in place: the thread owning row r,
+// columns [c0, c0 + kHSeg) of the result reads its 18 inputs into registers
+// (a sliding window: each input loaded once), and after a barrier writes the
+// sums over the first kLW columns of the row.  Every thread of the CTA calls it.
+__device__ __forceinline__ void row_pass(float (*t)[kLPW], bool act, int r, int c0)
 {
-    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
-        const int r = i / kLPW, c = i - r * kLPW;
-        const int gy = y0 + r - kLR, gx = x0 + c - kLR;
-        t[r][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? __ldg(src + (size_t)gy * W + gx) : 0.f;
+    float out[kHSeg];
+    if (act) {
+        float w[kHSeg + 2 * kLR];
+#pragma unroll
+        for (int i = 0; i < kHSeg + 2 * kLR; ++i) w[i] = t[r][c0 + i];
+#pragma unroll
+        for (int j = 0; j < kHSeg; ++j) {
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kLR + 1; ++k) m = fmaf(c_gauss[k], w[j + k], m);
+            out[j] = m;
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < kHSeg; ++j) t[r][c0 + j] = out[j];
     }
 }
 
+// The 11-tap column pass of one row-summed array: kVSeg outputs of column tx
+// starting at output row ty * kVSeg, from 15 loads.
+__device__ __forceinline__ void col_pass(const float (*t)[kLPW], int tx, int ty, float (&out)[kVSeg])
+{
+    float w[kVSeg + 2 * kLR];
+#pragma unroll
+    for (int i = 0; i < kVSeg + 2 * kLR; ++i) w[i] = t[ty * kVSeg + i][tx];
+#pragma unroll
+    for (int j = 0; j < kVSeg; ++j) {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) m = fmaf(c_gauss[k], w[j + k], m);
+        out[j] = m;
+    }
+}
+
+// One CTA per 32 x 40 output tile and channel: the padded tile of x and y and
+// their products in shared memory (zero outside the image), the row passes in
+// place, then each thread's column of five outputs.
 __global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
 {
-    __shared__ float sx[kLPH][kLPW], sy[kLPH][kLPW];
-    __shared__ float hb[5][kLPH][kLW];
+    __shared__ float sm[5][kLPH][kLPW];       // x, y, x^2, y^2, x y; then their row sums
     __shared__ float2 red[kLThreads / 32];
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
+    const size_t base = (size_t)blockIdx.z * a.H * a.W;
+    float l1_sum = 0.f;
+    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
+        const int r = i / kLPW, col = i - r * kLPW;
+        const int gy = y0 + r - kLR, gx = x0 + col - kLR;
+        float u = 0.f, v = 0.f;
+        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
+            const size_t e = base + (size_t)gy * a.W + gx;
+            u = __ldg(a.x + e);
+            v = __ldg(a.y + e);
+            // |x - y| once per pixel: over the tile's own cells
+            if (r >= kLR && r < kLR + kLH && col >= kLR && col < kLR + kLW) l1_sum += fabsf(u - v);
+        }
+        sm[0][r][col] = u;
+        sm[1][r][col] = v;
+        sm[2][r][col] = u * u;
+        sm[3][r][col] = v * v;
+        sm[4][r][col] = u * v;
+    }
+    __syncthreads();
+    const int hr = threadIdx.x / (kLW / kHSeg), hc = (threadIdx.x % (kLW / kHSeg)) * kHSeg;
+#pragma unroll 1
+    for (int m = 0; m < 5; ++m) row_pass(sm[m], hr < kLPH, hr, hc);
+    __syncthreads();
     const int tx = threadIdx.x % kLW, ty = threadIdx.x / kLW;
-    const int px = x0 + tx, py = y0 + ty;
-    const bool in = px < a.W && py < a.H;
-    float s_sum = 0.f, l1_sum = 0.f;
-    for (int c = 0; c < a.C; ++c) {
-        const size_t base = (size_t)c * a.H * a.W;
-        __syncthreads();                                   // the previous channel's tiles are read
-        load_tile(a.x + base, a.H, a.W, x0, y0, sx);
-        load_tile(a.y + base, a.H, a.W, x0, y0, sy);
-        __syncthreads();
-        // horizontal pass over every padded row
-        for (int i = threadIdx.x; i < kLPH * kLW; i += kLThreads) {
-            const int r = i / kLW, col = i - r * kLW;
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+    float mx[kVSeg], my[kVSeg], ex2[kVSeg], ey2[kVSeg], exy[kVSeg];
+    col_pass(sm[0], tx, ty, mx);
+    col_pass(sm[1], tx, ty, my);
+    col_pass(sm[2], tx, ty, ex2);
+    col_pass(sm[3], tx, ty, ey2);
+    col_pass(sm[4], tx, ty, exy);
+    float s_sum = 0.f;
+    const int px = x0 + tx;
 #pragma unroll
-            for (int k = 0; k < 2 * kLR + 1; ++k) {
-                const float g = c_gauss[k], u = sx[r][col + k], v = sy[r][col + k];
-                m0 = fmaf(g, u, m0);
-                m1 = fmaf(g, v, m1);
-                m2 = fmaf(g, u * u, m2);
-                m3 = fmaf(g, v * v, m3);
-                m4 = fmaf(g, u * v, m4);
-            }
-            hb[0][r][col] = m0;
-            hb[1][r][col] = m1;
-            hb[2][r][col] = m2;
-            hb[3][r][col] = m3;
-            hb[4][r][col] = m4;
-        }
-        __syncthreads();
-        float mx = 0.f, my = 0.f, ex2 = 0.f, ey2 = 0.f, exy = 0.f;
-#pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float g = c_gauss[k];
-            mx = fmaf(g, hb[0][ty + k][tx], mx);
-            my = fmaf(g, hb[1][ty + k][tx], my);
-            ex2 = fmaf(g, hb[2][ty + k][tx], ex2);
-            ey2 = fmaf(g, hb[3][ty + k][tx], ey2);
-            exy = fmaf(g, hb[4][ty + k][tx], exy);
-        }
-        if (in) {
-            const float n1 = 2.f * mx * my + C1, n2 = 2.f * (exy - mx * my) + C2;
-            const float d1 = mx * mx + my * my + C1, d2 = (ex2 - mx * mx) + (ey2 - my * my) + C2;
-            const float S = (n1 * n2) / (d1 * d2);
+    for (int j = 0; j < kVSeg; ++j) {
+        const int py = y0 + ty * kVSeg + j;
+        if (px < a.W && py < a.H) {
+            const float n1 = 2.f * mx[j] * my[j] + C1, n2 = 2.f * (exy[j] - mx[j] * my[j]) + C2;
+            const float d1 = mx[j] * mx[j] + my[j] * my[j] + C1;
+            const float d2 = (ex2[j] - mx[j] * mx[j]) + (ey2[j] - my[j] * my[j]) + C2;
+            const float rn1 = __fdividef(1.f, n1), rn2 = __fdividef(1.f, n2);
+            const float rd1 = __fdividef(1.f, d1), rd2 = __fdividef(1.f, d2);
+            const float S = n1 * n2 * rd1 * rd2;
             const size_t e = base + (size_t)py * a.W + px;
-            a.smu[e] = S * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
-            a.sa[e] = -S / d2;
-            a.sb[e] = 2.f * S / n2;
+            a.smu[e] = S * (2.f * my[j] * rn1 - 2.f * my[j] * rn2 - 2.f * mx[j] * rd1 + 2.f * mx[j] * rd2);
+            a.sa[e] = -S * rd2;
+            a.sb[e] = 2.f * S * rn2;
             s_sum += S;
-            l1_sum += fabsf(sx[ty + kLR][tx + kLR] - sy[ty + kLR][tx + kLR]);
         }
     }
     const unsigned FULL = 0xffffffffu;
@@ -120,54 +156,51 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
             t.x += red[w].x;
             t.y += red[w].y;
         }
-        a.block_sums[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        a.block_sums[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
     }
 }
 
+// The same tiling over the three partial maps, then dL/dx per pixel.
 __global__ void __launch_bounds__(kLThreads) k_ssim_bwd(const LossArgs a)
 {
     __shared__ float sm[3][kLPH][kLPW];
-    __shared__ float hb[3][kLPH][kLW];
     const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
+    const size_t base = (size_t)blockIdx.z * a.H * a.W;
+    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
+        const int r = i / kLPW, col = i - r * kLPW;
+        const int gy = y0 + r - kLR, gx = x0 + col - kLR;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
+            const size_t e = base + (size_t)gy * a.W + gx;
+            m0 = __ldg(a.smu + e);
+            m1 = __ldg(a.sa + e);
+            m2 = __ldg(a.sb + e);
+        }
+        sm[0][r][col] = m0;
+        sm[1][r][col] = m1;
+        sm[2][r][col] = m2;
+    }
+    __syncthreads();
+    const int hr = threadIdx.x / (kLW / kHSeg), hc = (threadIdx.x % (kLW / kHSeg)) * kHSeg;
+#pragma unroll 1
+    for (int m = 0; m < 3; ++m) row_pass(sm[m], hr < kLPH, hr, hc);
+    __syncthreads();
     const int tx = threadIdx.x % kLW, ty = threadIdx.x / kLW;
-    const int px = x0 + tx, py = y0 + ty;
-    const bool in = px < a.W && py < a.H;
-    for (int c = 0; c < a.C; ++c) {
-        const size_t base = (size_t)c * a.H * a.W;
-        __syncthreads();
-        load_tile(a.smu + base, a.H, a.W, x0, y0, sm[0]);
-        load_tile(a.sa + base, a.H, a.W, x0, y0, sm[1]);
-        load_tile(a.sb + base, a.H, a.W, x0, y0, sm[2]);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kLPH * kLW; i += kLThreads) {
-            const int r = i / kLW, col = i - r * kLW;
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    float gm[kVSeg], ga[kVSeg], gb[kVSeg];
+    col_pass(sm[0], tx, ty, gm);
+    col_pass(sm[1], tx, ty, ga);
+    col_pass(sm[2], tx, ty, gb);
+    const int px = x0 + tx;
 #pragma unroll
-            for (int k = 0; k < 2 * kLR + 1; ++k) {
-                const float g = c_gauss[k];
-                m0 = fmaf(g, sm[0][r][col + k], m0);
-                m1 = fmaf(g, sm[1][r][col + k], m1);
-                m2 = fmaf(g, sm[2][r][col + k], m2);
-            }
-            hb[0][r][col] = m0;
-            hb[1][r][col] = m1;
-            hb[2][r][col] = m2;
+    for (int j = 0; j < kVSeg; ++j) {
+        const int py = y0 + ty * kVSeg + j;
+        if (px < a.W && py < a.H) {
+            const size_t e = base + (size_t)py * a.W + px;
+            const float xp = __ldg(a.x + e), yp = __ldg(a.y + e);
+            const float sgn = xp > yp ? 1.f : (xp < yp ? -1.f : 0.f);
+            const float dssim = (gm[j] + 2.f * xp * ga[j] + yp * gb[j]) * a.inv_n;
+            a.dx[e] = (1.f - a.lambda) * sgn * a.inv_n - a.lambda * dssim;
         }
-        __syncthreads();
-        if (!in) continue;
-        float gm = 0.f, ga = 0.f, gb = 0.f;
-#pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float g = c_gauss[k];
-            gm = fmaf(g, hb[0][ty + k][tx], gm);
-            ga = fmaf(g, hb[1][ty + k][tx], ga);
-            gb = fmaf(g, hb[2][ty + k][tx], gb);
-        }
-        const size_t e = base + (size_t)py * a.W + px;
-        const float xp = __ldg(a.x + e), yp = __ldg(a.y + e);
-        const float sgn = xp > yp ? 1.f : (xp < yp ? -1.f : 0.f);
-        const float dssim = (gm + 2.f * xp * ga + yp * gb) * a.inv_n;
-        a.dx[e] = (1.f - a.lambda) * sgn * a.inv_n - a.lambda * dssim;
     }
 }
 
@@ -230,7 +263,7 @@ vrs_status vrs_image_loss_scratch(int32_t C, int32_t H, int32_t W, int64_t *byte
 {
     if (C < 1 || H < 1 || W < 1 || !bytes) return VRS_ERR_INVALID;
     const int64_t n = (int64_t)C * H * W;
-    const int64_t blocks = (int64_t)((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH);
+    const int64_t blocks = (int64_t)((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH) * C;
     *bytes = sums_offset(n) + blocks * 8;
     return VRS_OK;
 }
@@ -270,10 +303,12 @@ vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, in
     a.W = W;
     a.lambda = lambda;
     a.inv_n = (float)(1.0 / (double)n);
-    const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH);
+    const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH, C);
+    if (grid.y > 65535u || grid.z > 65535u) return VRS_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_ssim_fwd<<<grid, kLThreads, 0, s>>>(a);
-    k_loss_reduce<<<1, 256, 0, s>>>(a.block_sums, (int)(grid.x * grid.y), lambda, 1.0 / (double)n, loss_out);
+    k_loss_reduce<<<1, 256, 0, s>>>(a.block_sums, (int)(grid.x * grid.y * grid.z), lambda, 1.0 / (double)n,
+                                    loss_out);
     if (dL_dimage) k_ssim_bwd<<<grid, kLThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
 }
