@@ -29,6 +29,7 @@ constexpr int kHSeg = 8;                                  // row-pass outputs pe
 constexpr int kVSeg = kLH / (kLThreads / kLW);            // column-pass outputs per thread (5)
 static_assert((kLThreads / kLW) * kVSeg == kLH, "the column pass covers the tile");
 static_assert(kLPH * (kLW / kHSeg) <= kLThreads, "the row pass is one round");
+constexpr int kLoadIters = (kLPW * kLPH + kLThreads - 1) / kLThreads;   // padded-tile loads per thread
 
 __constant__ float c_gauss[2 * kLR + 1];
 
@@ -94,22 +95,35 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
     const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
     const size_t base = (size_t)blockIdx.z * a.H * a.W;
     float l1_sum = 0.f;
-    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
-        const int r = i / kLPW, col = i - r * kLPW;
-        const int gy = y0 + r - kLR, gx = x0 + col - kLR;
-        float u = 0.f, v = 0.f;
-        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
-            const size_t e = base + (size_t)gy * a.W + gx;
-            u = __ldg(a.x + e);
-            v = __ldg(a.y + e);
-            // |x - y| once per pixel: over the tile's own cells
-            if (r >= kLR && r < kLR + kLH && col >= kLR && col < kLR + kLW) l1_sum += fabsf(u - v);
+    {
+        // every load of the thread first, then the stores (the loads stay in flight together)
+        float u[kLoadIters], v[kLoadIters];
+#pragma unroll
+        for (int it = 0; it < kLoadIters; ++it) {
+            const int i = threadIdx.x + it * kLThreads;
+            const int r = i / kLPW, col = i - r * kLPW;
+            const int gy = y0 + r - kLR, gx = x0 + col - kLR;
+            u[it] = v[it] = 0.f;
+            if (i < kLPW * kLPH && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
+                const size_t e = base + (size_t)gy * a.W + gx;
+                u[it] = __ldg(a.x + e);
+                v[it] = __ldg(a.y + e);
+            }
         }
-        sm[0][r][col] = u;
-        sm[1][r][col] = v;
-        sm[2][r][col] = u * u;
-        sm[3][r][col] = v * v;
-        sm[4][r][col] = u * v;
+#pragma unroll
+        for (int it = 0; it < kLoadIters; ++it) {
+            const int i = threadIdx.x + it * kLThreads;
+            if (i < kLPW * kLPH) {
+                const int r = i / kLPW, col = i - r * kLPW;
+                // |x - y| once per pixel: over the tile's own cells (zero outside the image)
+                if (r >= kLR && r < kLR + kLH && col >= kLR && col < kLR + kLW) l1_sum += fabsf(u[it] - v[it]);
+                sm[0][r][col] = u[it];
+                sm[1][r][col] = v[it];
+                sm[2][r][col] = u[it] * u[it];
+                sm[3][r][col] = v[it] * v[it];
+                sm[4][r][col] = u[it] * v[it];
+            }
+        }
     }
     __syncthreads();
     const int hr = threadIdx.x / (kLW / kHSeg), hc = (threadIdx.x % (kLW / kHSeg)) * kHSeg;
@@ -166,19 +180,31 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_bwd(const LossArgs a)
     __shared__ float sm[3][kLPH][kLPW];
     const int x0 = blockIdx.x * kLW, y0 = blockIdx.y * kLH;
     const size_t base = (size_t)blockIdx.z * a.H * a.W;
-    for (int i = threadIdx.x; i < kLPW * kLPH; i += kLThreads) {
-        const int r = i / kLPW, col = i - r * kLPW;
-        const int gy = y0 + r - kLR, gx = x0 + col - kLR;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
-            const size_t e = base + (size_t)gy * a.W + gx;
-            m0 = __ldg(a.smu + e);
-            m1 = __ldg(a.sa + e);
-            m2 = __ldg(a.sb + e);
+    {
+        float m0[kLoadIters], m1[kLoadIters], m2[kLoadIters];
+#pragma unroll
+        for (int it = 0; it < kLoadIters; ++it) {
+            const int i = threadIdx.x + it * kLThreads;
+            const int r = i / kLPW, col = i - r * kLPW;
+            const int gy = y0 + r - kLR, gx = x0 + col - kLR;
+            m0[it] = m1[it] = m2[it] = 0.f;
+            if (i < kLPW * kLPH && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
+                const size_t e = base + (size_t)gy * a.W + gx;
+                m0[it] = __ldg(a.smu + e);
+                m1[it] = __ldg(a.sa + e);
+                m2[it] = __ldg(a.sb + e);
+            }
         }
-        sm[0][r][col] = m0;
-        sm[1][r][col] = m1;
-        sm[2][r][col] = m2;
+#pragma unroll
+        for (int it = 0; it < kLoadIters; ++it) {
+            const int i = threadIdx.x + it * kLThreads;
+            if (i < kLPW * kLPH) {
+                const int r = i / kLPW, col = i - r * kLPW;
+                sm[0][r][col] = m0[it];
+                sm[1][r][col] = m1[it];
+                sm[2][r][col] = m2[it];
+            }
+        }
     }
     __syncthreads();
     const int hr = threadIdx.x / (kLW / kHSeg), hc = (threadIdx.x % (kLW / kHSeg)) * kHSeg;
@@ -204,29 +230,44 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_bwd(const LossArgs a)
     }
 }
 
-__global__ void k_loss_reduce(const float2 *block_sums, int n_blocks, float lambda, double inv_n, float *out)
+// One CTA of 1024 threads: each sums its share of the per-CTA sums in FP64, then
+// warp shuffles and one shared round; a fixed order, so the result is repeatable.
+constexpr int kReduceThreads = 1024;
+
+__global__ void __launch_bounds__(kReduceThreads) k_loss_reduce(const float2 *block_sums, int n_blocks, float lambda,
+                                                                double inv_n, float *out)
 {
-    __shared__ double rs[256], rl[256];
+    __shared__ double rs[kReduceThreads / 32], rl[kReduceThreads / 32];
     double s = 0.0, l = 0.0;
-    for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
-        s += (double)block_sums[i].x;
-        l += (double)block_sums[i].y;
+    for (int i = threadIdx.x; i < n_blocks; i += kReduceThreads) {
+        const float2 v = block_sums[i];
+        s += (double)v.x;
+        l += (double)v.y;
     }
-    rs[threadIdx.x] = s;
-    rl[threadIdx.x] = l;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rs[threadIdx.x >> 5] = s;
+        rl[threadIdx.x >> 5] = l;
+    }
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            rs[threadIdx.x] += rs[threadIdx.x + o];
-            rl[threadIdx.x] += rl[threadIdx.x + o];
+    if (threadIdx.x < 32) {
+        s = rs[threadIdx.x];
+        l = rl[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            l += __shfl_xor_sync(0xffffffffu, l, o);
         }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double ssim = rs[0] * inv_n, l1 = rl[0] * inv_n;
-        out[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
-        out[1] = (float)l1;
-        out[2] = (float)ssim;
+        if (threadIdx.x == 0) {
+            const double ssim = s * inv_n, l1 = l * inv_n;
+            out[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
+            out[1] = (float)l1;
+            out[2] = (float)ssim;
+        }
     }
 }
 
@@ -307,7 +348,7 @@ vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, in
     if (grid.y > 65535u || grid.z > 65535u) return VRS_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_ssim_fwd<<<grid, kLThreads, 0, s>>>(a);
-    k_loss_reduce<<<1, 256, 0, s>>>(a.block_sums, (int)(grid.x * grid.y * grid.z), lambda, 1.0 / (double)n,
+    k_loss_reduce<<<1, kReduceThreads, 0, s>>>(a.block_sums, (int)(grid.x * grid.y * grid.z), lambda, 1.0 / (double)n,
                                     loss_out);
     if (dL_dimage) k_ssim_bwd<<<grid, kLThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
