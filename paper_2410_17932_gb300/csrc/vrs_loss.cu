@@ -13,7 +13,8 @@
 //   k_ssim_bwd: the window sums of the three partials (the adjoint of a
 //     zero-padded symmetric window is the same window) give
 //     dSSIM/dx_p = (w * S_mu + 2 x_p w * S_A + y_p w * S_B) / N.
-//   k_loss_reduce: the per-CTA sums in FP64, in a fixed order.
+//   the last CTA of k_ssim_fwd to finish sums the per-CTA sums in FP64, in a
+//     fixed order.
 //
 // vrs_opacity_decay: Sec. 4 "Training" multiplies the opacities by 0.999 at
 // intervals and prunes below 0.005: the new logit of factor * sigmoid(logit),
@@ -38,8 +39,11 @@ struct LossArgs {
     float *smu, *sa, *sb;      // [C][H][W] partials of S
     float *dx;                 // nullable: dL/dimage
     float2 *block_sums;        // per CTA: (sum S, sum |x - y|)
+    uint32_t *ticket;          // CTAs of k_ssim_fwd done (zeroed before the launch)
+    float *loss_out;           // (L, L1, SSIM)
     int C, H, W;
     float lambda, inv_n;
+    double inv_n_d;
 };
 
 // The 11-tap row pass of one padded array, in place: the thread owning row r,
@@ -81,6 +85,42 @@ __device__ __forceinline__ void col_pass(const float (*t)[kLPW], int tx, int ty,
 #pragma unroll
         for (int k = 0; k < 2 * kLR + 1; ++k) m = fmaf(c_gauss[k], w[j + k], m);
         out[j] = m;
+    }
+}
+
+// The last CTA of k_ssim_fwd: the per-CTA sums in FP64, each thread over a fixed
+// stride of them, then a fixed tree, so the result does not depend on which CTA
+// ran last; the loss, L1 and SSIM.
+__device__ void loss_sums(const LossArgs &a, uint32_t n_blocks)
+{
+    __shared__ double rs[kLThreads / 32], rl[kLThreads / 32];
+    __threadfence();
+    double s = 0.0, l = 0.0;
+    for (uint32_t i = threadIdx.x; i < n_blocks; i += kLThreads) {
+        const float2 v = __ldcg(a.block_sums + i);       // L2: written by other CTAs
+        s += (double)v.x;
+        l += (double)v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rs[threadIdx.x >> 5] = s;
+        rl[threadIdx.x >> 5] = l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kLThreads / 32; ++w) {
+            s += rs[w];
+            l += rl[w];
+        }
+        const double inv_n = a.inv_n_d;
+        const double ssim = s * inv_n, l1 = l * inv_n;
+        a.loss_out[0] = (float)((1.0 - a.lambda) * l1 + a.lambda * (1.0 - ssim));
+        a.loss_out[1] = (float)l1;
+        a.loss_out[2] = (float)ssim;
     }
 }
 
@@ -164,6 +204,7 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
     }
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(s_sum, l1_sum);
     __syncthreads();
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
         float2 t = red[0];
         for (int w = 1; w < kLThreads / 32; ++w) {
@@ -171,7 +212,12 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_fwd(const LossArgs a)
             t.y += red[w].y;
         }
         a.block_sums[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+        __threadfence();                      // the sum is visible before the ticket counts it
+        const uint32_t n_ctas = gridDim.x * gridDim.y * gridDim.z;
+        s_last = atomicAdd(a.ticket, 1u) == n_ctas - 1;
     }
+    __syncthreads();
+    if (s_last) loss_sums(a, gridDim.x * gridDim.y * gridDim.z);
 }
 
 // The same tiling over the three partial maps, then dL/dx per pixel.
@@ -230,47 +276,6 @@ __global__ void __launch_bounds__(kLThreads) k_ssim_bwd(const LossArgs a)
     }
 }
 
-// One CTA of 1024 threads: each sums its share of the per-CTA sums in FP64, then
-// warp shuffles and one shared round; a fixed order, so the result is repeatable.
-constexpr int kReduceThreads = 1024;
-
-__global__ void __launch_bounds__(kReduceThreads) k_loss_reduce(const float2 *block_sums, int n_blocks, float lambda,
-                                                                double inv_n, float *out)
-{
-    __shared__ double rs[kReduceThreads / 32], rl[kReduceThreads / 32];
-    double s = 0.0, l = 0.0;
-    for (int i = threadIdx.x; i < n_blocks; i += kReduceThreads) {
-        const float2 v = block_sums[i];
-        s += (double)v.x;
-        l += (double)v.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        l += __shfl_xor_sync(0xffffffffu, l, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        rs[threadIdx.x >> 5] = s;
-        rl[threadIdx.x >> 5] = l;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        s = rs[threadIdx.x];
-        l = rl[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            l += __shfl_xor_sync(0xffffffffu, l, o);
-        }
-        if (threadIdx.x == 0) {
-            const double ssim = s * inv_n, l1 = l * inv_n;
-            out[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
-            out[1] = (float)l1;
-            out[2] = (float)ssim;
-        }
-    }
-}
-
 __global__ void k_opacity_decay(float *logits, int64_t n, float factor, float threshold, uint8_t *keep,
                                 uint32_t *n_kept)
 {
@@ -305,7 +310,7 @@ vrs_status vrs_image_loss_scratch(int32_t C, int32_t H, int32_t W, int64_t *byte
     if (C < 1 || H < 1 || W < 1 || !bytes) return VRS_ERR_INVALID;
     const int64_t n = (int64_t)C * H * W;
     const int64_t blocks = (int64_t)((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH) * C;
-    *bytes = sums_offset(n) + blocks * 8;
+    *bytes = sums_offset(n) + blocks * 8 + 16;    // the partial maps, the per-CTA sums, the ticket
     return VRS_OK;
 }
 
@@ -338,6 +343,10 @@ vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, in
     a.sa = a.smu + n;
     a.sb = a.sa + n;
     a.block_sums = reinterpret_cast<float2 *>(static_cast<char *>(scratch) + sums_offset(n));
+    const int64_t n_ctas = (int64_t)((W + kLW - 1) / kLW) * ((H + kLH - 1) / kLH) * C;
+    a.ticket = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + sums_offset(n) + n_ctas * 8);
+    a.loss_out = loss_out;
+    a.inv_n_d = 1.0 / (double)n;
     a.dx = dL_dimage;
     a.C = C;
     a.H = H;
@@ -347,9 +356,8 @@ vrs_status vrs_image_loss(const float *image, const float *target, int32_t C, in
     const dim3 grid((W + kLW - 1) / kLW, (H + kLH - 1) / kLH, C);
     if (grid.y > 65535u || grid.z > 65535u) return VRS_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(a.ticket, 0, sizeof(uint32_t), s) != cudaSuccess) return VRS_ERR_CUDA;
     k_ssim_fwd<<<grid, kLThreads, 0, s>>>(a);
-    k_loss_reduce<<<1, kReduceThreads, 0, s>>>(a.block_sums, (int)(grid.x * grid.y * grid.z), lambda, 1.0 / (double)n,
-                                    loss_out);
     if (dL_dimage) k_ssim_bwd<<<grid, kLThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;
 }
