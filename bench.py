@@ -544,7 +544,7 @@ def _batched_32(args, flush):
     by_sched = {}
     for ms, c in timings:
         if c["tile"] == best["tile"]:
-            k = "persistent" if c["persistent"] else "per_tile_grid"
+            k = ("per_tile_grid", "persistent_longest_first", "persistent_tile_order")[int(c["persistent"])]
             by_sched[k] = min(by_sched.get(k, 1e9), round(ms, 4))
     return {"batched_graph_ms": round(ms_batched, 4), "per_view_graph_ms": round(ms_per_view_graph, 4),
             "speedup_graph_vs_graph": round(ms_per_view_graph / ms_batched, 3),
@@ -662,7 +662,7 @@ def run_e2e(args, scenes, views, sts, ras, flush, world):
     latency = statistics.mean(tms)
     # pipelined frame loop: rasterizer r = k % 2 owns its scene buffers and outputs
     sts2 = [SceneTensors(*[torch.empty_like(x) for x in s_.tensors()], s_.sh_degree) for s_ in sts]
-    ras2 = Rasterizer(sts2, views, tile=int(ras.plan.tile), persistent=bool(ras.plan.persistent),
+    ras2 = Rasterizer(sts2, views, tile=int(ras.plan.tile), persistent=int(ras.plan.persistent),
                       resort=int(ras.plan.resort), half_out=bool(ras.plan.half_out))
     for s_, hs in zip(sts2, host):
         for dst, src_ in zip(s_.tensors(), hs):
@@ -724,7 +724,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="periphery_stereo_05m", choices=list(WORKLOADS))
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--persistent", type=int, default=-1, help="-1: autotuned choice")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="blend schedule: 0 one CTA per tile, 1 persistent longest first, 2 persistent in tile order")
     ap.add_argument("--sort", type=int, default=0, help="sort mode of the plan (0, 1 or 2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -753,7 +754,7 @@ def main():
         dist.init_process_group("nccl")
     scenes, views = load_workload(args.workload)
     sts = [SceneTensors.from_scene(s) for s in scenes]
-    persistent = bool(args.persistent) if args.persistent >= 0 else False
+    persistent = int(args.persistent) if args.persistent >= 0 else 0
     ras = Rasterizer(sts, views, tile=args.tile, persistent=persistent, sort=args.sort)
     ras.forward()                       # sizes the instance list
     code, flags, inst = ras.last_status
@@ -877,9 +878,9 @@ def main():
     if p.sort_mode != 1:
         # scan (+ block sums beyond 64 Ki tiles), scatter, tile sort
         sort_launches = 3 + (1 if (int(p.n_tiles) + 1023) // 1024 > 64 else 0)
-        launches_per_step = 2 * len(scenes) + sort_launches + (3 if p.persistent else 1)
+        launches_per_step = 2 * len(scenes) + sort_launches + (3 if p.persistent == 1 else 1)
     else:
-        launches_per_step = 2 * len(scenes) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent else 1)
+        launches_per_step = 2 * len(scenes) + 3 * int(p.sort_passes) + 1 + (3 if p.persistent == 1 else 1)
     if rank == 0:
         line = {
             "metric": METRIC,

@@ -116,8 +116,10 @@ typedef struct {
 
 typedef struct {
     int32_t tile;          /* tile edge in pixels: 8, 16 or 32 (0 = 16) */
-    int32_t persistent;    /* 1 = blend every tile of every view in one persistent
-                              launch, heaviest tiles first; 0 = one CTA per tile */
+    int32_t persistent;    /* 0 = one CTA per tile; 1 = blend every tile of every view in
+                              one persistent launch (a resident wave of CTAs pulling tiles),
+                              heaviest tiles first; 2 = the same launch, tiles in tile order
+                              (view by view, row by row); any value gives the same images */
     int32_t backward;      /* 1 = reserve the workspace that vrs_render_bwd needs */
     int32_t sort;          /* 0 = bucket by tile, then sort each tile's bucket (default);
                               1 = one global LSD radix sort of all keys;

@@ -2,16 +2,18 @@
 
 The batched path renders every view of every scene in one launch sequence:
 one preprocess launch per scene, one sort and one blend launch for the whole
-batch.  The persistent blend pulls tiles in longest-first order, so views of
-uneven size share the GPU without tail effects.  The sequence is allocation
+batch.  The persistent blends keep one resident wave of CTAs pulling tiles, in
+longest-first order (views of uneven size share the GPU without tail effects)
+or in tile order (neighbouring tiles' records stay in L2, and no CTA waits to be
+launched).  The sequence is allocation
 and synchronisation free, so it can be captured once in a CUDA graph and
 replayed every frame.
 
 The tuner times candidate plans on the caller's own batch and caches the
 fastest under a key of (GPU name, view sizes, scene sizes):
-  - blend schedule: one CTA per tile, or the persistent longest-first grid,
-    whose CTAs claim 1 or 4 tiles of the work order per atomic (the
-    batch-per-block knob);
+  - blend schedule: one CTA per tile, or a persistent grid in longest-first
+    or in tile order, whose CTAs claim 1 or 4 tiles of the work order per
+    atomic (the batch-per-block knob);
   - sort: tile buckets, or the global LSD radix sort with the minimal key
     width (tile-id bits + 32) or the full 64 bits;
   - tile edge 8 / 16 / 32 only when ``allow_tile_change`` is set, because the
@@ -37,7 +39,7 @@ CACHE_PATH = os.environ.get("VRS_AUTOTUNE_CACHE",
 
 def _key(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: bool) -> str:
     dev = torch.cuda.get_device_name()
-    sig = json.dumps(["v2", dev, [(v.width, v.height, v.scene) for v in views],
+    sig = json.dumps(["v3", dev, [(v.width, v.height, v.scene) for v in views],
                       [(s.n, s.sh_degree) for s in scenes], allow_tile_change])
     return hashlib.sha1(sig.encode()).hexdigest()
 
@@ -81,7 +83,7 @@ def time_ms(fn, iters: int = 20, warmup: int = 3) -> float:
 def candidates(allow_tile_change: bool, tile: int = 16) -> List[Dict]:
     tiles = (8, 16, 32) if allow_tile_change else (tile,)
     out = []
-    for t, p, s in itertools.product(tiles, (0, 1), (0, 1)):
+    for t, p, s in itertools.product(tiles, (0, 1, 2), (0, 1)):
         for pull in ((1, 4) if p else (1,)):
             for kb in ((0, 64) if s == 1 and pull == 1 else (0,)):
                 out.append(dict(tile=t, persistent=p, sort=s, tiles_per_pull=pull, key_bits=kb))

@@ -165,13 +165,14 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     if (o.resort && (o.backward || (tile == 32 && o.resort > 8))) return VRS_ERR_INVALID;
     if (o.half_out && o.backward) return VRS_ERR_INVALID;
     if (o.tiles_per_pull < 0 || o.tiles_per_pull > 64) return VRS_ERR_INVALID;
+    if (o.persistent < 0 || o.persistent > 2) return VRS_ERR_INVALID;
     if (o.key_bits < 0 || o.key_bits > 64) return VRS_ERR_INVALID;
     vrs_plan P;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
     P.n_scenes = n_scenes;
     P.tile = tile;
-    P.persistent = o.persistent ? 1 : 0;
+    P.persistent = o.persistent;
     P.backward = o.backward ? 1 : 0;
     P.sort_mode = o.sort;
     P.count_pairs = o.count_pairs ? 1 : 0;

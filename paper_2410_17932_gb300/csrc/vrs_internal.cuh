@@ -514,7 +514,8 @@ struct BlendCfg {
     static constexpr int WARPS = THREADS / 32;
     static constexpr int WGX = TS / 8;       // warps per tile row
     static constexpr int BATCH = THREADS;
-    static constexpr int MIN_BLOCKS = (1024 / THREADS) * 9 / 8;   // forward blend: 36 warps per SM, <= 56 registers
+    // forward blend: 36 warps per SM (<= 56 registers), at most 32 CTAs
+    static constexpr int MIN_BLOCKS = (1024 / THREADS) * 9 / 8 < 32 ? (1024 / THREADS) * 9 / 8 : 32;
 };
 
 

@@ -27,7 +27,7 @@ struct FwdArgs {
     float *depth;
     float *Tf;
     uint32_t *ncontrib;
-    const uint32_t *order;      // persistent: tile work order (heaviest first)
+    const uint32_t *order;      // persistent: tile work order (heaviest first), or null: tile order
     int64_t n_tiles;
     int64_t n_records;
     unsigned long long cap;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                 }
                 const uint32_t k = s_k + ((uint32_t)a.tiles_per_pull - s_left);
                 --s_left;
-                s_tile = (int64_t)k < a.n_tiles ? (int64_t)a.order[k] : -1;
+                s_tile = (int64_t)k < a.n_tiles ? (a.order ? (int64_t)a.order[k] : (int64_t)k) : -1;
             }
             __syncthreads();
             t = s_tile;
@@ -363,6 +363,34 @@ static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid
     return cudaGetLastError();
 }
 
+// CTAs of the persistent instantiation that fit on one SM at once.
+template <int TS>
+static int resident_ctas_ts(bool count, bool last, bool half)
+{
+    int n = 0;
+    cudaError_t e;
+    constexpr int T = BlendCfg<TS>::THREADS;
+    if (half) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fwd<TS, false, false, true, true>, T, 0);
+    else if (count && last) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fwd<TS, true, true, true>, T, 0);
+    else if (count) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fwd<TS, true, false, true>, T, 0);
+    else if (last) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fwd<TS, false, true, true>, T, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fwd<TS, false, false, true>, T, 0);
+    if (e != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+static int resident_ctas(int tile, bool count, bool last, bool half)
+{
+    switch (tile) {
+        case 8: return resident_ctas_ts<8>(count, last, half);
+        case 32: return resident_ctas_ts<32>(count, last, half);
+        default: return resident_ctas_ts<16>(count, last, half);
+    }
+}
+
 cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
                               float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
@@ -396,16 +424,20 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
     int grid = (int)n_tiles;
     cudaError_t e;
     if (persistent) {
-        // order_tmp: [kBuckets] histogram + [kBuckets] cursors
-        e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kBuckets, s);
-        if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(&st->work[0], 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        const int g = n_sms * 4;
-        k_order_hist<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, st);
-        k_order_scatter<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, order_tmp + kBuckets, order, st);
+        if (persistent == 1) {
+            // heaviest tiles first; order_tmp: [kBuckets] histogram + [kBuckets] cursors
+            e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kBuckets, s);
+            if (e != cudaSuccess) return e;
+            const int g = n_sms * 4;
+            k_order_hist<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, st);
+            k_order_scatter<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, order_tmp + kBuckets, order, st);
+        } else {
+            a.order = nullptr;           // tile order: neighbouring tiles run together
+        }
         // one resident wave of CTAs pulling tiles
-        const int per_sm = vt.tile == 8 ? 24 : (vt.tile == 16 ? 8 : 2);
+        const int per_sm = resident_ctas(vt.tile, count != 0, ncontrib != nullptr, half_out != 0);
         const int64_t ctas = (int64_t)n_sms * per_sm;
         grid = (int)(ctas < n_tiles ? ctas : n_tiles);
     }

@@ -110,14 +110,14 @@ class Rasterizer:
     """A planned batch of views over one or more scenes, with its workspace and outputs."""
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, tile: int = 16,
-                 persistent: bool = False, backward: bool = False, max_instances: int = 0,
+                 persistent: int = 0, backward: bool = False, max_instances: int = 0,
                  sort: int = 0, resort: int = 0, half_out: bool = False, key_bits: int = 0,
                  tiles_per_pull: int = 1, device="cuda"):
         self.scenes = list(scenes)
         self.views = list(views)
         self.device = torch.device(device)
         self.tile = tile
-        self.persistent = bool(persistent)
+        self.persistent = int(persistent)       # 0 per tile, 1 heaviest first, 2 tile order
         self.backward = bool(backward)
         self.sort = int(sort)
         self.resort = int(resort)    # 0: list order; 4/8/16: per-pixel order through a window of that size

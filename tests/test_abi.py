@@ -116,6 +116,7 @@ def test_plan_sizes_and_layout_on_host(lib):
     dict(views=[(0, 10, 0)]), dict(views=[(10, 10, 1)]), dict(views=[(10, 20000, 0)]),
     dict(views=[(10, 10, 0)], tile=12), dict(views=[(10, 10, 0)], scenes=((10, 4),)),
     dict(views=[(10, 10, 0)], scenes=((-1, 0),)), dict(views=[(10, 10, 0)], max_instances=-5),
+    dict(views=[(10, 10, 0)], persistent=3), dict(views=[(10, 10, 0)], persistent=-1),
 ])
 def test_plan_rejects_invalid_arguments(lib, bad):
     L = lib

@@ -64,7 +64,7 @@ def test_autotune_choice_keeps_images(tmp_path, monkeypatch):
     views = views[:8]
     sts = [SceneTensors.from_scene(s) for s in scenes]
     best = autotune.tune(sts, views, iters=3)
-    assert best["tile"] == 16 and best["persistent"] in (0, 1) and best["sort"] in (0, 1)
+    assert best["tile"] == 16 and best["persistent"] in (0, 1, 2) and best["sort"] in (0, 1)
     assert best["tiles_per_pull"] in (1, 4) and best["key_bits"] in (0, 64)
     assert autotune.tune(sts, views) == best          # served from the cache
     a = Rasterizer(sts, views)
@@ -114,7 +114,8 @@ def test_schedule_and_key_width_knobs_keep_images():
     scenes, views = _multiview(0.01)
     ref, sts = make_rasterizer(scenes, views)
     ref.forward()
-    for kw in (dict(persistent=True, tiles_per_pull=4), dict(persistent=True, tiles_per_pull=3),
+    for kw in (dict(persistent=1, tiles_per_pull=4), dict(persistent=1, tiles_per_pull=3),
+               dict(persistent=2), dict(persistent=2, tiles_per_pull=4),
                dict(sort=1, key_bits=64), dict(sort=1, key_bits=int(ref.plan.key_bits) + 3)):
         from paper_2410_17932_gb300.render import Rasterizer
         r = Rasterizer(sts, views, **kw)

@@ -110,11 +110,12 @@ def test_one_tile_wide_view(tile):
     compare_images((rgb, depth, T), orc, f"narrow{tile}")
 
 
-def test_persistent_equals_per_tile():
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_persistent_equals_per_tile(persistent):
     torch = torch_cuda()
     scs, cams = I.plain_200()
     a = _run(scs, cams)
-    b = _run(scs, cams, persistent=True)
+    b = _run(scs, cams, persistent=persistent)
     for x, y in zip((a.rgb, a.depth, a.T), (b.rgb, b.depth, b.T)):
         assert torch.equal(x, y)
 
@@ -213,9 +214,11 @@ def test_invalid_arguments_rejected_on_host():
         == L.VRS_ERR_INVALID
 
 
-@pytest.mark.parametrize("n", [300, 3000, 20000])
+@pytest.mark.parametrize("n", [300, 700, 1100, 3000, 20000])
 def test_bucketed_sort_crowded_tiles(n):
-    """n splats stacked on four tiles: the warp, shared-memory and merge paths of the bucketed sort."""
+    """n splats stacked on four tiles: the warp path and the CTA path of the bucketed sort (runs
+    of 128 merged in shared memory for chunks of 512 and 1024, a last chunk of under 256 at
+    n = 1100, chunks merged in global memory beyond 1024)."""
     torch = torch_cuda()
     sc = I.uniform_box_scene(n, 90 + n, xy=(-0.01, 0.01), z=(2.0, 6.0), log_scale=(-6.0, 0.2))
     cam = I.identity_camera(64, 64, 200.0)

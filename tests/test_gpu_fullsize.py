@@ -103,10 +103,11 @@ def test_periphery_stereo_05m_persistent_identical():
     torch = torch_cuda()
     scenes, views = I.periphery_stereo_05m(n=200_000)
     a, _ = make_rasterizer(scenes, views)
-    b, _ = make_rasterizer(scenes, views, persistent=True)
     a.forward()
-    b.forward()
-    assert torch.equal(a.rgb, b.rgb) and torch.equal(a.depth, b.depth) and torch.equal(a.T, b.T)
+    for persistent in (1, 2):
+        b, _ = make_rasterizer(scenes, views, persistent=persistent)
+        b.forward()
+        assert torch.equal(a.rgb, b.rgb) and torch.equal(a.depth, b.depth) and torch.equal(a.T, b.T)
 
 
 @pytest.mark.slow
