@@ -110,12 +110,12 @@ def test_one_tile_wide_view(tile):
     compare_images((rgb, depth, T), orc, f"narrow{tile}")
 
 
-@pytest.mark.parametrize("persistent", [1, 2])
-def test_persistent_equals_per_tile(persistent):
+@pytest.mark.parametrize("persistent,tile", [(1, 16), (2, 16), (1, 8), (2, 8), (2, 32)])
+def test_persistent_equals_per_tile(persistent, tile):
     torch = torch_cuda()
     scs, cams = I.plain_200()
-    a = _run(scs, cams)
-    b = _run(scs, cams, persistent=persistent)
+    a = _run(scs, cams, tile=tile)
+    b = _run(scs, cams, persistent=persistent, tile=tile)
     for x, y in zip((a.rgb, a.depth, a.T), (b.rgb, b.depth, b.T)):
         assert torch.equal(x, y)
 
