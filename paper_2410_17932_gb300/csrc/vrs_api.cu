@@ -38,7 +38,7 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
-                                   uint32_t *list, int n_sms, cudaStream_t s);
+                                   uint32_t *list, const uint4 *pairs, int scene, int n_sms, cudaStream_t s);
 }  // namespace vrs
 
 using namespace vrs;
@@ -393,13 +393,22 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
                           at<uint32_t>(workspace, plan->off_ncontrib), T_final, dL_drgb, dL_ddepth,
                           dL_dT, g2, plan->n_tiles, plan->n_records, (unsigned long long)plan->max_instances, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
+    // the touched-Gaussian list goes to the record-index buffer the sort left unused (when
+    // it holds a record index per record), so that the forward's pair list stays intact and
+    // one-view scenes can list their touched Gaussians from it; else to the pair-list area
+    const bool list_in_vals = plan->max_instances >= plan->n_records;
+    uint32_t *list = list_in_vals ? at<uint32_t>(workspace, plan->off_vals[1 - plan->sorted_buf])
+                                  : at<uint32_t>(workspace, plan->off_pairs);
+    int64_t pair_base = 0;
     for (int sc = 0; sc < plan->n_scenes; ++sc) {
         int8_t vlist[VRS_MAX_VIEWS];
         const int nv = views_of_scene(plan, sc, vlist);
         e = launch_backward_params(vt, dev_scene(scenes[sc]), dev_scene(grads[sc]), vlist, nv, g2,
-                                   at<DevStatus>(workspace, plan->off_status),
-                                   at<uint32_t>(workspace, plan->off_pairs), plan->n_sms, s);
+                                   at<DevStatus>(workspace, plan->off_status), list,
+                                   list_in_vals ? at<uint4>(workspace, plan->off_pairs) + 2 * pair_base : nullptr,
+                                   sc, plan->n_sms, s);
         if (e != cudaSuccess) return VRS_ERR_CUDA;
+        pair_base += (int64_t)plan->scene_n[sc] * nv;
     }
     return VRS_OK;
 }

@@ -334,6 +334,9 @@ struct ParamArgs {
     const DevStatus *st;
     uint32_t *list;            // Gaussians with a nonzero record gradient (scratch)
     uint32_t *list_count;
+    const uint4 *pairs;        // the scene's visible-pair list of the forward (2 uint4 per pair)
+    int32_t scene;             // index of the scene in the plan
+    unsigned long long pair_cap;
 };
 
 // The 3K values of an SH row in order, f(index, value), as 16-byte loads where
@@ -595,6 +598,50 @@ __global__ void __launch_bounds__(kTouchedThreads) k_touched(const __grid_consta
     if (t) p.list[s_base[wp] + __popc(b & lanemask_lt())] = (uint32_t)g;
 }
 
+// One view: every Gaussian with a nonzero record gradient is a visible pair of the
+// forward's pair list, once, so the list is walked instead of every record (6 % of a
+// training view's pairs are visible).  One atomic per CTA and round.
+__global__ void __launch_bounds__(kTouchedThreads) k_touched_pairs(const __grid_constant__ ViewTable vt,
+                                                                   const __grid_constant__ ParamArgs p)
+{
+    __shared__ uint32_t s_cnt[kTouchedWarps], s_base[kTouchedWarps];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (p.st->flags & ST_CAPACITY) return;     // uniform over the grid
+    const unsigned long long n_raw = p.st->scene_pairs[p.scene];
+    const unsigned long long n = n_raw < p.pair_cap ? n_raw : p.pair_cap;
+    const int64_t rec_base = vt.v[p.views[0]].rec_base;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kTouchedThreads;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * kTouchedThreads; i0 < n; i0 += stride) {
+        const unsigned long long i = i0 + threadIdx.x;
+        bool t = false;
+        uint32_t g = 0u;
+        if (i < n) {
+            g = __ldg(p.pairs + 2 * i).x;
+            const float2 *G2 = reinterpret_cast<const float2 *>(p.grad2d + (size_t)(rec_base + g) * kGrad2D);
+#pragma unroll
+            for (int k = 0; k < kGrad2D / 2; ++k) {
+                const float2 v = G2[k];
+                t |= v.x != 0.f || v.y != 0.f;
+            }
+        }
+        const uint32_t b = __ballot_sync(0xffffffffu, t);
+        if (lane == 0) s_cnt[wp] = (uint32_t)__popc(b);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t sum = 0;
+            for (int q = 0; q < kTouchedWarps; ++q) sum += s_cnt[q];
+            uint32_t base = sum ? atomicAdd(p.list_count, sum) : 0u;
+            for (int q = 0; q < kTouchedWarps; ++q) {
+                s_base[q] = base;
+                base += s_cnt[q];
+            }
+        }
+        __syncthreads();
+        if (t) p.list[s_base[wp] + __popc(b & lanemask_lt())] = g;
+        __syncthreads();                      // s_cnt and s_base are rewritten next round
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__ ViewTable vt,
                                                          const __grid_constant__ ParamArgs p)
@@ -620,7 +667,7 @@ static cudaError_t launch_params_k(const ViewTable &vt, const ParamArgs &p, int 
 
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
-                                   uint32_t *list, int n_sms, cudaStream_t s)
+                                   uint32_t *list, const uint4 *pairs, int scene, int n_sms, cudaStream_t s)
 {
     if (S.n <= 0 || n_views <= 0) return cudaSuccess;
     ParamArgs p;
@@ -632,12 +679,18 @@ cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const
     p.st = st;
     p.list = list;
     p.list_count = &st->work[4];
+    p.pairs = pairs;
+    p.scene = scene;
+    p.pair_cap = (unsigned long long)S.n * (unsigned long long)n_views;
     cudaError_t e = cudaMemsetAsync(&st->work[4], 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_touched<<<grid_for(S.n, kTouchedThreads), kTouchedThreads, 0, s>>>(vt, p);
+    if (n_sms <= 0) n_sms = 152;
+    // one view: the forward's pair list holds each touched Gaussian once; several (or no
+    // pair list): a Gaussian has a pair per view, so every record of the scene is read
+    if (n_views == 1 && pairs) k_touched_pairs<<<n_sms * 8, kTouchedThreads, 0, s>>>(vt, p);
+    else k_touched<<<grid_for(S.n, kTouchedThreads), kTouchedThreads, 0, s>>>(vt, p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (n_sms <= 0) n_sms = 152;
     switch (S.K) {
         case 1: return launch_params_k<1>(vt, p, n_sms, s);
         case 4: return launch_params_k<4>(vt, p, n_sms, s);
