@@ -563,6 +563,21 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ 
     if (nonfinite_sh) atomicOr(&p.st->flags, ST_NONFINITE);
 }
 
+template <int K, bool HALF>
+static cudaError_t launch_pairs(const ViewTable &vt, const PreParams &p, int64_t want, int n_sms, cudaStream_t s)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<K, HALF>, kPairThreads, 0) != cudaSuccess ||
+        per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 4;
+    }
+    const int64_t wave = (int64_t)(n_sms > 0 ? n_sms : 152) * per_sm;
+    const unsigned grid = (unsigned)(want < wave ? want : wave);
+    k_pairs<K, HALF><<<grid > 0 ? grid : 1, kPairThreads, 0, s>>>(vt, p);
+    return cudaGetLastError();
+}
+
 // Host launcher: two launches per scene (the SH degree is a template argument
 // of the pair kernel so that a row's coefficients stay in registers).
 cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene, const int8_t *views,
@@ -596,23 +611,21 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     else k_decide_listed<2><<<grid_for(S.n, 2 * kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // one pair per thread up to the list's capacity; CTAs past the device-side
-    // count exit at once (the loop covers any remainder)
-    (void)n_sms;
+    // one pair per thread, CTAs looping over the list: the grid is sized for the list's
+    // capacity but capped at one resident wave, since the list holds only the visible pairs
+    // (a quarter of an eye's) and launching thousands of CTAs that exit at once costs time
     const int64_t want = grid_for((int64_t)S.n * n_views, kPairThreads);
-    const unsigned grid = (unsigned)(want < (int64_t)1 << 30 ? want : (int64_t)1 << 30);
     switch (S.K + (S.sh_half ? 100 : 0)) {
-        case 1: k_pairs<1, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 4: k_pairs<4, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 9: k_pairs<9, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 16: k_pairs<16, false><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 101: k_pairs<1, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 104: k_pairs<4, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 109: k_pairs<9, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
-        case 116: k_pairs<16, true><<<grid, kPairThreads, 0, stream>>>(vt, p); break;
+        case 1: return launch_pairs<1, false>(vt, p, want, n_sms, stream);
+        case 4: return launch_pairs<4, false>(vt, p, want, n_sms, stream);
+        case 9: return launch_pairs<9, false>(vt, p, want, n_sms, stream);
+        case 16: return launch_pairs<16, false>(vt, p, want, n_sms, stream);
+        case 101: return launch_pairs<1, true>(vt, p, want, n_sms, stream);
+        case 104: return launch_pairs<4, true>(vt, p, want, n_sms, stream);
+        case 109: return launch_pairs<9, true>(vt, p, want, n_sms, stream);
+        case 116: return launch_pairs<16, true>(vt, p, want, n_sms, stream);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace vrs
