@@ -828,7 +828,11 @@ def main():
         achieved = ops / (stage["render_fwd"] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": f"k_render_fwd<{int(p.tile)}>", "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4),
-                "traffic": args.blend_traffic if args.blend_traffic is not None else captured_blend_traffic(),
+                # the captured figure is the periphery stereo frame's (tile 16, per-tile grid)
+                "traffic": (args.blend_traffic if args.blend_traffic is not None else
+                            captured_blend_traffic() if (args.workload == "periphery_stereo_05m"
+                                                         and int(p.tile) == 16 and not p.persistent)
+                            else None),
                 "peak_source": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
                 "units": f"{pair_blends} blended Gaussian-pixel pairs x {ALU_OPS_PER_BLEND} ops",
                 "context": {"definitional_evaluations": pair_evals,
