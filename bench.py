@@ -391,8 +391,17 @@ def run_extras(args):
 
         for _ in range(3):
             step()
-        out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(step, flush, args.extra_steps), 4)
-        out["training_view_1m_fwd_ms"] = round(_time_loop(ras.forward_async, flush, args.extra_steps), 4)
+        # the step as a training loop runs it: one CUDA-graph replay (forward and backward
+        # launches without host gaps); the same launches issued one by one beside it
+        from paper_2410_17932_gb300 import autotune
+        runner = autotune.CallableGraph(step)
+        for _ in range(3):
+            runner.replay()
+        out["training_view_1m_fwd_bwd_ms_per_view"] = round(_time_loop(runner.replay, flush, args.extra_steps), 4)
+        out["training_view_1m_fwd_bwd_plain_launches_ms"] = round(_time_loop(step, flush, args.extra_steps), 4)
+        fwd_runner = autotune.GraphRunner(ras)
+        out["training_view_1m_fwd_ms"] = round(_time_loop(fwd_runner.replay, flush, args.extra_steps), 4)
+        del runner, fwd_runner
         # the step's stages in order, then the backward's roofline: its reverse blend dominates
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.extra_steps)]
         for e in evs:

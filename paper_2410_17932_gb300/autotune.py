@@ -44,6 +44,29 @@ def _key(scenes: Sequence[SceneTensors], views: Sequence, allow_tile_change: boo
     return hashlib.sha1(sig.encode()).hexdigest()
 
 
+class CallableGraph:
+    """Captures a launch sequence (a callable that only enqueues work on the current stream,
+    allocates nothing and does not synchronise, e.g. a training step's forward_async and
+    backward_params) in a CUDA graph and replays it."""
+
+    def __init__(self, fn, warmup: int = 2):
+        self.fn = fn
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            fn()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+
+
 class GraphRunner:
     """Captures Rasterizer.forward_async in a CUDA graph and replays it."""
 
