@@ -9,7 +9,8 @@
 //                                  composite (depth bits << 32 | record index)
 //   k_tile_sort                    one launch for both sizes: one warp per tile
 //                                  of <= 256 instances (a bitonic network in
-//                                  registers and shuffles), and larger tiles one
+//                                  registers and shuffles, on 32-bit keys of the
+//                                  depth and the bucket slot), and larger tiles one
 //                                  CTA each (runs of 128 sorted by its warps in
 //                                  registers and merged in shared memory up to
 //                                  1024, beyond that sorted 1024-runs merged in
@@ -149,29 +150,30 @@ __global__ void __launch_bounds__(256) k_tile_scatter(const TileSortArgs a)
     }
 }
 
-// Bitonic sort of 32*E composites held by one warp, element e = i*32 + lane in v[i],
+// Bitonic sort of 32*E keys held by one warp, element e = i*32 + lane in v[i],
 // in the form whose comparators all put the minimum at the lower element: each
 // merge of width k starts by comparing e with its mirror e ^ (k - 1), then
 // half-cleans with partners e ^ j.  No comparator needs a direction bit.
 // The per-element bodies are unrolled; the stage loops are not, which keeps the
-// four instantiations small enough for the instruction cache.
-template <int E>
-__device__ __forceinline__ void shfl_stage(unsigned long long (&v)[E], int mask, int lowbit, int lane)
+// instantiations small enough for the instruction cache.  T: the 64-bit
+// composites, or 32-bit keys.
+template <int E, typename T>
+__device__ __forceinline__ void shfl_stage(T (&v)[E], int mask, int lowbit, int lane)
 {
     const bool lower = (lane & lowbit) == 0;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[i], mask);
+        const T o = __shfl_xor_sync(0xffffffffu, v[i], mask);
         v[i] = (lower == (v[i] < o)) ? v[i] : o;
     }
 }
 
 // Mirror step of a merge wider than a warp: partner register i ^ M, lane ^ 31.
-template <int E, int M>
-__device__ __forceinline__ void flip_regs(unsigned long long (&v)[E])
+template <int E, int M, typename T>
+__device__ __forceinline__ void flip_regs(T (&v)[E])
 {
     if constexpr (M < E) {
-        unsigned long long o[E];
+        T o[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) o[i] = __shfl_xor_sync(0xffffffffu, v[i ^ M], 31);
 #pragma unroll
@@ -180,22 +182,22 @@ __device__ __forceinline__ void flip_regs(unsigned long long (&v)[E])
 }
 
 // Half-cleaner step across registers: partners i and i ^ JI in the same lane.
-template <int E, int JI>
-__device__ __forceinline__ void reg_half(unsigned long long (&v)[E])
+template <int E, int JI, typename T>
+__device__ __forceinline__ void reg_half(T (&v)[E])
 {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int p = i ^ JI;
         if (p > i && p < E) {
-            const unsigned long long x = v[i], y = v[p];
+            const T x = v[i], y = v[p];
             v[i] = x < y ? x : y;
             v[p] = x < y ? y : x;
         }
     }
 }
 
-template <int E>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lane)
+template <int E, typename T>
+__device__ __forceinline__ void warp_bitonic(T (&v)[E], int lane)
 {
     constexpr int P = 32 * E;
 #pragma unroll 1
@@ -217,24 +219,77 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lan
     }
 }
 
+// One warp sorts a tile of n <= 32 E instances.  The network runs on 32-bit keys: the
+// depth bits' offset from the tile's least (depth is non-negative, so its bits order as
+// its value), shifted right just enough to fit 23 bits, above the instance's 8-bit
+// slot in the bucket; the sorted slots then gather the composites.  Keys order the
+// depths exactly except where two shifted offsets are equal (equal depths, or depths
+// within 2^shift units in the last place): the warp finds any such neighbours after
+// the sort and then sorts the full 64-bit composites instead, which also order equal
+// depths by record index.
 template <int E>
 __device__ __forceinline__ void warp_sort_tile(const TileSortArgs &a, uint32_t t, uint32_t start, uint32_t n,
                                                int lane)
 {
-    unsigned long long v[E];
+    static_assert(32 * E <= 256, "8-bit slots");
+    const unsigned FULL = 0xffffffffu;
+    uint32_t d[E];
+    uint32_t dmin = 0xffffffffu, dmax = 0u;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const uint32_t e = i * 32 + lane;
-        v[i] = e < n ? a.bucket[start + e] : ~0ull;
+        d[i] = e < n ? (uint32_t)(a.bucket[start + e] >> 32) : 0xffffffffu;
+        if (e < n) {
+            dmin = min(dmin, d[i]);
+            dmax = max(dmax, d[i]);
+        }
     }
-    warp_bitonic<E>(v, lane);
+    dmin = __reduce_min_sync(FULL, dmin);
+    dmax = __reduce_max_sync(FULL, dmax);
+    const uint32_t range = dmax - dmin;
+    const int shift = max(0, (32 - __clz(range)) - 23);
+    uint32_t k[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const uint32_t e = i * 32 + lane;
+        k[i] = e < n ? (((d[i] - dmin) >> shift) << 8) | e : 0xffffffffu;
+    }
+    warp_bitonic<E>(k, lane);
+    // equal shifted offsets between sorted neighbours (padding keys excluded)
+    bool tie = false;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const uint32_t down = __shfl_down_sync(FULL, k[i], 1);
+        const uint32_t wrap = __shfl_sync(FULL, k[i + 1 < E ? i + 1 : i], 0);
+        const uint32_t nxt = lane < 31 ? down : (i + 1 < E ? wrap : 0xffffffffu);
+        tie |= k[i] != 0xffffffffu && nxt != 0xffffffffu && (k[i] >> 8) == (nxt >> 8);
+    }
     const unsigned long long th = (unsigned long long)t << 32;
+    if (__any_sync(FULL, tie)) {
+        unsigned long long v[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const uint32_t e = i * 32 + lane;
+            v[i] = e < n ? a.bucket[start + e] : ~0ull;
+        }
+        warp_bitonic<E>(v, lane);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const uint32_t e = i * 32 + lane;
+            if (e < n) {
+                a.keys_out[start + e] = th | (v[i] >> 32);
+                a.vals_out[start + e] = (uint32_t)v[i];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const uint32_t e = i * 32 + lane;
         if (e < n) {
-            a.keys_out[start + e] = th | (v[i] >> 32);
-            a.vals_out[start + e] = (uint32_t)v[i];
+            const unsigned long long c = a.bucket[start + (k[i] & 0xffu)];
+            a.keys_out[start + e] = th | (c >> 32);
+            a.vals_out[start + e] = (uint32_t)c;
         }
     }
 }
