@@ -427,7 +427,7 @@ __device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned l
 // Both sorts in one launch, so that the few long big-tile CTAs overlap the many
 // short warp sorts: CTAs below n_big work through the big-tile list, the others
 // give each of their warps one tile.
-__global__ void __launch_bounds__(kBigThreads, 5) k_tile_sort(const TileSortArgs a, unsigned n_big)
+__global__ void __launch_bounds__(kBigThreads, 6) k_tile_sort(const TileSortArgs a, unsigned n_big)
 {
     __shared__ unsigned long long s[kBigChunk], s2[kBigChunk];
     __shared__ uint32_t s_idx;
