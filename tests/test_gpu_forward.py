@@ -232,6 +232,30 @@ def test_bucketed_sort_crowded_tiles(n):
     compare_images((rgb, depth, T), oracle.render(sc, cam), f"crowded{n}")
 
 
+@pytest.mark.parametrize("n,mode", [(60, "equal"), (120, "equal"), (200, "equal"), (256, "equal"),
+                                    (200, "near"), (250, "near")])
+def test_bucketed_sort_depth_ties(n, mode):
+    """Tiles of up to 256 instances whose depths tie: "equal" stacks the splats on five depth
+    planes (equal keys, ordered by record index), "near" spreads half over 2..6 and puts the
+    rest within a few units in the last place of 3.0, so that the warp sort's shifted 32-bit
+    keys tie while the depths differ.  Both must take the exact 64-bit order."""
+    torch = torch_cuda()
+    sc = I.uniform_box_scene(n, 700 + n, xy=(-0.01, 0.01), z=(2.0, 6.0), log_scale=(-6.0, 0.2))
+    rng = np.random.default_rng(n)
+    if mode == "equal":
+        sc.means[:, 2] = np.float32(2.0) + np.float32(0.5) * rng.integers(0, 5, n).astype(np.float32)
+    else:
+        near = rng.random(n) < 0.5
+        ulps = rng.integers(0, 6, int(near.sum())).astype(np.uint32)
+        sc.means[near, 2] = (np.float32(3.0).view(np.uint32) + ulps).view(np.float32)
+    cam = I.identity_camera(64, 64, 200.0)
+    a = _run([sc], [cam], sort=0)
+    bs = _check_sort(a, [sc], [cam])
+    assert (bs["ranges"][:, 1] - bs["ranges"][:, 0]).max() >= n // 2
+    b = _run([sc], [cam], sort=1)
+    _check_sort(b, [sc], [cam])
+
+
 def test_radix_and_bucketed_sorts_agree_multiview():
     torch = torch_cuda()
     s0 = I.uniform_box_scene(4000, 51, sh_degree=2)
