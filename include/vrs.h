@@ -166,7 +166,12 @@ typedef struct {
     int64_t off_ncontrib;      /* [n_pixels] uint32 last blended position + 1, written by
                                   vrs_render_fwd for plans made with backward = 1 (the
                                   reverse pass starts there); untouched otherwise */
-    int64_t off_order;         /* [n_tiles] uint32 tile work order (persistent path) */
+    int64_t off_order;         /* [n_tiles] uint32 tile work order, heaviest first (persistent
+                                  blend; reverse pass), then its bucket scratch.  Backward plans
+                                  also keep, in the workspace's last
+                                  ceil(n_tiles * tile^2 / 64 * 4 / 256) * 256 bytes, each 8x8
+                                  block's largest last blended position (uint32 [n_tiles][tile^2/64]),
+                                  written by vrs_render_fwd */
     int64_t off_grad2d;        /* [n_records][10] float 2D gradients (backward only) */
     int64_t off_tilesort;      /* uint32 [n_tiles] counts, [n_tiles] cursors, [n_tiles] list of
                                   tiles sorted by a whole CTA, [ceil(n_tiles / 1024)] block sums

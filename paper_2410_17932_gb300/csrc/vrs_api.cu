@@ -20,7 +20,7 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
                              uint32_t blend_max, int n_sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
-                              float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
+                              float *depth, float *Tf, uint32_t *ncontrib, uint32_t *tile_work, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
                               unsigned long long cap, int persistent, int count, int half_out,
                               int tiles_per_pull, const unsigned long long *bucket,
@@ -34,8 +34,10 @@ cudaError_t launch_render_resort(const ViewTable &vt, const float4 *viewtab, con
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
-                              const float *dL_ddepth, const float *dL_dT, float *grad2d,
+                              const float *dL_ddepth, const float *dL_dT, float *grad2d, const uint32_t *order,
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
+                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
                                    uint32_t *list, const uint4 *pairs, int scene, int n_sms, cudaStream_t s);
@@ -45,7 +47,14 @@ using namespace vrs;
 
 namespace {
 
-constexpr int kOrderTmp = 2 * 34;   // histogram + cursors of the work-order buckets
+constexpr int kOrderTmp = 2 * kOrderBuckets;   // histogram + cursors of the work-order buckets
+
+// Warps of a blend CTA: entries per tile of the reverse pass's work estimate.
+int warps_per_tile(int tile) { return tile * tile / 64; }
+
+// Backward plans: the reverse pass's per-warp work estimates, written by the
+// forward, take the workspace's last region (its offset follows from the size).
+int64_t work_bytes(const vrs_plan &P) { return P.n_tiles * warps_per_tile(P.tile) * 4; }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -57,6 +66,12 @@ int bits_for(int64_t n)
 }
 
 vrs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VRS_OK : VRS_ERR_CUDA; }
+
+uint32_t *work_estimates(const vrs_plan *P, void *workspace)
+{
+    return reinterpret_cast<uint32_t *>(static_cast<char *>(workspace) + P->workspace_bytes -
+                                        align_up(work_bytes(*P), 256));
+}
 
 template <typename T>
 T *at(void *ws, int64_t off) { return reinterpret_cast<T *>(static_cast<char *>(ws) + off); }
@@ -245,6 +260,7 @@ vrs_status vrs_plan_batch(const vrs_scene *scenes, int32_t n_scenes, const vrs_c
     P.off_pairs = take(rec * 32);
     P.off_raydepth = P.resort ? take(rec * 3 * 16) : 0;
     P.off_resort_flags = P.resort ? take(pix) : 0;
+    if (P.backward) take(work_bytes(P));   // the last region (see work_estimates)
     P.workspace_bytes = off;
     *plan = P;
     return VRS_OK;
@@ -351,7 +367,7 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
         at<uint32_t>(workspace, plan->off_vals[sb]), at<uint2>(workspace, plan->off_ranges),
         at<DevStatus>(workspace, plan->off_status), rgb, depth, T_final,
         plan->backward ? at<uint32_t>(workspace, plan->off_ncontrib) : nullptr,   // only the reverse pass reads it
-        order, order + plan->n_tiles, plan->n_tiles,
+        plan->backward ? work_estimates(plan, workspace) : nullptr, order, order + plan->n_tiles, plan->n_tiles,
         plan->n_records, (unsigned long long)plan->max_instances, plan->persistent,
         plan->half_out ? 0 : plan->count_pairs, plan->half_out, plan->tiles_per_pull,
         at<unsigned long long>(workspace, plan->off_keys[1]), at<unsigned long long>(workspace, plan->off_keys[sb]),
@@ -386,12 +402,17 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
     const DevStatus *st = at<DevStatus>(workspace, plan->off_status);
     cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float) * kGrad2D * (size_t)plan->n_records, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
+    // heaviest tiles first, so that the last wave holds no long tile
+    uint32_t *order = at<uint32_t>(workspace, plan->off_order);
+    e = launch_tile_order(at<uint2>(workspace, plan->off_ranges), work_estimates(plan, workspace),
+                          warps_per_tile(plan->tile), plan->n_tiles, st, order, order + plan->n_tiles, plan->n_sms, s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
     e = launch_render_bwd(vt, at<float4>(workspace, plan->off_status + 256),
                           at<float4>(workspace, plan->off_records),
                           at<uint32_t>(workspace, plan->off_vals[plan->sorted_buf]),
                           at<uint2>(workspace, plan->off_ranges), st,
                           at<uint32_t>(workspace, plan->off_ncontrib), T_final, dL_drgb, dL_ddepth,
-                          dL_dT, g2, plan->n_tiles, plan->n_records, (unsigned long long)plan->max_instances, s);
+                          dL_dT, g2, order, plan->n_tiles, plan->n_records, (unsigned long long)plan->max_instances, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
     // the touched-Gaussian list goes to the record-index buffer the sort left unused (when
     // it holds a record index per record), so that the forward's pair list stays intact and

@@ -32,6 +32,7 @@ struct BwdArgs {
     const float *g_depth;
     const float *g_T;        // nullable
     float *grad2d;
+    const uint32_t *order;   // tile of each CTA (heaviest first), or null: tile order
     int64_t n_records;
     unsigned long long cap;
 };
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     const float pxc = (float)(bx + 2 * (lane & 3)) + 0.5f, pyc = (float)(by + (lane >> 2)) + 0.5f;
     const float2 pxc2 = make_float2(pxc, pxc + 1.0f);
 
-    const int64_t t = blockIdx.x;
+    const int64_t t = a.order ? (int64_t)__ldg(a.order + blockIdx.x) : (int64_t)blockIdx.x;
     const int vi = view_of_tile(vt, t);
     const DevView &V = vt.v[vi];
     const float4 pp = a.viewtab[vi];
@@ -270,10 +271,10 @@ static cudaError_t launch_bwd_ts(const ViewTable &vt, const BwdArgs &a, int64_t 
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, const DevStatus *st,
                               const uint32_t *ncontrib, const float *Tf, const float *dL_drgb,
-                              const float *dL_ddepth, const float *dL_dT, float *grad2d,
+                              const float *dL_ddepth, const float *dL_dT, float *grad2d, const uint32_t *order,
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s)
 {
-    BwdArgs a{viewtab, rec, vals, ranges, st, ncontrib, Tf, dL_drgb, dL_ddepth, dL_dT, grad2d, n_records, cap};
+    BwdArgs a{viewtab, rec, vals, ranges, st, ncontrib, Tf, dL_drgb, dL_ddepth, dL_dT, grad2d, order, n_records, cap};
     if (n_tiles <= 0) return cudaSuccess;
     switch (vt.tile) {
         case 8: return launch_bwd_ts<8>(vt, a, n_tiles, s);

@@ -508,6 +508,18 @@ __device__ __forceinline__ void pair_u2(float K, float L, float l0, float l1, fl
 // Blend-kernel geometry and the staging of one instance into a tile's local
 // frame, shared by the forward and backward blend kernels.
 
+// Buckets of the tile work order: zero, then four per octave of the work estimate
+// (see order_bucket); the order's scratch holds a histogram and cursors of them.
+constexpr int kOrderBuckets = 129;
+
+__device__ __forceinline__ int order_bucket(uint32_t c)
+{
+    if (c == 0) return 0;
+    const int lz = 31 - __clz(c);                                  // floor(log2 c)
+    const int sub = lz >= 2 ? (int)((c >> (lz - 2)) & 3u) : (lz == 1 ? (int)((c & 1u) << 1) : 0);
+    return 1 + 4 * lz + sub;
+}
+
 template <int TS>
 struct BlendCfg {
     static constexpr int THREADS = TS * TS / 2;

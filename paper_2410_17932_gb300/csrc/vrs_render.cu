@@ -28,6 +28,7 @@ struct FwdArgs {
     float *Tf;
     uint32_t *ncontrib;
     const uint32_t *order;      // persistent: tile work order (heaviest first), or null: tile order
+    uint32_t *tile_work;        // LAST, nullable: per tile and warp, its block's largest last blended position
     int64_t n_tiles;
     int64_t n_records;
     unsigned long long cap;
@@ -250,6 +251,11 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
                 }
             }
         }
+        if (LAST && a.tile_work) {
+            // the reverse pass walks each block from its largest last position: its work estimate
+            const uint32_t m = __reduce_max_sync(FULL, max(P.last0, P.last1));
+            if (lane == 0) a.tile_work[t * Cfg::WARPS + w] = m;
+        }
         n_eval += (in0 ? P.stop0 : 0u) + (in1 ? P.stop1 : 0u);
         const int64_t HW = (int64_t)V.w * V.h;
         const int64_t lp = (int64_t)py * V.w + px;
@@ -304,30 +310,36 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
 }
 
 // ---------------------------------------------------------------------------
-// Work order for the persistent launch: tiles bucketed by floor(log2(count)),
-// heaviest bucket first (a longest-processing-time-first schedule).
+// Tile work order, heaviest first (a longest-processing-time-first schedule):
+// tiles bucketed by a work estimate, four buckets per octave.  The estimate is
+// the largest of a tile's wpt entries of work (the reverse pass: each warp's
+// largest last blended position), else the tile's instance count.
 
-constexpr int kBuckets = 34;
+__device__ __forceinline__ uint32_t tile_estimate(const uint2 *ranges, const uint32_t *work, int wpt, int64_t t)
+{
+    if (!work) return ranges[t].y - ranges[t].x;
+    uint32_t m = 0;
+    for (int i = 0; i < wpt; ++i) m = max(m, work[t * wpt + i]);
+    return m;
+}
 
-__global__ void k_order_hist(const uint2 *ranges, int64_t n_tiles, uint32_t *hist, const DevStatus *st)
+__global__ void k_order_hist(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles, uint32_t *hist,
+                             const DevStatus *st)
 {
     if (st->flags & ST_CAPACITY) return;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = ranges[t].y - ranges[t].x;
-        const int b = c == 0 ? 0 : 33 - __clz(c);
-        atomicAdd(&hist[b], 1u);
-    }
+         t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[order_bucket(tile_estimate(ranges, work, wpt, t))], 1u);
 }
 
-__global__ void k_order_scatter(const uint2 *ranges, int64_t n_tiles, const uint32_t *hist,
-                                uint32_t *cursor, uint32_t *order, const DevStatus *st)
+__global__ void k_order_scatter(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
+                                const uint32_t *hist, uint32_t *cursor, uint32_t *order, const DevStatus *st)
 {
     if (st->flags & ST_CAPACITY) return;
-    __shared__ uint32_t start[kBuckets];
+    __shared__ uint32_t start[kOrderBuckets];
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
-        for (int b = kBuckets - 1; b >= 0; --b) {
+        for (int b = kOrderBuckets - 1; b >= 0; --b) {
             start[b] = acc;
             acc += hist[b];
         }
@@ -335,10 +347,21 @@ __global__ void k_order_scatter(const uint2 *ranges, int64_t n_tiles, const uint
     __syncthreads();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = ranges[t].y - ranges[t].x;
-        const int b = c == 0 ? 0 : 33 - __clz(c);
+        const int b = order_bucket(tile_estimate(ranges, work, wpt, t));
         order[start[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
     }
+}
+
+// order_tmp: [kOrderBuckets] histogram + [kOrderBuckets] cursors.
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
+                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
+    if (e != cudaSuccess) return e;
+    const int g = n_sms * 4;
+    k_order_hist<<<g, 256, 0, s>>>(ranges, work, wpt, n_tiles, order_tmp, st);
+    k_order_scatter<<<g, 256, 0, s>>>(ranges, work, wpt, n_tiles, order_tmp, order_tmp + kOrderBuckets, order, st);
+    return cudaGetLastError();
 }
 
 template <int TS, bool PERSIST>
@@ -393,7 +416,7 @@ static int resident_ctas(int tile, bool count, bool last, bool half)
 
 cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
                               const uint32_t *vals, const uint2 *ranges, DevStatus *st, float *rgb,
-                              float *depth, float *Tf, uint32_t *ncontrib, uint32_t *order,
+                              float *depth, float *Tf, uint32_t *ncontrib, uint32_t *tile_work, uint32_t *order,
                               uint32_t *order_tmp, int64_t n_tiles, int64_t n_records,
                               unsigned long long cap, int persistent, int count, int half_out,
                               int tiles_per_pull, const unsigned long long *bucket,
@@ -417,6 +440,7 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
     a.depth = depth;
     a.Tf = Tf;
     a.ncontrib = ncontrib;
+    a.tile_work = ncontrib ? tile_work : nullptr;
     a.order = order;
     a.n_tiles = n_tiles;
     a.n_records = n_records;
@@ -427,12 +451,8 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
         e = cudaMemsetAsync(&st->work[0], 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
         if (persistent == 1) {
-            // heaviest tiles first; order_tmp: [kBuckets] histogram + [kBuckets] cursors
-            e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kBuckets, s);
+            e = launch_tile_order(ranges, nullptr, 0, n_tiles, st, order, order_tmp, n_sms, s);
             if (e != cudaSuccess) return e;
-            const int g = n_sms * 4;
-            k_order_hist<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, st);
-            k_order_scatter<<<g, 256, 0, s>>>(ranges, n_tiles, order_tmp, order_tmp + kBuckets, order, st);
         } else {
             a.order = nullptr;           // tile order: neighbouring tiles run together
         }

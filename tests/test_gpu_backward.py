@@ -114,6 +114,51 @@ def test_backward_tile_sizes_agree():
     _check(g8[0], ref, "tile 8")
 
 
+def _order_bucket(c):
+    """Four buckets per octave of a work estimate, 0 for none (the work order's buckets)."""
+    if c == 0:
+        return 0
+    lz = c.bit_length() - 1
+    sub = (c >> (lz - 2)) & 3 if lz >= 2 else ((c & 1) << 1 if lz == 1 else 0)
+    return 1 + 4 * lz + sub
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_backward_tile_order_heaviest_first(tile):
+    """The reverse pass takes its tiles heaviest first: the forward records, per tile and 8x8
+    block, the block's largest last blended position; the order is a permutation of the tiles
+    whose estimates (the largest of the tile's blocks) never rise by a bucket along it."""
+    sc, cam, gC, gD, _ = _training_subset(6)
+    cam2 = I.Camera(I._yaw_pitch(0.05, -0.03), [0.02, 0.01, 0.05], 58.0, 58.0, 37.0, 29.0, 75, 57)
+    g2 = I.upstream_grads([cam2], 9)[0]
+    ras, _ = _gpu_grads([sc], [cam, cam2], [gC, g2[0]], [gD, g2[1]], tile=tile)
+    P = ras.plan
+    ws = ras.workspace.cpu().numpy()
+    n_tiles, wpt, wgx = int(P.n_tiles), tile * tile // 64, tile // 8
+    order = ws[P.off_order:P.off_order + 4 * n_tiles].view(np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(n_tiles, dtype=np.uint32))
+    nb = n_tiles * wpt * 4
+    off_work = int(P.workspace_bytes) - (nb + 255) // 256 * 256
+    work = ws[off_work:off_work + nb].view(np.uint32).reshape(n_tiles, wpt)
+    last = ws[P.off_ncontrib:P.off_ncontrib + 4 * int(P.n_pixels)].view(np.uint32)
+    expect = np.zeros_like(work)
+    for v in range(2):
+        W, H, gw, gh = P.view_w[v], P.view_h[v], P.view_gw[v], P.view_gh[v]
+        plane = np.zeros((gh * tile, gw * tile), np.uint32)
+        b = P.view_pix_base[v]
+        plane[:H, :W] = last[b:b + W * H].reshape(H, W)
+        blocks = plane.reshape(gh * tile // 8, 8, gw * tile // 8, 8).max(axis=(1, 3))
+        for lt in range(gw * gh):
+            ty, tx = divmod(lt, gw)
+            for w in range(wpt):
+                expect[P.view_tile_base[v] + lt, w] = blocks[ty * wgx + w // wgx, tx * wgx + w % wgx]
+    assert np.array_equal(work, expect)
+    assert last.max() > 0
+    est = work.max(axis=1)
+    b = np.array([_order_bucket(int(est[t])) for t in order])
+    assert np.all(np.diff(b) <= 0)
+
+
 def test_autograd_function():
     torch = torch_cuda()
     from paper_2410_17932_gb300.render import Rasterizer, SceneTensors, render
