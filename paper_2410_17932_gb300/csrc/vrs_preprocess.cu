@@ -334,7 +334,7 @@ struct ShRow<true> {
 };
 
 template <int K, bool HALF>
-__global__ void __launch_bounds__(kPairThreads) k_pairs(const __grid_constant__ ViewTable vt,
+__global__ void __launch_bounds__(kPairThreads, 8) k_pairs(const __grid_constant__ ViewTable vt,
                                                         const __grid_constant__ PreParams p)
 {
     const unsigned FULL = 0xffffffffu;
