@@ -43,7 +43,7 @@ struct DevStatus {
     unsigned long long block_evals;
     unsigned long long scene_pairs[VRS_MAX_SCENES];   // visible (Gaussian, view) pairs per scene
     unsigned long long resort_flagged;                  // per-pixel order: pixels whose window overflowed
-    uint32_t work[8];          // counters: [0] persistent blend, [1..2] tile sort, [4] backward list
+    uint32_t work[8];          // counters: [0] persistent blend, [1..3] tile sort, [4] backward list
 };
 static_assert(sizeof(DevStatus) <= 256, "the status block is 256 bytes");
 
@@ -119,6 +119,33 @@ __device__ __forceinline__ float ex2_approx(float x)
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Programmatic dependent launch.  A kernel started by launch_pdl may be
+// scheduled while the kernel before it in the stream is still draining; its
+// threads call pdl_wait() first, which returns once that kernel has completed
+// and its writes are visible, so the body runs in stream order and only the
+// launch and the CTAs' scheduling overlap.  pdl_trigger() lets the next kernel
+// be scheduled once every CTA of this one has started.  Both are no-ops under
+// an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              const Args &...args)
+{
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt()

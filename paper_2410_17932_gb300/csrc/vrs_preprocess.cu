@@ -221,6 +221,8 @@ template <int PER>
 __global__ void __launch_bounds__(kDecideThreads) k_decide_listed(const __grid_constant__ ViewTable vt,
                                                                   const __grid_constant__ PreParams p)
 {
+    pdl_wait();
+    pdl_trigger();
     // the views' principal points, read by the blend kernels to build each
     // tile's local frame (the plan holds sizes only); every scene's launch
     // writes the same values
@@ -337,6 +339,8 @@ template <int K, bool HALF>
 __global__ void __launch_bounds__(kPairThreads, 8) k_pairs(const __grid_constant__ ViewTable vt,
                                                         const __grid_constant__ PreParams p)
 {
+    pdl_wait();
+    pdl_trigger();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned long long n_pairs_raw = p.st->scene_pairs[p.scene];
@@ -574,8 +578,7 @@ static cudaError_t launch_pairs(const ViewTable &vt, const PreParams &p, int64_t
     }
     const int64_t wave = (int64_t)(n_sms > 0 ? n_sms : 152) * per_sm;
     const unsigned grid = (unsigned)(want < wave ? want : wave);
-    k_pairs<K, HALF><<<grid > 0 ? grid : 1, kPairThreads, 0, s>>>(vt, p);
-    return cudaGetLastError();
+    return launch_pdl(k_pairs<K, HALF>, dim3(grid > 0 ? grid : 1), dim3(kPairThreads), 0, s, vt, p);
 }
 
 // Host launcher: two launches per scene (the SH degree is a template argument
@@ -607,9 +610,12 @@ cudaError_t launch_preprocess(const ViewTable &vt, const DevScene &S, int scene,
     // the screen, so a CTA gathers enough candidates to keep its threads busy);
     // several views: 2 per thread (a quarter of an eye's pairs survive, and more
     // CTAs keep more of the exact path's latency in flight)
-    if (n_views == 1) k_decide_listed<8><<<grid_for(S.n, 8 * kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
-    else k_decide_listed<2><<<grid_for(S.n, 2 * kDecideThreads), kDecideThreads, 0, stream>>>(vt, p);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e =
+        n_views == 1
+            ? launch_pdl(k_decide_listed<8>, dim3(grid_for(S.n, 8 * kDecideThreads)), dim3(kDecideThreads), 0, stream,
+                         vt, p)
+            : launch_pdl(k_decide_listed<2>, dim3(grid_for(S.n, 2 * kDecideThreads)), dim3(kDecideThreads), 0, stream,
+                         vt, p);
     if (e != cudaSuccess) return e;
     // one pair per thread, CTAs looping over the list: the grid is sized for the list's
     // capacity but capped at one resident wave, since the list holds only the visible pairs

@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS, BlendCfg<TS>::MIN_BLOCK
     __shared__ unsigned long long s_comp[Cfg::BATCH];   // sort mode 2: the tile's composites
     __shared__ unsigned long long s_cnt[3];
 
+    pdl_wait();
+    pdl_trigger();
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int bx = (w % Cfg::WGX) * 8, by = (w / Cfg::WGX) * 8;
@@ -365,7 +367,7 @@ cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt
 }
 
 template <int TS, bool PERSIST>
-static void launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
+static cudaError_t launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
     // the last-blended-position plane is written only when the caller keeps it
     constexpr int T = BlendCfg<TS>::THREADS;
@@ -374,6 +376,7 @@ static void launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool
     else if (count) k_render_fwd<TS, true, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
     else if (a.ncontrib) k_render_fwd<TS, false, true, PERSIST><<<grid, T, 0, s>>>(vt, a);
     else k_render_fwd<TS, false, false, PERSIST><<<grid, T, 0, s>>>(vt, a);
+    return cudaGetLastError();
 }
 
 // The persistent schedule is a separate instantiation, so that the per-tile
@@ -381,9 +384,7 @@ static void launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int grid, bool
 template <int TS>
 static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
-    if (a.persistent) launch_fwd_tsp<TS, true>(vt, a, grid, count, s);
-    else launch_fwd_tsp<TS, false>(vt, a, grid, count, s);
-    return cudaGetLastError();
+    return a.persistent ? launch_fwd_tsp<TS, true>(vt, a, grid, count, s) : launch_fwd_tsp<TS, false>(vt, a, grid, count, s);
 }
 
 // CTAs of the persistent instantiation that fit on one SM at once.

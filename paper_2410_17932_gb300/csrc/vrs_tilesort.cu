@@ -68,6 +68,8 @@ __device__ __forceinline__ uint32_t block_sum1024(uint32_t v, uint32_t *sh)
 
 __global__ void __launch_bounds__(kScanBlock) k_tile_blocksum(const TileSortArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t sh[32];
     if (a.st->flags & ST_CAPACITY) return;    // every tile range is written, even with no instances
     const int64_t t = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
@@ -83,6 +85,8 @@ constexpr unsigned kDirectBlocks = 64;
 
 __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, int direct)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t sh[32];
     __shared__ uint32_t base_s;
     if (a.st->flags & ST_CAPACITY) return;    // every tile range is written, even with no instances
@@ -119,7 +123,10 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, 
     if (t < a.n_tiles) {
         a.ranges[t] = v ? make_uint2(off, off + v) : make_uint2(0u, 0u);
         a.cursor[t] = off;
-        if (v > (uint32_t)kSmallMax && v > a.blend_max) a.big_list[atomicAdd(&a.st->work[1], 1u)] = (uint32_t)t;
+        if (v > (uint32_t)kSmallMax && v > a.blend_max) {
+            const uint32_t slot = atomicAdd(&a.st->work[1], 1u);
+            if (slot < (uint32_t)a.n_tiles) a.big_list[slot] = (uint32_t)t;   // always, the counter starting at 0
+        }
     }
 }
 
@@ -128,6 +135,8 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, 
 // atomics, not by bandwidth.
 __global__ void __launch_bounds__(256) k_tile_scatter(const TileSortArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t M = live_instances(a.st, a.cap);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += 4 * stride) {
@@ -376,7 +385,7 @@ __device__ void block_merge(const unsigned long long *src, uint32_t la, uint32_t
 __device__ __forceinline__ void sort_big_tiles(const TileSortArgs &a, unsigned long long *s, unsigned long long *s2,
                                                uint32_t &s_idx)
 {
-    const uint32_t n_big = a.st->work[1];
+    const uint32_t n_big = min(a.st->work[1], (uint32_t)a.n_tiles);
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.st->work[2], 1u);
         __syncthreads();
@@ -431,13 +440,27 @@ __global__ void __launch_bounds__(kBigThreads, 6) k_tile_sort(const TileSortArgs
 {
     __shared__ unsigned long long s[kBigChunk], s2[kBigChunk];
     __shared__ uint32_t s_idx;
-    if (live_instances(a.st, a.cap) == 0) return;
-    if (blockIdx.x < n_big) {
-        sort_big_tiles(a, s, s2, s_idx);
-        return;
+    pdl_wait();
+    pdl_trigger();
+    if (live_instances(a.st, a.cap) != 0) {
+        if (blockIdx.x < n_big) {
+            sort_big_tiles(a, s, s2, s_idx);
+        } else {
+            const int64_t t = (int64_t)(blockIdx.x - n_big) * (kBigThreads / 32) + (threadIdx.x >> 5);
+            sort_small_tile(a, t, threadIdx.x & 31);
+        }
     }
-    const int64_t t = (int64_t)(blockIdx.x - n_big) * (kBigThreads / 32) + (threadIdx.x >> 5);
-    sort_small_tile(a, t, threadIdx.x & 31);
+    // the last CTA to finish clears the big-tile counters for the next sort (the
+    // scan appends to work[1]; no CTA reads them after its own ticket)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.st->work[3], 1u) == gridDim.x - 1) {
+            a.st->work[1] = 0u;
+            a.st->work[2] = 0u;
+            a.st->work[3] = 0u;
+        }
+    }
 }
 
 cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *vals_in,
@@ -449,13 +472,19 @@ cudaError_t launch_tile_sort(const unsigned long long *keys_in, const uint32_t *
     if (n_tiles <= 0) return cudaSuccess;
     TileSortArgs a{keys_in, vals_in, bucket, keys_out, vals_out, cnt, cursor, blocksum, big_list,
                    ranges, st, cap, n_tiles, blend_max};
-    cudaError_t e = cudaMemsetAsync(&st->work[1], 0, 2 * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
+    // the big-tile counters (work[1], work[2]) are zero here: cleared with the status
+    // block by the preprocess, and again by the last CTA of every tile sort
     const unsigned nb = (unsigned)((n_tiles + kScanBlock - 1) / kScanBlock);
     const int direct = nb <= kDirectBlocks ? 1 : 0;
-    if (!direct) k_tile_blocksum<<<nb, kScanBlock, 0, s>>>(a);
-    k_tile_scan<<<nb, kScanBlock, 0, s>>>(a, direct);
-    k_tile_scatter<<<n_sms * 8, 256, 0, s>>>(a);
+    cudaError_t e;
+    if (!direct) {
+        e = launch_pdl(k_tile_blocksum, dim3(nb), dim3(kScanBlock), 0, s, a);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_pdl(k_tile_scan, dim3(nb), dim3(kScanBlock), 0, s, a, direct);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_tile_scatter, dim3(n_sms * 8), dim3(256), 0, s, a);
+    if (e != cudaSuccess) return e;
     const unsigned n_big = (unsigned)n_sms * 2u;
     const int64_t per = kBigThreads / 32;
     k_tile_sort<<<(unsigned)(n_big + (n_tiles + per - 1) / per), kBigThreads, 0, s>>>(a, n_big);

@@ -232,6 +232,22 @@ def test_bucketed_sort_crowded_tiles(n):
     compare_images((rgb, depth, T), oracle.render(sc, cam), f"crowded{n}")
 
 
+def test_bucketed_sort_repeated_calls():
+    """vrs_bin_sort called again on the same instances, without a new preprocess, gives the same
+    lists: the big-tile list and its claim counter start from zero on every call (the last CTA
+    of each tile sort clears them)."""
+    torch = torch_cuda()
+    sc = I.uniform_box_scene(1500, 77, xy=(-0.01, 0.01), z=(2.0, 6.0), log_scale=(-6.0, 0.2))
+    cam = I.identity_camera(64, 64, 200.0)
+    a = _run([sc], [cam], sort=0)
+    bs = _check_sort(a, [sc], [cam])
+    assert (bs["ranges"][:, 1] - bs["ranges"][:, 0]).max() > 1024
+    for _ in range(3):
+        a.bin_sort()
+        torch.cuda.synchronize()
+        _check_sort(a, [sc], [cam])
+
+
 @pytest.mark.parametrize("n,mode", [(60, "equal"), (120, "equal"), (200, "equal"), (256, "equal"),
                                     (200, "near"), (250, "near")])
 def test_bucketed_sort_depth_ties(n, mode):
