@@ -38,6 +38,8 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
 cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
                               const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, cudaStream_t s);
+cudaError_t launch_clear_pair_rows(const uint4 *pairs, const DevStatus *st, int scene, int64_t n_gauss,
+                                   int64_t rec_base, float *grad2d, int n_sms, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
                                    const int8_t *views, int n_views, const float *grad2d, DevStatus *st,
                                    uint32_t *list, const uint4 *pairs, int scene, int n_sms, cudaStream_t s);
@@ -156,6 +158,19 @@ int views_of_scene(const vrs_plan *P, int s, int8_t *out)
     for (int v = 0; v < P->n_views; ++v)
         if (P->view_scene[v] == s) out[n++] = (int8_t)v;
     return n;
+}
+
+// Backward plans whose reverse pass reads only the visible pairs' 2D-gradient rows: every
+// scene with Gaussians has one view, and the touched-Gaussian list fits the spare
+// record-index buffer (so the pair list survives for it).
+bool pair_grads(const vrs_plan *P)
+{
+    if (!P->backward || P->max_instances < P->n_records) return false;
+    for (int s = 0; s < P->n_scenes; ++s) {
+        int8_t vl[VRS_MAX_VIEWS];
+        if (P->scene_n[s] > 0 && views_of_scene(P, s, vl) > 1) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -400,8 +415,24 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float *g2 = at<float>(workspace, plan->off_grad2d);
     const DevStatus *st = at<DevStatus>(workspace, plan->off_status);
-    cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float) * kGrad2D * (size_t)plan->n_records, s);
-    if (e != cudaSuccess) return VRS_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (pair_grads(plan)) {
+        // every scene has one view: only its visible pairs' rows are read, and cleared
+        int64_t pb = 0;
+        for (int sc = 0; sc < plan->n_scenes; ++sc) {
+            int8_t vl[VRS_MAX_VIEWS];
+            const int nv = views_of_scene(plan, sc, vl);
+            if (nv == 1) {
+                e = launch_clear_pair_rows(at<uint4>(workspace, plan->off_pairs) + 2 * pb, st, sc, plan->scene_n[sc],
+                                           plan->view_rec_base[vl[0]], g2, plan->n_sms, s);
+                if (e != cudaSuccess) return VRS_ERR_CUDA;
+            }
+            pb += (int64_t)plan->scene_n[sc] * nv;
+        }
+    } else {
+        e = cudaMemsetAsync(g2, 0, sizeof(float) * kGrad2D * (size_t)plan->n_records, s);
+        if (e != cudaSuccess) return VRS_ERR_CUDA;
+    }
     // heaviest tiles first, so that the last wave holds no long tile
     uint32_t *order = at<uint32_t>(workspace, plan->off_order);
     e = launch_tile_order(at<uint2>(workspace, plan->off_ranges), work_estimates(plan, workspace),

@@ -567,6 +567,33 @@ __device__ __forceinline__ bool touched_warp(const ViewTable &vt, const ParamArg
     return ((((uint64_t)hi << 32) | lo) >> off & 31u) != 0u;
 }
 
+// A scene with one view: its reverse pass and chain rule read only the 2D-gradient rows
+// of the forward's visible pairs, so only those are cleared (the pair list's records,
+// a few percent of the scene's) instead of every record's.
+__global__ void __launch_bounds__(256) k_clear_pair_rows(const uint4 *pairs, const DevStatus *st, int scene,
+                                                         unsigned long long pair_cap, int64_t rec_base,
+                                                         float *grad2d)
+{
+    if (st->flags & ST_CAPACITY) return;
+    const unsigned long long n_raw = st->scene_pairs[scene];
+    const unsigned long long n = n_raw < pair_cap ? n_raw : pair_cap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        float2 *r = reinterpret_cast<float2 *>(grad2d + (size_t)(rec_base + __ldg(&pairs[2 * i].x)) * kGrad2D);
+#pragma unroll
+        for (int k = 0; k < kGrad2D / 2; ++k) r[k] = make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t launch_clear_pair_rows(const uint4 *pairs, const DevStatus *st, int scene, int64_t n_gauss,
+                                   int64_t rec_base, float *grad2d, int n_sms, cudaStream_t s)
+{
+    if (n_gauss <= 0) return cudaSuccess;
+    k_clear_pair_rows<<<(n_sms > 0 ? n_sms : 152) * 4, 256, 0, s>>>(pairs, st, scene, (unsigned long long)n_gauss,
+                                                                     rec_base, grad2d);
+    return cudaGetLastError();
+}
+
 // Most Gaussians touch no pixel of any view: a light pass lists those that do
 // (one warp-aggregated atomic per warp), and the chain rule, heavy in registers,
 // then walks that list densely.

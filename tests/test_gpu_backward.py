@@ -114,6 +114,37 @@ def test_backward_tile_sizes_agree():
     _check(g8[0], ref, "tile 8")
 
 
+@pytest.mark.parametrize("two_views", [False, True])
+def test_backward_twice_after_one_forward(two_views):
+    """A second reverse pass after the same forward gives the same gradients: the 2D-gradient
+    rows start at zero each time (one view: cleared by the preprocess and by the chain rule
+    after reading them; several views: cleared before the reverse pass)."""
+    torch = torch_cuda()
+    sc, cam, gC, gD, _ = _training_subset(8)
+    views, gCs, gDs = [cam], [gC], [gD]
+    if two_views:
+        cam2 = I.Camera(I._yaw_pitch(0.03, 0.01), [0.02, 0.0, 0.05], 57.0, 57.0, 31.0, 30.0, 62, 60)
+        g2 = I.upstream_grads([cam2], 11)[0]
+        views, gCs, gDs = [cam, cam2], [gC, g2[0]], [gD, g2[1]]
+    ras, sts = make_rasterizer([sc], views, backward=True)
+    ras.forward()
+    gCt = torch.zeros_like(ras.rgb)
+    gDt = torch.zeros_like(ras.depth)
+    for v in range(len(views)):
+        b, W, H = ras.view_slices(v)
+        gCt[3 * b:3 * b + 3 * W * H] = torch.as_tensor(gCs[v].reshape(-1), device="cuda")
+        gDt[b:b + W * H] = torch.as_tensor(gDs[v].reshape(-1), device="cuda")
+    runs = []
+    for _ in range(2):
+        gr = ras.backward_params(gCt, gDt, None)
+        torch.cuda.synchronize()
+        runs.append({k: getattr(gr[0], k).cpu().numpy().astype(np.float64) for k in NAMES})
+    for k in NAMES:
+        a, b = runs
+        assert np.abs(a[k]).max() > 0, k
+        assert np.allclose(a[k], b[k], rtol=1e-4, atol=1e-6 * np.abs(a[k]).max()), k
+
+
 def _order_bucket(c):
     """Four buckets per octave of a work estimate, 0 for none (the work order's buckets)."""
     if c == 0:
