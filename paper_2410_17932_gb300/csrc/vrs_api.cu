@@ -37,7 +37,8 @@ cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const 
                               const float *dL_ddepth, const float *dL_dT, float *grad2d, const uint32_t *order,
                               int64_t n_tiles, int64_t n_records, unsigned long long cap, cudaStream_t s);
 cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
-                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, cudaStream_t s);
+                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, bool clear_tmp,
+                              cudaStream_t s);
 cudaError_t launch_clear_pair_rows(const uint4 *pairs, const DevStatus *st, int scene, int64_t n_gauss,
                                    int64_t rec_base, float *grad2d, int n_sms, cudaStream_t s);
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,
@@ -415,7 +416,11 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float *g2 = at<float>(workspace, plan->off_grad2d);
     const DevStatus *st = at<DevStatus>(workspace, plan->off_status);
-    cudaError_t e = cudaSuccess;
+    // the work order's scratch first, so that the clearing, order and reverse-pass kernels
+    // follow one another without a memset between them
+    uint32_t *order = at<uint32_t>(workspace, plan->off_order);
+    cudaError_t e = cudaMemsetAsync(order + plan->n_tiles, 0, sizeof(uint32_t) * kOrderTmp, s);
+    if (e != cudaSuccess) return VRS_ERR_CUDA;
     if (pair_grads(plan)) {
         // every scene has one view: only its visible pairs' rows are read, and cleared
         int64_t pb = 0;
@@ -434,9 +439,9 @@ vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene
         if (e != cudaSuccess) return VRS_ERR_CUDA;
     }
     // heaviest tiles first, so that the last wave holds no long tile
-    uint32_t *order = at<uint32_t>(workspace, plan->off_order);
     e = launch_tile_order(at<uint2>(workspace, plan->off_ranges), work_estimates(plan, workspace),
-                          warps_per_tile(plan->tile), plan->n_tiles, st, order, order + plan->n_tiles, plan->n_sms, s);
+                          warps_per_tile(plan->tile), plan->n_tiles, st, order, order + plan->n_tiles, plan->n_sms,
+                          false, s);
     if (e != cudaSuccess) return VRS_ERR_CUDA;
     e = launch_render_bwd(vt, at<float4>(workspace, plan->off_status + 256),
                           at<float4>(workspace, plan->off_records),

@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
     __shared__ uint32_t wGR[Cfg::WARPS][kGroup];
     int ng = 0;
 
+    pdl_wait();
+    pdl_trigger();
     if (a.st->flags & ST_CAPACITY) return;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -264,8 +266,7 @@ __global__ void __launch_bounds__(BlendCfg<TS>::THREADS)
 template <int TS>
 static cudaError_t launch_bwd_ts(const ViewTable &vt, const BwdArgs &a, int64_t n_tiles, cudaStream_t s)
 {
-    k_render_bwd<TS><<<(unsigned)n_tiles, BlendCfg<TS>::THREADS, 0, s>>>(vt, a);
-    return cudaGetLastError();
+    return launch_pdl(k_render_bwd<TS>, dim3((unsigned)n_tiles), dim3(BlendCfg<TS>::THREADS), 0, s, vt, a);
 }
 
 cudaError_t launch_render_bwd(const ViewTable &vt, const float4 *viewtab, const float4 *rec,
@@ -574,6 +575,8 @@ __global__ void __launch_bounds__(256) k_clear_pair_rows(const uint4 *pairs, con
                                                          unsigned long long pair_cap, int64_t rec_base,
                                                          float *grad2d)
 {
+    pdl_wait();
+    pdl_trigger();
     if (st->flags & ST_CAPACITY) return;
     const unsigned long long n_raw = st->scene_pairs[scene];
     const unsigned long long n = n_raw < pair_cap ? n_raw : pair_cap;
@@ -607,6 +610,8 @@ __global__ void __launch_bounds__(kTouchedThreads) k_touched(const __grid_consta
     __shared__ uint32_t s_cnt[kTouchedWarps], s_base[kTouchedWarps];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int g0 = (blockIdx.x * blockDim.x + threadIdx.x) - lane;
+    pdl_wait();
+    pdl_trigger();
     if (p.st->flags & ST_CAPACITY) return;     // uniform over the grid
     const int g = g0 + lane;
     const bool t = g0 < p.S.n && touched_warp(vt, p, g0, lane) && g < p.S.n;
@@ -634,6 +639,8 @@ __global__ void __launch_bounds__(kTouchedThreads) k_touched_pairs(const __grid_
 {
     __shared__ uint32_t s_cnt[kTouchedWarps], s_base[kTouchedWarps];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    pdl_wait();
+    pdl_trigger();
     if (p.st->flags & ST_CAPACITY) return;     // uniform over the grid
     const unsigned long long n_raw = p.st->scene_pairs[p.scene];
     const unsigned long long n = n_raw < p.pair_cap ? n_raw : p.pair_cap;
@@ -674,6 +681,8 @@ template <int K>
 __global__ void __launch_bounds__(128) k_backward_params(const __grid_constant__ ViewTable vt,
                                                          const __grid_constant__ ParamArgs p)
 {
+    pdl_wait();
+    pdl_trigger();
     if (p.st->flags & ST_CAPACITY) return;
     const uint32_t n = *p.list_count;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -689,8 +698,7 @@ static cudaError_t launch_params_k(const ViewTable &vt, const ParamArgs &p, int 
         cudaGetLastError();
         per_sm = 2;
     }
-    k_backward_params<K><<<(unsigned)(n_sms * per_sm), 128, 0, s>>>(vt, p);
-    return cudaGetLastError();
+    return launch_pdl(k_backward_params<K>, dim3((unsigned)(n_sms * per_sm)), dim3(128), 0, s, vt, p);
 }
 
 cudaError_t launch_backward_params(const ViewTable &vt, const DevScene &S, const DevScene &G,

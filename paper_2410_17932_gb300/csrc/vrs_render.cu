@@ -328,6 +328,8 @@ __device__ __forceinline__ uint32_t tile_estimate(const uint2 *ranges, const uin
 __global__ void k_order_hist(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles, uint32_t *hist,
                              const DevStatus *st)
 {
+    pdl_wait();
+    pdl_trigger();
     if (st->flags & ST_CAPACITY) return;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -337,6 +339,8 @@ __global__ void k_order_hist(const uint2 *ranges, const uint32_t *work, int wpt,
 __global__ void k_order_scatter(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
                                 const uint32_t *hist, uint32_t *cursor, uint32_t *order, const DevStatus *st)
 {
+    pdl_wait();
+    pdl_trigger();
     if (st->flags & ST_CAPACITY) return;
     __shared__ uint32_t start[kOrderBuckets];
     if (threadIdx.x == 0) {
@@ -354,16 +358,22 @@ __global__ void k_order_scatter(const uint2 *ranges, const uint32_t *work, int w
     }
 }
 
-// order_tmp: [kOrderBuckets] histogram + [kOrderBuckets] cursors.
+// order_tmp: [kOrderBuckets] histogram + [kOrderBuckets] cursors, cleared here unless
+// the caller has (clear_tmp = false: cleared earlier in the stream).
 cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *work, int wpt, int64_t n_tiles,
-                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, cudaStream_t s)
+                              const DevStatus *st, uint32_t *order, uint32_t *order_tmp, int n_sms, bool clear_tmp,
+                              cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
+    cudaError_t e;
+    if (clear_tmp) {
+        e = cudaMemsetAsync(order_tmp, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 g(n_sms * 4), b(256);
+    e = launch_pdl(k_order_hist, g, b, 0, s, ranges, work, wpt, n_tiles, order_tmp, st);
     if (e != cudaSuccess) return e;
-    const int g = n_sms * 4;
-    k_order_hist<<<g, 256, 0, s>>>(ranges, work, wpt, n_tiles, order_tmp, st);
-    k_order_scatter<<<g, 256, 0, s>>>(ranges, work, wpt, n_tiles, order_tmp, order_tmp + kOrderBuckets, order, st);
-    return cudaGetLastError();
+    return launch_pdl(k_order_scatter, g, b, 0, s, ranges, work, wpt, n_tiles, (const uint32_t *)order_tmp,
+                      order_tmp + kOrderBuckets, order, st);
 }
 
 template <int TS, bool PERSIST>
@@ -452,7 +462,7 @@ cudaError_t launch_render_fwd(const ViewTable &vt, const float4 *viewtab, const 
         e = cudaMemsetAsync(&st->work[0], 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
         if (persistent == 1) {
-            e = launch_tile_order(ranges, nullptr, 0, n_tiles, st, order, order_tmp, n_sms, s);
+            e = launch_tile_order(ranges, nullptr, 0, n_tiles, st, order, order_tmp, n_sms, true, s);
             if (e != cudaSuccess) return e;
         } else {
             a.order = nullptr;           // tile order: neighbouring tiles run together
