@@ -44,8 +44,11 @@
  *    Errors detectable only on the device (instance capacity exceeded, a
  *    non-finite parameter, an all-zero quaternion) set bits in a status word
  *    inside the workspace; kernels after a capacity overflow skip their work.
- *    vrs_query_status reads that word.  No kernel waits on another, so no
- *    call can hang on the device.
+ *    vrs_query_status reads that word.  No kernel spins on a flag or a counter
+ *    that another kernel sets; the only waits are those of programmatic
+ *    dependent launch (a kernel's first instruction waits until the kernel
+ *    before it in the stream has completed), so no call can hang on the
+ *    device.
  *
  * Parameterisation (Sec. 3.1: opacity, colour, scale and rotation per splat):
  *  means [n][3], log_scales [n][3] (log of the per-axis standard deviation),
@@ -299,7 +302,12 @@ vrs_status vrs_render_fwd(const vrs_plan *plan, void *workspace, float *rgb, flo
  * ACCUMULATED (+=) into per-scene device arrays shaped like the parameters:
  * grads[s] holds g_means, g_log_scales, g_quats, g_opacity_logits, g_sh for
  * scene s in the fields of a vrs_scene (const is cast away; n and sh_degree
- * must match). */
+ * must match).  Each call starts from zeroed record gradients, so it may be
+ * repeated after one forward; it also writes the call's record (2D)
+ * gradients at workspace + plan.off_grad2d, [n_records][10] floats: dL/d of
+ * (u, v, Sigma'_xx, Sigma'_xy, Sigma'_yy, opacity, r, g, b, depth).  When every
+ * scene has one view only the rows of the visible (Gaussian, view) pairs are
+ * cleared and written; the other rows keep whatever they held. */
 vrs_status vrs_render_bwd(const vrs_plan *plan, void *workspace, const vrs_scene *scenes,
                           const vrs_camera *views, const float *T_final, const float *dL_drgb,
                           const float *dL_ddepth, const float *dL_dT, const vrs_scene *grads,
