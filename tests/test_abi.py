@@ -110,6 +110,12 @@ def test_plan_sizes_and_layout_on_host(lib):
     assert p.off_keys[1] - p.off_keys[0] >= 8 * p.max_instances
     assert p.off_ncontrib - p.off_ranges >= 8 * p.n_tiles
     assert p.off_order - p.off_ncontrib >= 4 * p.n_pixels
+    # backward plans: the forward's per-warp work estimates (tile^2 / 64 per tile) take the
+    # workspace's last 256-byte-rounded region, after the pair list
+    work = (p.n_tiles * (16 * 16 // 64) * 4 + 255) // 256 * 256
+    assert p.workspace_bytes - work >= p.off_pairs + 32 * p.n_records
+    code, q = _plan(L, [(2016, 2240, 0), (2016, 2240, 0)], backward=0)
+    assert code == L.VRS_OK and q.workspace_bytes <= p.workspace_bytes - work
 
 
 @pytest.mark.parametrize("bad", [
