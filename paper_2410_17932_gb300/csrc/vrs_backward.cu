@@ -9,13 +9,21 @@
 // sums S_C = sum_{j>i} rgb_j w_j and S_D = sum_{j>i} d_j w_j (w_j = alpha_j T_j):
 //   dL/dalpha_i = T_i (g_C . rgb_i + g_D d_i) - (g_C . S_C + g_D S_D + g_T T_final) / (1 - alpha_i).
 // The staging, culling and alpha of every pair are the forward's, bit for bit
-// (shared device functions), so the same pairs are blended.  Per splat, the 10
-// gradients of the warp's 64 pixels are summed with shuffles and added to the
-// splat's record gradient with one atomic per value.
+// (shared device functions), so the same pairs are blended.  Each warp owns an
+// 8x8 block; per splat its lanes write their 10 gradient terms to a per-warp
+// shared-memory buffer, and every three splats lane p sums row p and adds it to
+// the splat's record gradient with one atomic.  CTA i takes the i-th tile of a
+// work order, heaviest first by the forward's per-block estimates.
 //
-// k_backward_params: per Gaussian, the chain rule from the record gradients of
-// each view to means, log-scales, quaternion, opacity logit and SH coefficients,
-// accumulated into the caller's arrays.
+// k_clear_pair_rows: for a scene with one view, clears the record gradients of
+// its visible pairs, the only ones the pass reads, before it runs.
+//
+// k_touched / k_touched_pairs: the list of Gaussians with a nonzero record
+// gradient in some view.
+//
+// k_backward_params: per listed Gaussian, the chain rule from the record
+// gradients of each view to means, log-scales, quaternion, opacity logit and SH
+// coefficients, accumulated into the caller's arrays.
 #include "vrs_internal.cuh"
 
 namespace vrs {

@@ -394,7 +394,8 @@ static cudaError_t launch_fwd_tsp(const ViewTable &vt, const FwdArgs &a, int gri
 template <int TS>
 static cudaError_t launch_fwd_ts(const ViewTable &vt, const FwdArgs &a, int grid, bool count, cudaStream_t s)
 {
-    return a.persistent ? launch_fwd_tsp<TS, true>(vt, a, grid, count, s) : launch_fwd_tsp<TS, false>(vt, a, grid, count, s);
+    return a.persistent ? launch_fwd_tsp<TS, true>(vt, a, grid, count, s)
+                        : launch_fwd_tsp<TS, false>(vt, a, grid, count, s);
 }
 
 // CTAs of the persistent instantiation that fit on one SM at once.

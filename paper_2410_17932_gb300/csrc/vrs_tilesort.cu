@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_scan(const TileSortArgs a, 
         a.cursor[t] = off;
         if (v > (uint32_t)kSmallMax && v > a.blend_max) {
             const uint32_t slot = atomicAdd(&a.st->work[1], 1u);
-            if (slot < (uint32_t)a.n_tiles) a.big_list[slot] = (uint32_t)t;   // always, the counter starting at 0
+            // the counter starts at zero, so the slot is in range; the test keeps a sort
+            // that did not run to its end from sending the next one past the list
+            if (slot < (uint32_t)a.n_tiles) a.big_list[slot] = (uint32_t)t;
         }
     }
 }
