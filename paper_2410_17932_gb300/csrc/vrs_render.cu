@@ -342,13 +342,15 @@ __global__ void k_order_scatter(const uint2 *ranges, const uint32_t *work, int w
     pdl_wait();
     pdl_trigger();
     if (st->flags & ST_CAPACITY) return;
-    __shared__ uint32_t start[kOrderBuckets];
-    if (threadIdx.x == 0) {
+    // bucket b starts after every heavier bucket's tiles: the histogram is read once into
+    // shared memory, then each bucket's start is summed by its own thread
+    __shared__ uint32_t h[kOrderBuckets], start[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = hist[b];
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) {
         uint32_t acc = 0;
-        for (int b = kOrderBuckets - 1; b >= 0; --b) {
-            start[b] = acc;
-            acc += hist[b];
-        }
+        for (int q = b + 1; q < kOrderBuckets; ++q) acc += h[q];
+        start[b] = acc;
     }
     __syncthreads();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tiles;
